@@ -1,0 +1,106 @@
+"""ORACLE — test infrastructure only.
+
+Plain FP64 construction of the axisymmetric scale-discretised wavelets and
+scaling function of Sect. 2.2 (smooth generating functions of McEwen et al.
+2008), the scale range J, and the band-limits of the multiresolution
+algorithm of Sect. 3.1.  Integrals use scipy's adaptive quadrature (a library
+primitive); nothing here is shared with the GPU library.
+"""
+import functools
+import math
+
+import numpy as np
+from scipy import integrate
+
+
+def s(t):
+    """Bump function s(t) = exp(-1/(1-t^2)) on (-1, 1), zero elsewhere (Sect. 2.2)."""
+    if -1.0 < t < 1.0:
+        return math.exp(-1.0 / (1.0 - t * t))
+    return 0.0
+
+
+def s_lambda(t, lam):
+    """s_lambda(t) = s(2 lambda/(lambda-1) (t - 1/lambda) - 1), support [1/lambda, 1] (Sect. 2.2)."""
+    return s(2.0 * lam / (lam - 1.0) * (t - 1.0 / lam) - 1.0)
+
+
+def _integrand(u, lam):
+    return s_lambda(u, lam) ** 2 / u
+
+
+def _integral(lo, hi, lam):
+    val, _ = integrate.quad(_integrand, lo, hi, args=(lam,), epsabs=0.0,
+                            epsrel=1e-13, limit=400)
+    return val
+
+
+@functools.lru_cache(maxsize=None)
+def _denominator(lam):
+    return _integral(1.0 / lam, 1.0, lam)
+
+
+@functools.lru_cache(maxsize=None)
+def k_lambda(t, lam):
+    """Eq. (smoothscaling): ratio of the integrals of s_lambda^2(t')/t' over
+    [t, 1] and [1/lambda, 1]; unity for t <= 1/lambda, zero for t >= 1."""
+    lam = float(lam)
+    if t <= 1.0 / lam:
+        return 1.0
+    if t >= 1.0:
+        return 0.0
+    return _integral(t, 1.0, lam) / _denominator(lam)
+
+
+def kappa_lambda(t, lam):
+    """Wavelet generating function kappa_lambda(t) = sqrt(k(t/lambda) - k(t)) (Sect. 2.2).
+    A difference that rounds below zero is taken as zero."""
+    d = k_lambda(t / lam, lam) - k_lambda(t, lam)
+    return math.sqrt(d) if d > 0.0 else 0.0
+
+
+def eta_lambda(t, lam):
+    """Scaling generating function eta_lambda(t) = sqrt(k(t)) (Sect. 2.2)."""
+    return math.sqrt(k_lambda(t, lam))
+
+
+def jmax(L, B):
+    """J = ceil(log_B(L-1)) (Sect. 2.2), evaluated in integers as the smallest
+    J >= 0 with B^J >= L-1."""
+    J = 0
+    while B ** J < L - 1:
+        J += 1
+    return J
+
+
+def check_params(L, B, J0):
+    J = jmax(L, B)
+    if not (L >= 2 and B >= 2 and 0 <= J0 < J):
+        raise ValueError("need L >= 2, B >= 2 and 0 <= J0 < J (got L=%d B=%d J0=%d J=%d)"
+                         % (L, B, J0, J))
+    return J
+
+
+def psi_l0(L, B, j):
+    """Psi^j_l0 = sqrt((2l+1)/(4 pi)) kappa_lambda(l / lambda^j), l < L (Sect. 2.2)."""
+    return np.array([math.sqrt((2 * l + 1) / (4 * math.pi)) * kappa_lambda(l / B ** j, B)
+                     for l in range(L)])
+
+
+def phi_l0(L, B, J0):
+    """Phi_l0 = sqrt((2l+1)/(4 pi)) eta_lambda(l / lambda^J0), l < L (Sect. 2.2)."""
+    return np.array([math.sqrt((2 * l + 1) / (4 * math.pi)) * eta_lambda(l / B ** J0, B)
+                     for l in range(L)])
+
+
+def bandlimits(L, B, J0, multires):
+    """Band-limits of the scaling map and of wavelet scales j = J0..J.
+
+    Multiresolution (Sect. 3.1): scale j lives at band-limit min(L, lambda^{j+1});
+    the scaling map at min(L, lambda^J0), because eta(l/lambda^J0) = 0 for
+    l >= lambda^J0.  Full resolution: every map at L.
+    """
+    J = check_params(L, B, J0)
+    if not multires:
+        return L, [L] * (J - J0 + 1)
+    return min(L, B ** J0), [min(L, B ** (j + 1)) for j in range(J0, J + 1)]

@@ -1,0 +1,101 @@
+"""ORACLE — test infrastructure only.
+
+Plain FP64 axisymmetric scale-discretised wavelet transform on MW samples:
+
+  analysis  (Eqs. wav2, wav4; multiresolution of Sect. 3.1):
+      f_lm = forward_L(f)
+      W^Phi_lm = sqrt(4 pi/(2l+1)) f_lm Phi*_l0,   map at the scaling band-limit
+      W^j_lm   = sqrt(4 pi/(2l+1)) f_lm Psi^j*_l0, map at scale j's band-limit
+  synthesis (Eq. waveletsynthesis):
+      f_lm = sqrt(4 pi/(2l+1)) [W^Phi_lm Phi_l0 + sum_j W^j_lm Psi^j_l0],
+      with W_lm = forward_N(W) of each map, then f = inverse_L(f_lm)
+  adjoint of the analysis: the conjugate transpose of each step in reverse
+      order (for real maps this is the transpose under the Euclidean inner
+      product of the stored samples).
+
+Maps are lists of arrays: f_wav[j - J0] has shape (N_j, 2 N_j - 1).
+"""
+import math
+
+import numpy as np
+
+from . import kernels, sht
+
+
+def _ell_index(N):
+    """l for every index l*l + l + m, l < N."""
+    return np.repeat(np.arange(N), 2 * np.arange(N) + 1)
+
+
+def _norm(N):
+    l = _ell_index(N)
+    return np.sqrt(4.0 * math.pi / (2.0 * l + 1.0))
+
+
+def tables(L, B, J0):
+    """(Phi_l0, [Psi^j_l0 for j = J0..J]) for l < L."""
+    J = kernels.check_params(L, B, J0)
+    phi = kernels.phi_l0(L, B, J0)
+    psi = [kernels.psi_l0(L, B, j) for j in range(J0, J + 1)]
+    return phi, psi
+
+
+def _expand(per_l, N):
+    return np.asarray(per_l)[_ell_index(N)]
+
+
+def analysis_lm(flm, L, B, J0, multires=True):
+    """Harmonic coefficients of the scaling map and wavelet maps, each truncated
+    at its band-limit (Eqs. wav2, wav4)."""
+    phi, psi = tables(L, B, J0)
+    n_scal, n_wav = kernels.bandlimits(L, B, J0, multires)
+    c = _norm(L) * flm[:L * L]
+    scal = (c * np.conj(_expand(phi, L)))[:n_scal * n_scal]
+    wav = [(c * np.conj(_expand(p, L)))[:n * n] for p, n in zip(psi, n_wav)]
+    return scal, wav
+
+
+def analysis(f, L, B, J0, multires=True, real=True):
+    flm = sht.forward(f, L)
+    scal_lm, wav_lm = analysis_lm(flm, L, B, J0, multires)
+    n_scal, n_wav = kernels.bandlimits(L, B, J0, multires)
+    f_scal = sht.inverse(scal_lm, n_scal, real=real)
+    f_wav = [sht.inverse(w, n, real=real) for w, n in zip(wav_lm, n_wav)]
+    return f_wav, f_scal
+
+
+def _pad(xlm, L):
+    out = np.zeros(L * L, dtype=complex)
+    out[:len(xlm)] = xlm
+    return out
+
+
+def synthesis_lm(scal_lm, wav_lm, L, B, J0):
+    """Eq. (waveletsynthesis) in harmonic space."""
+    phi, psi = tables(L, B, J0)
+    c = _norm(L)
+    flm = c * _pad(scal_lm, L) * _expand(phi, L)
+    for w, p in zip(wav_lm, psi):
+        flm = flm + c * _pad(w, L) * _expand(p, L)
+    return flm
+
+
+def synthesis(f_wav, f_scal, L, B, J0, multires=True, real=True):
+    n_scal, n_wav = kernels.bandlimits(L, B, J0, multires)
+    scal_lm = sht.forward(f_scal, n_scal)
+    wav_lm = [sht.forward(w, n) for w, n in zip(f_wav, n_wav)]
+    flm = synthesis_lm(scal_lm, wav_lm, L, B, J0)
+    return sht.inverse(flm, L, real=real)
+
+
+def analysis_adjoint(g_wav, g_scal, L, B, J0, multires=True, real=True):
+    """Conjugate transpose of analysis(): sum over maps of
+    forward_L^H diag(conj(c)) inverse_N^H, with c the kernel factor of each map."""
+    phi, psi = tables(L, B, J0)
+    n_scal, n_wav = kernels.bandlimits(L, B, J0, multires)
+    c = _norm(L)
+    ylm = np.conj(c * np.conj(_expand(phi, L))) * _pad(sht.inverse_adjoint(g_scal, n_scal), L)
+    for g, p, n in zip(g_wav, psi, n_wav):
+        ylm = ylm + np.conj(c * np.conj(_expand(p, L))) * _pad(sht.inverse_adjoint(g, n), L)
+    out = sht.forward_adjoint(ylm, L)
+    return out.real.copy() if real else out

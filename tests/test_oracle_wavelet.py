@@ -1,0 +1,125 @@
+"""Pins for the oracle's wavelet analysis, synthesis and analysis-adjoint
+(Eqs. wav2, wav4, waveletsynthesis; multiresolution of Sect. 3.1)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import kernels, sht, wavelet
+from paper_1211_1680_gb300 import inputs
+
+CASES = [  # (L, B, J0, multires, real)
+    (32, 2, 0, False, True),    # the L=32 full-resolution workload
+    (32, 2, 0, True, True),
+    (40, 3, 1, True, False),
+    (27, 3, 2, False, False),
+    (64, 2, 2, True, True),
+]
+
+
+@pytest.mark.parametrize("L,B,J0,multires,real", CASES)
+def test_exact_reconstruction(L, B, J0, multires, real):
+    """Synthesis after analysis returns the band-limited map (Eq. identity)."""
+    f = sht.inverse(inputs.random_flm(L, 7, real=real), L, real=real)
+    fw, fs = wavelet.analysis(f, L, B, J0, multires, real)
+    n_scal, n_wav = kernels.bandlimits(L, B, J0, multires)
+    assert fs.shape == (n_scal, 2 * n_scal - 1)
+    assert [w.shape for w in fw] == [(n, 2 * n - 1) for n in n_wav]
+    fr = wavelet.synthesis(fw, fs, L, B, J0, multires, real)
+    assert np.max(np.abs(fr - f)) / np.max(np.abs(f)) < 1e-13
+
+
+@pytest.mark.parametrize("ell", [0, 3, 7, 12, 20])
+def test_axisymmetric_input(ell):
+    """f = Y_l0: Eq. (wav2) gives W^j = sqrt(4 pi/(2l+1)) Psi^j_l0 Y_l0, i.e.
+    kappa(l/lambda^j) Y_l0, at every scale's band-limit."""
+    L, B, J0 = 24, 2, 1
+    flm = np.zeros(L * L, complex)
+    flm[ell * ell + ell] = 1.0
+    f = sht.inverse(flm, L, real=True)
+    fw, fs = wavelet.analysis(f, L, B, J0, True, True)
+    n_scal, n_wav = kernels.bandlimits(L, B, J0, True)
+    for j, (w, n) in enumerate(zip(fw, n_wav), start=J0):
+        ref = np.zeros(n * n, complex)
+        if ell < n:
+            ref[ell * ell + ell] = kernels.kappa_lambda(ell / B ** j, B)
+        assert np.max(np.abs(w - sht.inverse(ref, n, real=True))) < 1e-13
+    ref = np.zeros(n_scal * n_scal, complex)
+    if ell < n_scal:
+        ref[ell * ell + ell] = kernels.eta_lambda(ell / B ** J0, B)
+    assert np.max(np.abs(fs - sht.inverse(ref, n_scal, real=True))) < 1e-13
+
+
+def test_multires_matches_full_resolution():
+    """Sect. 3.1: the multiresolution maps hold the same information as the
+    full-resolution ones: their harmonic coefficients agree and the
+    full-resolution maps have none above the scale band-limit."""
+    L, B, J0 = 48, 2, 1
+    f = sht.inverse(inputs.random_flm(L, 11, real=True), L, real=True)
+    fw_m, fs_m = wavelet.analysis(f, L, B, J0, True, True)
+    fw_f, fs_f = wavelet.analysis(f, L, B, J0, False, True)
+    n_scal, n_wav = kernels.bandlimits(L, B, J0, True)
+    pairs = list(zip(fw_m, fw_f, n_wav)) + [(fs_m, fs_f, n_scal)]
+    for wm, wf, n in pairs:
+        lm_m = sht.forward(wm, n)
+        lm_f = sht.forward(wf, L)
+        assert np.max(np.abs(lm_f[:n * n] - lm_m)) < 1e-13
+        assert np.max(np.abs(lm_f[n * n:])) < 1e-13 if n < L else True
+
+
+@pytest.mark.parametrize("L,B,J0,multires,real", CASES[1:] + [(16, 2, 1, False, True)])
+def test_adjoint_dot_product(L, B, J0, multires, real):
+    """<A x, y> = <x, A^T y> on random (not band-limited) arrays."""
+    x = inputs.random_map((L, 2 * L - 1), 31, real=real)
+    fw, fs = wavelet.analysis(x, L, B, J0, multires, real)
+    gw = [inputs.random_map(w.shape, 40 + i, real=real) for i, w in enumerate(fw)]
+    gs = inputs.random_map(fs.shape, 39, real=real)
+    lhs = sum(np.vdot(g, w) for g, w in zip(gw, fw)) + np.vdot(gs, fs)
+    rhs = np.vdot(wavelet.analysis_adjoint(gw, gs, L, B, J0, multires, real), x)
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_adjoint_dense_transpose():
+    """At L = 4 build the analysis matrix and the adjoint matrix column by
+    column; the second is the transpose of the first."""
+    L, B, J0 = 4, 2, 0
+    for multires in (True, False):
+        n_in = L * (2 * L - 1)
+        cols = []
+        for k in range(n_in):
+            e = np.zeros(n_in)
+            e[k] = 1.0
+            fw, fs = wavelet.analysis(e.reshape(L, 2 * L - 1), L, B, J0, multires, True)
+            cols.append(np.concatenate([fs.ravel()] + [w.ravel() for w in fw]))
+        A = np.array(cols).T
+        shapes = [fs.shape] + [w.shape for w in fw]
+        sizes = [a * b for a, b in shapes]
+        rows = []
+        for k in range(A.shape[0]):
+            e = np.zeros(A.shape[0])
+            e[k] = 1.0
+            parts = np.split(e, np.cumsum(sizes)[:-1])
+            gs = parts[0].reshape(shapes[0])
+            gw = [p.reshape(s) for p, s in zip(parts[1:], shapes[1:])]
+            rows.append(wavelet.analysis_adjoint(gw, gs, L, B, J0, multires, True).ravel())
+        At = np.array(rows).T
+        assert np.max(np.abs(At - A.T)) < 1e-14
+
+
+def test_white_noise_variance():
+    """Wavelet-space noise (Sect. 4.2): for white harmonic noise of variance
+    sigma^2, E|W^j|^2 = sigma^2 sum_l |Psi^j_l0|^2 at every sample.  Averaged over
+    the samples of several realisations it must agree to a few per cent."""
+    L, B, J0 = 64, 2, 2
+    phi, psi = wavelet.tables(L, B, J0)
+    n_scal, n_wav = kernels.bandlimits(L, B, J0, True)
+    acc = [0.0] * len(psi)
+    reps = 6
+    for r in range(reps):
+        flm = inputs.random_flm(L, 500 + r, real=False)
+        scal_lm, wav_lm = wavelet.analysis_lm(flm, L, B, J0, True)
+        for i, (w, n) in enumerate(zip(wav_lm, n_wav)):
+            acc[i] += np.mean(np.abs(sht.inverse(w, n)) ** 2) / reps
+    for i, p in enumerate(psi):
+        if n_wav[i] >= 16:
+            assert acc[i] == pytest.approx(np.sum(p ** 2), rel=0.08)
