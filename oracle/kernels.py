@@ -54,9 +54,17 @@ def k_lambda(t, lam):
 
 def kappa_lambda(t, lam):
     """Wavelet generating function kappa_lambda(t) = sqrt(k(t/lambda) - k(t)) (Sect. 2.2).
-    A difference that rounds below zero is taken as zero."""
-    d = k_lambda(t / lam, lam) - k_lambda(t, lam)
-    return math.sqrt(d) if d > 0.0 else 0.0
+
+    By Eq. (smoothscaling) the difference of the two ratios is the integral of
+    s_lambda^2(t')/t' over [t/lambda, t] (clipped to the support [1/lambda, 1])
+    divided by the same denominator; it is evaluated in that form, so that no
+    cancellation occurs where both k values are close to 1."""
+    lam = float(lam)
+    lo = max(t / lam, 1.0 / lam)
+    hi = min(t, 1.0)
+    if hi <= lo:
+        return 0.0
+    return math.sqrt(_integral(lo, hi, lam) / _denominator(lam))
 
 
 def eta_lambda(t, lam):

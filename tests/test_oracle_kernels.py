@@ -94,3 +94,28 @@ def test_bandlimits():
     assert kernels.bandlimits(2048, 3, 1, True) == (3, [9, 27, 81, 243, 729, 2048, 2048])
     with pytest.raises(ValueError):
         kernels.bandlimits(32, 2, 5, True)   # J0 must be < J = 5
+
+
+def test_kappa_relative_accuracy_near_support_edges():
+    """kappa(t) where k(t/lambda) and k(t) are both within 1e-16 of 1 (t just
+    above 1/lambda), and elsewhere, against mpmath at 40 digits (kappa =
+    8.8e-9 at t = 65/128, lambda = 2; computed as a difference of two ratios
+    it would round to 0)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    for lam in (2, 3):
+        def s_mp(x):
+            return mpmath.e ** (-1 / (1 - x * x)) if -1 < x < 1 else mpmath.mpf(0)
+
+        def f(u):
+            x = 2 * mpmath.mpf(lam) / (lam - 1) * (u - mpmath.mpf(1) / lam) - 1
+            return s_mp(x) ** 2 / u
+        den = mpmath.quad(f, [mpmath.mpf(1) / lam, 1])
+        for t in (1.0 / lam + 0.004, 65.0 / 128 if lam == 2 else 0.34, 1.0 / lam + 0.05, 0.9, 0.99,
+                  1.3, lam * 0.99):
+            lo, hi = max(t / lam, 1.0 / lam), min(t, 1.0)
+            ref = float(mpmath.sqrt(mpmath.quad(f, [lo, hi]) / den))
+            got = kernels.kappa_lambda(t, lam)
+            assert got > 0.0
+            # absolute accuracy at the FP64 level everywhere, relative where kappa > 1e-12
+            assert abs(got - ref) < 2e-16 + (1e-11 * ref if ref > 1e-12 else 0.0)
