@@ -1,0 +1,124 @@
+/*
+ * s2let_gpu.h — C ABI of a GB300 (sm_103a) library for the axisymmetric
+ * scale-discretised wavelet transform on the sphere with McEwen-Wiaux (MW)
+ * equiangular sampling (Leistedt, McEwen, Vandergheynst & Wiaux, "S2LET: A
+ * code to perform fast wavelet analysis on the sphere", A&A 2013).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Sampling (Sect. 2.1, MW sampling theorem): a map of band-limit N has N
+ *   rings theta_t = pi (2t+1)/(2N-1), t = 0..N-1 (t = N-1 is the south pole),
+ *   and P = 2N-1 longitudes phi_p = 2 pi p / P.  It is stored row-major as
+ *   N x P samples; the pole ring is stored in full (P copies).
+ * Batches: every buffer holds `batch` maps (or coefficient sets) back to back.
+ * Element type: FP64 plans use double, other plans float.  Real maps hold one
+ *   value per sample; complex maps (S2LET_COMPLEX) hold interleaved (re, im).
+ * Harmonic coefficients (s2let_sht_*): complex interleaved, index l*l + l + m,
+ *   l < L, |m| <= l, L*L per map.  Real plans return the m < 0 half from the
+ *   symmetry f_{l,-m} = (-1)^m conj(f_lm) and read only m >= 0.
+ * Wavelet maps: `f_wav` is the concatenation over scales j = J_min..J of one
+ *   block per scale, each block `batch` maps at that scale's band-limit N_j
+ *   (s2let_wav_layout gives offsets); `f_scal` holds `batch` scaling maps.
+ *   Multiresolution (S2LET_MULTIRES, Sect. 3.1): N_j = min(L, B^(j+1)) and the
+ *   scaling band-limit is min(L, B^J_min); otherwise every map is at L.
+ * Memory: every data pointer is a DEVICE pointer owned by the caller; the
+ *   library never frees it.  The plan owns its tables and its workspace, which
+ *   are allocated in s2let_plan_create; transform calls allocate nothing.
+ * Streams: calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *   default stream).  Calls on one plan share its workspace and must not run
+ *   concurrently; distinct plans are independent.
+ * Errors: every function returns an int status.  Argument errors are detected
+ *   on the host before anything is launched.  Launch failures return
+ *   S2LET_ERR_CUDA.  The library never traps, asserts or exits on the device.
+ */
+#ifndef S2LET_GPU_H
+#define S2LET_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define S2LET_OK 0
+#define S2LET_ERR_ARG (-1)         /* invalid argument (size, flag, pointer)      */
+#define S2LET_ERR_ALLOC (-2)       /* device or host allocation failed            */
+#define S2LET_ERR_CUDA (-3)        /* a CUDA runtime call or kernel launch failed */
+#define S2LET_ERR_TIMEOUT (-4)     /* a bounded device-side wait gave up          */
+#define S2LET_ERR_UNSUPPORTED (-5) /* valid request this build does not support   */
+
+/* plan flags (bitwise or) */
+#define S2LET_REAL 0x0           /* real maps (default)                        */
+#define S2LET_COMPLEX 0x1        /* complex maps                               */
+#define S2LET_MULTIRES 0x2       /* multiresolution band-limits, Sect. 3.1     */
+#define S2LET_PREC_FP64 0x00     /* every stage in FP64                        */
+#define S2LET_PREC_FP32 0x10     /* FP32 storage and Legendre sums, float-float
+                                    recurrence, FP64 seeds and theta quadrature */
+#define S2LET_PREC_MASK 0xf0
+#define S2LET_QUAD_FP32 0x100    /* FP32 plans only: run the theta quadrature in
+                                    FP32 instead of FP64                       */
+
+typedef struct s2let_plan s2let_plan;
+
+/* J = ceil(log_B(L-1)), the largest wavelet scale (Sect. 2.2), computed in
+ * integers as the smallest J >= 0 with B^J >= L-1.  Returns J, or
+ * S2LET_ERR_ARG if L < 2 or B < 2. */
+int s2let_jmax(int L, int B);
+
+/* Create a plan for `batch` maps of band-limit L with dilation B (the paper's
+ * lambda, an integer >= 2 here) and lowest wavelet scale J_min, 0 <= J_min < J
+ * (Sect. 2.2).  Builds the kernel tables Phi_l0, Psi^j_l0 (Sect. 2.2), the
+ * Legendre seeds and the FFT tables on the current device and allocates the
+ * workspace.  Limits: 3 <= L <= 2048, 1 <= batch.  On error *plan is NULL. */
+int s2let_plan_create(s2let_plan **plan, int L, int B, int J_min, int flags, int batch);
+
+/* Free a plan and everything it owns (NULL is accepted). */
+int s2let_plan_destroy(s2let_plan *plan);
+
+/* Plan geometry: J, the number of wavelet scales J-J_min+1, the element
+ * count of f_wav and f_scal (per batch, in real numbers: complex maps count
+ * 2 per sample) and the band-limit of the scaling map.  Any output pointer
+ * may be NULL. */
+int s2let_plan_info(const s2let_plan *plan, int *J, int *n_scales, int64_t *wav_elems,
+                    int64_t *scal_elems, int *N_scal);
+
+/* Layout of scale j (J_min <= j <= J) inside f_wav: its band-limit N_j, the
+ * offset of its block and the block size, both in real numbers (elements of
+ * the plan's type).  j = -1 describes f_scal (offset 0). */
+int s2let_wav_layout(const s2let_plan *plan, int j, int *N_j, int64_t *offset, int64_t *elems);
+
+/* Wavelet analysis (Eqs. wav2 and wav4, Sect. 2.2; multiresolution of
+ * Sect. 3.1): forward MW transform of each map f at L, products with
+ * Psi^j_l0 and Phi_l0 in harmonic space, inverse transform of each scale at
+ * its band-limit.  In: f (batch maps at L).  Out: f_wav, f_scal. */
+int s2let_analysis(s2let_plan *plan, const void *f, void *f_wav, void *f_scal, void *stream);
+
+/* Wavelet synthesis (Eq. waveletsynthesis, Sect. 2.2): forward transform of
+ * every wavelet and scaling map at its band-limit, harmonic-space sum with
+ * Psi^j_l0 and Phi_l0, inverse transform at L.  In: f_wav, f_scal.  Out: f.
+ * Exact inverse of s2let_analysis for band-limited maps (Eq. identity). */
+int s2let_synthesis(s2let_plan *plan, const void *f_wav, const void *f_scal, void *f, void *stream);
+
+/* Adjoint of s2let_analysis: the transpose of the analysis operator under the
+ * Euclidean inner product of the stored samples (pole copies counted), i.e.
+ * the conjugate transpose for complex maps.  The paper does not state it; it
+ * is the transpose of Eqs. wav2/wav4 and of each transform step.  Used for
+ * gradients.  In: g_wav, g_scal (shaped like f_wav, f_scal).  Out: g_f. */
+int s2let_adjoint(s2let_plan *plan, const void *g_wav, const void *g_scal, void *g_f, void *stream);
+
+/* Forward MW spherical harmonic transform at L (Eq. harmonicsanalysis made a
+ * finite sum by the sampling theorem of Sect. 2.1).  In: f.  Out: flm. */
+int s2let_sht_forward(s2let_plan *plan, const void *f, void *flm, void *stream);
+
+/* Inverse MW spherical harmonic transform at L (Eq. harmonicssynthesis,
+ * Sect. 2.1).  In: flm.  Out: f. */
+int s2let_sht_inverse(s2let_plan *plan, const void *flm, void *f, void *stream);
+
+/* Short text for a status code. */
+const char *s2let_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* S2LET_GPU_H */

@@ -1,0 +1,309 @@
+// Ring DFTs (length P = 2N-1, any N) and the MW theta-quadrature, built on
+// one shared-memory power-of-two FFT and Bluestein's chirp-z identity
+// (Bluestein 1970):  nk = (n^2 + k^2 - (k-n)^2)/2, so a length-P DFT is a
+// circular convolution of length M >= 2P-1 with the chirp c_n = e^{i pi n^2/P}.
+//
+// Tables per band-limit N (all precomputed on the host in FP64):
+//   chirp[n]  = e^{i pi n^2 / P},               n < P
+//   bhat[k]   = FFT_M(b), b_j = chirp_|j| for |j| < P (indices mod M)
+//   what[k]   = FFT_M(v), v_s = w(s) = int_0^pi e^{i s theta} sin theta dtheta, |s| <= 2N-2
+//   tw[k]     = e^{-2 pi i k / M},              k < M/2
+//   phase[k+N-1] = e^{i pi k / P},              |k| <= N-1
+// M = next power of two >= max(4N-3, 2) serves both the Bluestein DFTs and
+// the w-convolution (|a+b| <= 2N-2 for |a|, |b| <= N-1 needs M >= 4N-3).
+#pragma once
+#include "common.cuh"
+
+namespace s2g {
+
+template <typename C> struct FftTab {
+    const C *chirp;
+    const C *bhat;
+    const C *what;
+    const C *tw;
+    const C *phase;
+    int N, P, M, logM;
+};
+
+// In-place radix-2 decimation-in-time FFT of length M in shared memory.
+// INV = false: sum_j a_j e^{-2 pi i jk/M}; INV = true: e^{+...}; unnormalised.
+template <typename C, bool INV>
+__device__ void smem_fft(C *a, int M, int logM, const C *__restrict__ tw)
+{
+    if (logM > 0) {
+        for (int i = threadIdx.x; i < M; i += blockDim.x) {
+            int j = (int)(__brev((unsigned)i) >> (32 - logM));
+            if (i < j) {
+                C t = a[i];
+                a[i] = a[j];
+                a[j] = t;
+            }
+        }
+    }
+    __syncthreads();
+    for (int s = 1; s <= logM; ++s) {
+        const int half = 1 << (s - 1);
+        const int stride = M >> s;
+        for (int j = threadIdx.x; j < (M >> 1); j += blockDim.x) {
+            const int k = j & (half - 1);
+            const int i1 = ((j >> (s - 1)) << s) + k;
+            const int i2 = i1 + half;
+            C w = tw[k * stride];
+            if (INV) w.y = -w.y;
+            C u = a[i1];
+            C v = cmul(w, a[i2]);
+            a[i1] = cadd(u, v);
+            a[i2] = csub(u, v);
+        }
+        __syncthreads();
+    }
+}
+
+// buf := IFFT_M( FFT_M(buf) * K ), K = khat or conj(khat); unnormalised.
+template <typename C, bool CONJ_K>
+__device__ void conv_core(C *buf, const FftTab<C> &T, const C *__restrict__ khat)
+{
+    smem_fft<C, false>(buf, T.M, T.logM, T.tw);
+    for (int i = threadIdx.x; i < T.M; i += blockDim.x) {
+        C k = khat[i];
+        buf[i] = CONJ_K ? cmulc(buf[i], k) : cmul(buf[i], k);
+    }
+    __syncthreads();
+    smem_fft<C, true>(buf, T.M, T.logM, T.tw);
+}
+
+template <typename R> __device__ __forceinline__ R inv_m(int M) { return (R)1 / (R)M; }
+
+// ---------------------------------------------------------------- S1: ring DFT
+// F_m(theta_t) = scale * sum_p f(theta_t, phi_p) e^{-i m phi_p}, phi_p = 2 pi p / P.
+// Real maps: two rings per block packed as one complex sequence, m = 0..N-1,
+// written to F[b][m][t].  Complex maps: one ring per block, m = -(N-1)..N-1,
+// written to F[b][m + N - 1][t].
+template <typename R>
+__global__ void k_ring_fwd_real(const R *__restrict__ f, cplx_t<R> *__restrict__ F, R scale,
+                                FftTab<cplx_t<R>> T)
+{
+    using C = cplx_t<R>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    const int N = T.N, P = T.P, M = T.M;
+    const int b = blockIdx.y;
+    const int t0 = 2 * blockIdx.x, t1 = t0 + 1;
+    const bool has1 = t1 < N;
+    const R *r0 = f + ((size_t)b * N + t0) * P;
+    const R *r1 = f + ((size_t)b * N + (has1 ? t1 : t0)) * P;
+    for (int n = threadIdx.x; n < M; n += blockDim.x) {
+        C v = mk((R)0, (R)0);
+        if (n < P) v = cmulc(mk(r0[n], has1 ? r1[n] : (R)0), T.chirp[n]);
+        buf[n] = v;
+    }
+    __syncthreads();
+    conv_core<C, false>(buf, T, T.bhat);
+    const R s = scale * inv_m<R>(M) * (R)0.5;
+    C *out = F + (size_t)b * N * N;
+    for (int m = threadIdx.x; m < N; m += blockDim.x) {
+        const int mp = (m == 0) ? 0 : P - m;
+        C zk = cmulc(buf[m], T.chirp[m]);    // conj(c_k) * buf[k]
+        C zp = cmulc(buf[mp], T.chirp[mp]);
+        // X0 = (Zk + conj(Zp)) / 2, X1 = (Zk - conj(Zp)) / (2i)
+        C x0 = mk((zk.x + zp.x) * s, (zk.y - zp.y) * s);
+        out[(size_t)m * N + t0] = x0;
+        if (has1) {
+            C x1 = mk((zk.y + zp.y) * s, (zp.x - zk.x) * s);
+            out[(size_t)m * N + t1] = x1;
+        }
+    }
+}
+
+template <typename R>
+__global__ void k_ring_fwd_cplx(const cplx_t<R> *__restrict__ f, cplx_t<R> *__restrict__ F, R scale,
+                                FftTab<cplx_t<R>> T)
+{
+    using C = cplx_t<R>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    const int N = T.N, P = T.P, M = T.M;
+    const int b = blockIdx.y, t = blockIdx.x;
+    const C *row = f + ((size_t)b * N + t) * P;
+    for (int n = threadIdx.x; n < M; n += blockDim.x)
+        buf[n] = (n < P) ? cmulc(row[n], T.chirp[n]) : mk((R)0, (R)0);
+    __syncthreads();
+    conv_core<C, false>(buf, T, T.bhat);
+    const R s = scale * inv_m<R>(M);
+    const int nm = 2 * N - 1;
+    C *out = F + (size_t)b * nm * N;
+    for (int mi = threadIdx.x; mi < nm; mi += blockDim.x) {
+        const int m = mi - (N - 1);
+        const int k = m >= 0 ? m : m + P;
+        out[(size_t)mi * N + t] = cscale(cmulc(buf[k], T.chirp[k]), s);
+    }
+}
+
+// ---------------------------------------------------------------- S6: inverse ring DFT
+// f(theta_t, phi_p) = scale * sum_m F_m(theta_t) e^{i m phi_p}.  Real maps use
+// F_{-m} = conj(F_m) and pack two rings per block.
+template <typename R>
+__global__ void k_ring_inv_real(const cplx_t<R> *__restrict__ F, R *__restrict__ f, R scale,
+                                FftTab<cplx_t<R>> T)
+{
+    using C = cplx_t<R>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    const int N = T.N, P = T.P, M = T.M;
+    const int b = blockIdx.y;
+    const int t0 = 2 * blockIdx.x, t1 = t0 + 1;
+    const bool has1 = t1 < N;
+    const C *in = F + (size_t)b * N * N;
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+        C v = mk((R)0, (R)0);
+        if (k < P) {
+            const bool neg = k >= N;
+            const int m = neg ? P - k : k;
+            C a = in[(size_t)m * N + t0];
+            C c = has1 ? in[(size_t)m * N + t1] : mk((R)0, (R)0);
+            if (neg) {
+                a = cconj(a);
+                c = cconj(c);
+            }
+            C z = mk(a.x - c.y, a.y + c.x);   // a + i c
+            v = cmul(z, T.chirp[k]);
+        }
+        buf[k] = v;
+    }
+    __syncthreads();
+    conv_core<C, true>(buf, T, T.bhat);
+    const R s = scale * inv_m<R>(M);
+    R *o0 = f + ((size_t)b * N + t0) * P;
+    R *o1 = f + ((size_t)b * N + t1) * P;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        C v = cmul(buf[p], T.chirp[p]);
+        o0[p] = v.x * s;
+        if (has1) o1[p] = v.y * s;
+    }
+}
+
+template <typename R>
+__global__ void k_ring_inv_cplx(const cplx_t<R> *__restrict__ F, cplx_t<R> *__restrict__ f, R scale,
+                                FftTab<cplx_t<R>> T)
+{
+    using C = cplx_t<R>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    const int N = T.N, P = T.P, M = T.M;
+    const int b = blockIdx.y, t = blockIdx.x;
+    const int nm = 2 * N - 1;
+    const C *in = F + (size_t)b * nm * N;
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+        C v = mk((R)0, (R)0);
+        if (k < P) {
+            const int m = k < N ? k : k - P;
+            v = cmul(in[(size_t)(m + N - 1) * N + t], T.chirp[k]);
+        }
+        buf[k] = v;
+    }
+    __syncthreads();
+    conv_core<C, true>(buf, T, T.bhat);
+    const R s = scale * inv_m<R>(M);
+    C *o = f + ((size_t)b * N + t) * P;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) o[p] = cscale(cmul(buf[p], T.chirp[p]), s);
+}
+
+// ---------------------------------------------------------------- S2: theta quadrature
+// For one order m and one map: x_t = F_m(theta_t), t < N, parity sigma = (-1)^m.
+//  (a) extend to the circle: x~_t = x_t (t < N), x~_t = sigma x_{P-1-t} (N <= t < P)
+//  (b) X_a = (1/P) sum_t x~_t e^{-i a theta_t},  theta_t = pi (2t+1)/P, |a| <= N-1
+//  (c) H_b = sum_a X_a w(a+b),                    |b| <= N-1
+//  (d) h_t = sum_b H_b e^{-i b theta_t},          t < P
+//  (e) G_t = qscale (h_t + sigma h_{P-1-t}) for t < N-1, G_{N-1} = qscale h_{N-1}
+// e^{-i a theta_t} = e^{-i pi a/P} e^{-2 pi i a t/P}: (b) and (d) are length-P
+// DFTs (Bluestein) with a phase; (c) is a circular convolution of length M.
+// The linear map x -> G is real and symmetric, so the same kernel also applies
+// its transpose.  Q is the compute type (FP64 by default), R the storage type.
+template <typename Q, typename R, int VPT>
+__global__ void k_theta_quad(const cplx_t<R> *__restrict__ Fin, cplx_t<R> *__restrict__ Gout,
+                             int nmi, int m_offset, Q qscale, FftTab<cplx_t<Q>> T)
+{
+    using C = cplx_t<Q>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    const int N = T.N, P = T.P, M = T.M;
+    const int mi = blockIdx.x, b = blockIdx.y;
+    const int m = mi - m_offset;
+    const Q sigma = (m & 1) ? (Q)-1 : (Q)1;
+    const cplx_t<R> *x = Fin + ((size_t)b * nmi + mi) * N;
+    cplx_t<R> *g = Gout + ((size_t)b * nmi + mi) * N;
+    const Q invM = (Q)1 / (Q)M;
+
+    // (a) + pre-chirp of (b)
+    for (int n = threadIdx.x; n < M; n += blockDim.x) {
+        C v = mk((Q)0, (Q)0);
+        if (n < N) {
+            v = ccast<C>(x[n]);
+        } else if (n < P) {
+            v = cscale(ccast<C>(x[P - 1 - n]), sigma);
+        }
+        if (n < P) v = cmulc(v, T.chirp[n]);
+        buf[n] = v;
+    }
+    __syncthreads();
+    conv_core<C, false>(buf, T, T.bhat);
+    // (b) Y_k = conj(c_k) buf_k / M;  X_a = (1/P) e^{-i pi a/P} Y_{a mod P}
+    // (c) input U_k = X_{-k} = (1/P) e^{i pi k/P} Y_{(-k) mod P} at k mod M, |k| <= N-1
+    C hold[VPT];
+    {
+        const Q s = invM / (Q)P;
+        int r = 0;
+        for (int j = threadIdx.x; j < M; j += blockDim.x, ++r) {
+            int k;
+            bool ok = true;
+            if (j <= N - 1) k = j;
+            else if (j >= M - (N - 1)) k = j - M;
+            else { k = 0; ok = false; }
+            C v = mk((Q)0, (Q)0);
+            if (ok) {
+                int src = (-k) % P;
+                if (src < 0) src += P;
+                v = cmul(cmulc(buf[src], T.chirp[src]), T.phase[k + N - 1]);
+                v = cscale(v, s);
+            }
+            hold[r] = v;
+        }
+        __syncthreads();
+        r = 0;
+        for (int j = threadIdx.x; j < M; j += blockDim.x, ++r) buf[j] = hold[r];
+        __syncthreads();
+    }
+    conv_core<C, false>(buf, T, T.what);
+    // H_b = buf[b mod M] / M;  (d) pre-chirp: z_n = H_b e^{-i pi b/P} conj(c_n), n = b mod P
+    {
+        int r = 0;
+        for (int n = threadIdx.x; n < M; n += blockDim.x, ++r) {
+            C v = mk((Q)0, (Q)0);
+            if (n < P) {
+                const int bb = (n <= N - 1) ? n : n - P;
+                const int src = bb >= 0 ? bb : bb + M;
+                v = cmulc(cscale(buf[src], invM), T.phase[bb + N - 1]);   // H_b e^{-i pi b/P}
+                v = cmulc(v, T.chirp[n]);
+            }
+            hold[r] = v;
+        }
+        __syncthreads();
+        r = 0;
+        for (int n = threadIdx.x; n < M; n += blockDim.x, ++r) buf[n] = hold[r];
+        __syncthreads();
+    }
+    conv_core<C, false>(buf, T, T.bhat);
+    // h_t = conj(c_t) buf_t / M; (e) fold
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        C h = cscale(cmulc(buf[t], T.chirp[t]), invM);
+        if (t < N - 1) {
+            const int u = P - 1 - t;
+            C h2 = cscale(cmulc(buf[u], T.chirp[u]), invM);
+            h = cadd(h, cscale(h2, sigma));
+        }
+        h = cscale(h, qscale);
+        g[t] = ccast<cplx_t<R>>(h);
+    }
+}
+
+}  // namespace s2g

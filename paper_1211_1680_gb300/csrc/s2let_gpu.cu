@@ -1,0 +1,663 @@
+// Plan, dispatch and C ABI of the S2LET GPU library (see include/s2let_gpu.h).
+//
+// Data path of one forward transform at band-limit N (batch B):
+//   S1 ring DFT      f[b][t][p]      -> F[b][m][t]     (fft.cuh)
+//   S2 quadrature    F[b][m][t]      -> G[b][m][t]     (fft.cuh, FP64 by default)
+//   S3 Legendre sum  G[b][m][t]      -> flm[b][m][l]   (legendre.cuh)
+// and of one inverse transform:
+//   S5 Legendre sum  flm[b][m][l]    -> F[b][m][t]
+//   S6 ring DFT      F[b][m][t]      -> f[b][t][p]
+// The kernel products of Eqs. wav2/wav4/waveletsynthesis are applied inside
+// S3 (epilogue, with accumulation over scales) and S5 (coefficient staging).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/s2let_gpu.h"
+#include "fft.cuh"
+#include "host_tables.h"
+#include "legendre.cuh"
+
+using namespace s2g;
+
+namespace {
+
+constexpr int kMaxL = 2048;
+
+int fft_threads(int M) { return std::max(32, std::min(1024, M / 16)); }
+
+template <typename T> T *dev_upload(const std::vector<T> &h, std::vector<void *> &owned, int &err)
+{
+    if (h.empty()) return nullptr;
+    void *p = nullptr;
+    if (cudaMalloc(&p, h.size() * sizeof(T)) != cudaSuccess) {
+        err = S2LET_ERR_ALLOC;
+        return nullptr;
+    }
+    owned.push_back(p);
+    if (cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) err = S2LET_ERR_CUDA;
+    return static_cast<T *>(p);
+}
+
+template <typename C> std::vector<C> to_c(const std::vector<s2h::cd> &v)
+{
+    std::vector<C> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+        o[i].x = v[i].real();
+        o[i].y = v[i].imag();
+    }
+    return o;
+}
+
+// Device tables for one band-limit.
+struct BandDev {
+    int N = 0, P = 0, M = 0, logM = 0;
+    FftTab<double2> fd{};
+    FftTab<float2> ff{};
+    int *ls = nullptr;
+    double2 *seed = nullptr;
+    RingD *ringd = nullptr;
+    RingF *ringf = nullptr;
+};
+
+}  // namespace
+
+struct s2let_plan {
+    int L = 0, B = 0, J0 = 0, J = 0, flags = 0, batch = 0;
+    bool cplx = false, multires = false, fp64 = true, quad64 = true;
+    int n_scal = 0;
+    std::vector<int> n_wav;                 // band-limit of scale J0 + i
+    std::vector<int64_t> wav_off;           // element offsets in f_wav
+    int64_t wav_elems = 0, scal_elems = 0;
+    std::map<int, BandDev> bands;
+    double2 *coefd = nullptr;               // [m][l] (a, a b), FP64
+    float4 *coeff = nullptr;                // [m][l] float-float
+    std::vector<void *> kfac;               // per map: scaling first, then scales J0..J (R[L])
+    void *F = nullptr, *flm = nullptr;      // workspace
+    std::vector<void *> owned;
+    ~s2let_plan()
+    {
+        for (void *p : owned) cudaFree(p);
+    }
+};
+
+namespace {
+
+int elem_size(const s2let_plan *p) { return p->fp64 ? 8 : 4; }
+int nmi(const s2let_plan *p, int N) { return p->cplx ? 2 * N - 1 : N; }
+int64_t map_elems(const s2let_plan *p, int N) { return (int64_t)N * (2 * N - 1) * (p->cplx ? 2 : 1); }
+
+#define S2_LAUNCH_CHECK()                                      \
+    do {                                                       \
+        if (cudaGetLastError() != cudaSuccess) return S2LET_ERR_CUDA; \
+    } while (0)
+
+template <typename R> const FftTab<cplx_t<R>> &fft_tab(const BandDev &b);
+template <> const FftTab<double2> &fft_tab<double>(const BandDev &b) { return b.fd; }
+template <> const FftTab<float2> &fft_tab<float>(const BandDev &b) { return b.ff; }
+
+template <typename R> LegTab<R> leg_tab(const s2let_plan *p, const BandDev &b);
+template <> LegTab<double> leg_tab<double>(const s2let_plan *p, const BandDev &b)
+{
+    LegTab<double> t;
+    t.ls = b.ls;
+    t.seed = b.seed;
+    t.ring = b.ringd;
+    t.coef = p->coefd;
+    t.ldc = p->L;
+    return t;
+}
+template <> LegTab<float> leg_tab<float>(const s2let_plan *p, const BandDev &b)
+{
+    LegTab<float> t;
+    t.ls = b.ls;
+    t.seed = b.seed;
+    t.ring = b.ringf;
+    t.coef = p->coeff;
+    t.ldc = p->L;
+    return t;
+}
+
+// ------------------------------------------------------------ stage launchers
+template <typename R>
+int run_ring_fwd(const s2let_plan *p, const BandDev &bd, const void *f, void *F, double scale, cudaStream_t st)
+{
+    const auto &T = fft_tab<R>(bd);
+    const size_t sm = (size_t)bd.M * sizeof(cplx_t<R>);
+    const int th = fft_threads(bd.M);
+    if (p->cplx) {
+        k_ring_fwd_cplx<R><<<dim3(bd.N, p->batch), th, sm, st>>>((const cplx_t<R> *)f, (cplx_t<R> *)F, (R)scale, T);
+    } else {
+        k_ring_fwd_real<R><<<dim3((bd.N + 1) / 2, p->batch), th, sm, st>>>((const R *)f, (cplx_t<R> *)F, (R)scale, T);
+    }
+    S2_LAUNCH_CHECK();
+    return S2LET_OK;
+}
+
+template <typename R>
+int run_ring_inv(const s2let_plan *p, const BandDev &bd, const void *F, void *f, double scale, cudaStream_t st)
+{
+    const auto &T = fft_tab<R>(bd);
+    const size_t sm = (size_t)bd.M * sizeof(cplx_t<R>);
+    const int th = fft_threads(bd.M);
+    if (p->cplx) {
+        k_ring_inv_cplx<R><<<dim3(bd.N, p->batch), th, sm, st>>>((const cplx_t<R> *)F, (cplx_t<R> *)f, (R)scale, T);
+    } else {
+        k_ring_inv_real<R><<<dim3((bd.N + 1) / 2, p->batch), th, sm, st>>>((const cplx_t<R> *)F, (R *)f, (R)scale, T);
+    }
+    S2_LAUNCH_CHECK();
+    return S2LET_OK;
+}
+
+template <typename R>
+int run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream_t st)
+{
+    const int n = nmi(p, bd.N);
+    const int off = p->cplx ? bd.N - 1 : 0;
+    const int th = fft_threads(bd.M);
+    if (p->quad64) {
+        const size_t sm = (size_t)bd.M * sizeof(double2);
+        k_theta_quad<double, R, 16><<<dim3(n, p->batch), th, sm, st>>>((const cplx_t<R> *)F, (cplx_t<R> *)F, n, off,
+                                                                       1.0, bd.fd);
+    } else {
+        const size_t sm = (size_t)bd.M * sizeof(float2);
+        k_theta_quad<float, R, 16><<<dim3(n, p->batch), th, sm, st>>>((const cplx_t<R> *)F, (cplx_t<R> *)F, n, off,
+                                                                      1.0f, bd.ff);
+    }
+    S2_LAUNCH_CHECK();
+    return S2LET_OK;
+}
+
+template <typename R, int BT, bool CPLX>
+void launch_synth(const s2let_plan *p, const BandDev &bd, const void *src, const void *kfac, double scale, void *dst,
+                  cudaStream_t st)
+{
+    constexpr int TT = 128;
+    dim3 grid(bd.N, (bd.N + TT - 1) / TT, (p->batch + BT - 1) / BT);
+    k_leg_synth<R, BT, CPLX, TT><<<grid, TT, 0, st>>>((const cplx_t<R> *)src, p->L, nmi(p, p->L), p->L,
+                                                      (const R *)kfac, (R)scale, (cplx_t<R> *)dst, bd.N, p->batch,
+                                                      leg_tab<R>(p, bd));
+}
+
+// S5: dst (band-limit N rectangle) from the plan's L-rectangle src.
+template <typename R>
+int run_synth(const s2let_plan *p, const BandDev &bd, const void *src, const void *kfac, double scale, void *dst,
+              cudaStream_t st)
+{
+    constexpr int BT = std::is_same<R, double>::value ? 4 : 8;
+    if (p->cplx) launch_synth<R, BT, true>(p, bd, src, kfac, scale, dst, st);
+    else launch_synth<R, BT, false>(p, bd, src, kfac, scale, dst, st);
+    S2_LAUNCH_CHECK();
+    return S2LET_OK;
+}
+
+template <typename R, int BT, bool CPLX, int RPT>
+void launch_anal(const s2let_plan *p, const BandDev &bd, const void *G, const void *kfac, double scale, int acc,
+                 void *dst, cudaStream_t st)
+{
+    constexpr int TPB = 256;
+    dim3 grid(bd.N, (p->batch + BT - 1) / BT);
+    k_leg_anal<R, BT, CPLX, RPT, TPB><<<grid, TPB, 0, st>>>((const cplx_t<R> *)G, bd.N, (const R *)kfac, (R)scale,
+                                                            acc, (cplx_t<R> *)dst, p->L, nmi(p, p->L), p->L,
+                                                            p->batch, leg_tab<R>(p, bd));
+}
+
+template <typename R, int BT, bool CPLX>
+void launch_anal_rpt(const s2let_plan *p, const BandDev &bd, const void *G, const void *kfac, double scale, int acc,
+                     void *dst, cudaStream_t st)
+{
+    if (bd.N <= 256) launch_anal<R, BT, CPLX, 1>(p, bd, G, kfac, scale, acc, dst, st);
+    else if (bd.N <= 512) launch_anal<R, BT, CPLX, 2>(p, bd, G, kfac, scale, acc, dst, st);
+    else if (bd.N <= 1024) launch_anal<R, BT, CPLX, 4>(p, bd, G, kfac, scale, acc, dst, st);
+    else launch_anal<R, BT, CPLX, 8>(p, bd, G, kfac, scale, acc, dst, st);
+}
+
+// S3: dst (the plan's L-rectangle) from G at band-limit N.
+template <typename R>
+int run_anal(const s2let_plan *p, const BandDev &bd, const void *G, const void *kfac, double scale, int acc,
+             void *dst, cudaStream_t st)
+{
+    constexpr int BT = std::is_same<R, double>::value ? 2 : 4;
+    if (p->cplx) launch_anal_rpt<R, BT, true>(p, bd, G, kfac, scale, acc, dst, st);
+    else launch_anal_rpt<R, BT, false>(p, bd, G, kfac, scale, acc, dst, st);
+    S2_LAUNCH_CHECK();
+    return S2LET_OK;
+}
+
+// ------------------------------------------------------------ pack / unpack f_lm
+template <typename R>
+__global__ void k_pack(const cplx_t<R> *__restrict__ rect, cplx_t<R> *__restrict__ out, int L, int cplx, int B)
+{
+    const size_t n = (size_t)L * L;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * B) return;
+    const int b = (int)(i / n);
+    const int idx = (int)(i % n);
+    const int l = (int)sqrtf((float)idx);
+    int ll = l;
+    while ((ll + 1) * (ll + 1) <= idx) ++ll;
+    while (ll * ll > idx) --ll;
+    const int m = idx - ll * ll - ll;
+    const int nm = cplx ? 2 * L - 1 : L;
+    cplx_t<R> v;
+    if (cplx) {
+        v = rect[((size_t)b * nm + (m + L - 1)) * L + ll];
+    } else if (m >= 0) {
+        v = rect[((size_t)b * nm + m) * L + ll];
+    } else {
+        v = cconj(rect[((size_t)b * nm + (-m)) * L + ll]);
+        if ((-m) & 1) {
+            v.x = -v.x;
+            v.y = -v.y;
+        }
+    }
+    out[i] = v;
+}
+
+template <typename R>
+__global__ void k_unpack(const cplx_t<R> *__restrict__ in, cplx_t<R> *__restrict__ rect, int L, int cplx, int B)
+{
+    const int nm = cplx ? 2 * L - 1 : L;
+    const size_t total = (size_t)B * nm * L;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int l = (int)(i % L);
+    const int mi = (int)((i / L) % nm);
+    const int b = (int)(i / ((size_t)L * nm));
+    const int m = cplx ? mi - (L - 1) : mi;
+    cplx_t<R> v = mk((R)0, (R)0);
+    if (l >= (m < 0 ? -m : m)) v = in[(size_t)b * L * L + (size_t)l * l + l + m];
+    rect[i] = v;
+}
+
+// ------------------------------------------------------------ transforms
+template <typename R> int sht_fwd_to_rect(s2let_plan *p, const void *f, cudaStream_t st)
+{
+    const BandDev &bd = p->bands.at(p->L);
+    int e;
+    if ((e = run_ring_fwd<R>(p, bd, f, p->F, 1.0 / bd.P, st))) return e;
+    if ((e = run_theta_quad<R>(p, bd, p->F, st))) return e;
+    return run_anal<R>(p, bd, p->F, nullptr, 2.0 * M_PI / bd.P, 0, p->flm, st);
+}
+
+template <typename R> int sht_forward_t(s2let_plan *p, const void *f, void *flm, cudaStream_t st)
+{
+    int e = sht_fwd_to_rect<R>(p, f, st);
+    if (e) return e;
+    const size_t n = (size_t)p->batch * p->L * p->L;
+    k_pack<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const cplx_t<R> *)p->flm, (cplx_t<R> *)flm, p->L,
+                                                           p->cplx, p->batch);
+    S2_LAUNCH_CHECK();
+    return S2LET_OK;
+}
+
+template <typename R> int sht_inverse_t(s2let_plan *p, const void *flm, void *f, cudaStream_t st)
+{
+    const BandDev &bd = p->bands.at(p->L);
+    const size_t n = (size_t)p->batch * nmi(p, p->L) * p->L;
+    k_unpack<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const cplx_t<R> *)flm, (cplx_t<R> *)p->flm, p->L,
+                                                             p->cplx, p->batch);
+    S2_LAUNCH_CHECK();
+    int e;
+    if ((e = run_synth<R>(p, bd, p->flm, nullptr, 1.0, p->F, st))) return e;
+    return run_ring_inv<R>(p, bd, p->F, f, 1.0, st);
+}
+
+// Maps of a wavelet transform, in processing order: index into kfac, band-limit,
+// pointer offset (elements) of the map block; scale J (band-limit L) first.
+struct MapRef {
+    int k;
+    int N;
+    int64_t off;
+    bool scal;
+};
+
+std::vector<MapRef> map_order(const s2let_plan *p)
+{
+    std::vector<MapRef> v;
+    const int ns = (int)p->n_wav.size();
+    for (int i = ns - 1; i >= 0; --i) v.push_back({1 + i, p->n_wav[i], p->wav_off[i], false});
+    v.push_back({0, p->n_scal, 0, true});
+    return v;
+}
+
+template <typename R> int analysis_t(s2let_plan *p, const void *f, void *fw, void *fs, cudaStream_t st)
+{
+    int e = sht_fwd_to_rect<R>(p, f, st);
+    if (e) return e;
+    const int es = elem_size(p);
+    for (const MapRef &mr : map_order(p)) {
+        const BandDev &bd = p->bands.at(mr.N);
+        char *out = mr.scal ? (char *)fs : (char *)fw + mr.off * es;
+        if ((e = run_synth<R>(p, bd, p->flm, p->kfac[mr.k], 1.0, p->F, st))) return e;
+        if ((e = run_ring_inv<R>(p, bd, p->F, out, 1.0, st))) return e;
+    }
+    return S2LET_OK;
+}
+
+template <typename R> int synthesis_t(s2let_plan *p, const void *fw, const void *fs, void *f, cudaStream_t st)
+{
+    const int es = elem_size(p);
+    int e, first = 1;
+    for (const MapRef &mr : map_order(p)) {
+        const BandDev &bd = p->bands.at(mr.N);
+        const char *in = mr.scal ? (const char *)fs : (const char *)fw + mr.off * es;
+        if ((e = run_ring_fwd<R>(p, bd, in, p->F, 1.0 / bd.P, st))) return e;
+        if ((e = run_theta_quad<R>(p, bd, p->F, st))) return e;
+        if ((e = run_anal<R>(p, bd, p->F, p->kfac[mr.k], 2.0 * M_PI / bd.P, first ? 0 : 1, p->flm, st))) return e;
+        first = 0;
+    }
+    const BandDev &bl = p->bands.at(p->L);
+    if ((e = run_synth<R>(p, bl, p->flm, nullptr, 1.0, p->F, st))) return e;
+    return run_ring_inv<R>(p, bl, p->F, f, 1.0, st);
+}
+
+template <typename R> int adjoint_t(s2let_plan *p, const void *gw, const void *gs, void *gf, cudaStream_t st)
+{
+    const int es = elem_size(p);
+    int e, first = 1;
+    for (const MapRef &mr : map_order(p)) {
+        const BandDev &bd = p->bands.at(mr.N);
+        const char *in = mr.scal ? (const char *)gs : (const char *)gw + mr.off * es;
+        // inverse-transform adjoint: unnormalised ring DFT, unweighted Legendre sum
+        if ((e = run_ring_fwd<R>(p, bd, in, p->F, 1.0, st))) return e;
+        if ((e = run_anal<R>(p, bd, p->F, p->kfac[mr.k], 1.0, first ? 0 : 1, p->flm, st))) return e;
+        first = 0;
+    }
+    // forward-transform adjoint: Legendre sum (2 pi / P), quadrature (symmetric), ring DFT (1/P)
+    const BandDev &bl = p->bands.at(p->L);
+    if ((e = run_synth<R>(p, bl, p->flm, nullptr, 2.0 * M_PI / bl.P, p->F, st))) return e;
+    if ((e = run_theta_quad<R>(p, bl, p->F, st))) return e;
+    return run_ring_inv<R>(p, bl, p->F, gf, 1.0 / bl.P, st);
+}
+
+// ------------------------------------------------------------ plan construction
+template <typename K> void allow_smem(K kernel, size_t bytes)
+{
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+void set_smem_limits(int Mmax)
+{
+    const size_t d = (size_t)Mmax * sizeof(double2), f = (size_t)Mmax * sizeof(float2);
+    allow_smem(k_ring_fwd_real<double>, d);
+    allow_smem(k_ring_fwd_cplx<double>, d);
+    allow_smem(k_ring_inv_real<double>, d);
+    allow_smem(k_ring_inv_cplx<double>, d);
+    allow_smem(k_ring_fwd_real<float>, f);
+    allow_smem(k_ring_fwd_cplx<float>, f);
+    allow_smem(k_ring_inv_real<float>, f);
+    allow_smem(k_ring_inv_cplx<float>, f);
+    allow_smem(k_theta_quad<double, double, 16>, d);
+    allow_smem(k_theta_quad<double, float, 16>, d);
+    allow_smem(k_theta_quad<float, float, 16>, f);
+}
+
+int build_band_dev(s2let_plan *p, int N, BandDev &bd)
+{
+    s2h::Band h;
+    s2h::build_band(N, h);
+    int err = S2LET_OK;
+    bd.N = h.N;
+    bd.P = h.P;
+    bd.M = h.M;
+    bd.logM = h.logM;
+    auto &o = p->owned;
+    bd.fd.chirp = dev_upload(to_c<double2>(h.chirp), o, err);
+    bd.fd.bhat = dev_upload(to_c<double2>(h.bhat), o, err);
+    bd.fd.what = dev_upload(to_c<double2>(h.what), o, err);
+    bd.fd.tw = dev_upload(to_c<double2>(h.tw), o, err);
+    bd.fd.phase = dev_upload(to_c<double2>(h.phase), o, err);
+    bd.ff.chirp = dev_upload(to_c<float2>(h.chirp), o, err);
+    bd.ff.bhat = dev_upload(to_c<float2>(h.bhat), o, err);
+    bd.ff.what = dev_upload(to_c<float2>(h.what), o, err);
+    bd.ff.tw = dev_upload(to_c<float2>(h.tw), o, err);
+    bd.ff.phase = dev_upload(to_c<float2>(h.phase), o, err);
+    bd.fd.N = h.N;
+    bd.fd.P = h.P;
+    bd.fd.M = h.M;
+    bd.fd.logM = h.logM;
+    bd.ff.N = h.N;
+    bd.ff.P = h.P;
+    bd.ff.M = h.M;
+    bd.ff.logM = h.logM;
+    std::vector<RingD> rd(N);
+    std::vector<RingF> rf(N);
+    for (int t = 0; t < N; ++t) {
+        rd[t].sgn = h.sgn[t];
+        rd[t].y = h.y[t];
+        rf[t].xh = h.xh[t];
+        rf[t].xl = h.xl[t];
+    }
+    bd.ringd = dev_upload(rd, o, err);
+    bd.ringf = dev_upload(rf, o, err);
+    double *sinth = dev_upload(h.sinth, o, err);
+    if (err) return err;
+    // seeds: sectoral values, then the first significant degree per (m, t)
+    const size_t nn = (size_t)N * N;
+    double *mant = nullptr;
+    int *expo = nullptr;
+    if (cudaMalloc(&mant, nn * sizeof(double)) != cudaSuccess) return S2LET_ERR_ALLOC;
+    if (cudaMalloc(&expo, nn * sizeof(int)) != cudaSuccess) {
+        cudaFree(mant);
+        return S2LET_ERR_ALLOC;
+    }
+    void *ls = nullptr, *seed = nullptr;
+    if (cudaMalloc(&ls, nn * sizeof(int)) != cudaSuccess || cudaMalloc(&seed, nn * sizeof(double2)) != cudaSuccess) {
+        cudaFree(mant);
+        cudaFree(expo);
+        if (ls) cudaFree(ls);
+        return S2LET_ERR_ALLOC;
+    }
+    o.push_back(ls);
+    o.push_back(seed);
+    bd.ls = (int *)ls;
+    bd.seed = (double2 *)seed;
+    k_sectoral<<<(N + 127) / 128, 128>>>(N, sinth, mant, expo);
+    k_seed_start<<<(unsigned)((nn + 127) / 128), 128>>>(N, mant, expo, bd.ringd, p->coefd, p->L, bd.ls, bd.seed);
+    cudaError_t ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
+    cudaFree(mant);
+    cudaFree(expo);
+    return ce == cudaSuccess ? S2LET_OK : S2LET_ERR_CUDA;
+}
+
+int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
+{
+    *out = nullptr;
+    if (L < 3 || L > kMaxL || B < 2 || batch < 1) return S2LET_ERR_ARG;
+    const int J = s2h::jmax(L, B);
+    if (J0 < 0 || J0 >= J) return S2LET_ERR_ARG;
+    const int prec = flags & S2LET_PREC_MASK;
+    if (prec != S2LET_PREC_FP64 && prec != S2LET_PREC_FP32) return S2LET_ERR_ARG;
+    if (flags & ~(S2LET_COMPLEX | S2LET_MULTIRES | S2LET_PREC_MASK | S2LET_QUAD_FP32)) return S2LET_ERR_ARG;
+    if ((flags & S2LET_QUAD_FP32) && prec == S2LET_PREC_FP64) return S2LET_ERR_ARG;
+
+    std::unique_ptr<s2let_plan> p(new (std::nothrow) s2let_plan());
+    if (!p) return S2LET_ERR_ALLOC;
+    p->L = L;
+    p->B = B;
+    p->J0 = J0;
+    p->J = J;
+    p->flags = flags;
+    p->batch = batch;
+    p->cplx = flags & S2LET_COMPLEX;
+    p->multires = flags & S2LET_MULTIRES;
+    p->fp64 = prec == S2LET_PREC_FP64;
+    p->quad64 = !(flags & S2LET_QUAD_FP32);
+    // band-limits (Sect. 3.1)
+    auto ipow = [](long long b, int e) {
+        long long r = 1;
+        for (int i = 0; i < e; ++i) r = std::min<long long>(r * b, 1LL << 40);
+        return r;
+    };
+    p->n_scal = p->multires ? (int)std::min<long long>(L, ipow(B, J0)) : L;
+    int64_t off = 0;
+    for (int j = J0; j <= J; ++j) {
+        const int N = p->multires ? (int)std::min<long long>(L, ipow(B, j + 1)) : L;
+        p->n_wav.push_back(N);
+        p->wav_off.push_back(off);
+        off += map_elems(p.get(), N) * batch;
+    }
+    p->wav_elems = off;
+    p->scal_elems = map_elems(p.get(), p->n_scal) * batch;
+
+    int err = S2LET_OK;
+    // recurrence coefficients for degrees and orders < L
+    std::vector<double> a, ab;
+    s2h::legendre_coefs(L, a, ab);
+    std::vector<double2> cd(a.size());
+    std::vector<float4> cf(a.size());
+    for (size_t i = 0; i < a.size(); ++i) {
+        cd[i] = make_double2(a[i], ab[i]);
+        const float ah = (float)a[i], bh = (float)ab[i];
+        cf[i] = make_float4(ah, (float)(a[i] - (double)ah), bh, (float)(ab[i] - (double)bh));
+    }
+    p->coefd = dev_upload(cd, p->owned, err);
+    p->coeff = dev_upload(cf, p->owned, err);
+    if (err) return err;
+    // kernel factors sqrt(4 pi/(2l+1)) Phi_l0 = eta(l / B^J0), sqrt(4 pi/(2l+1)) Psi^j_l0 = kappa(l / B^j)
+    for (int k = 0; k <= J - J0 + 1; ++k) {
+        std::vector<double> fac(L);
+        for (int l = 0; l < L; ++l) {
+            fac[l] = (k == 0) ? s2h::eta_lambda(l / std::pow((double)B, J0), B)
+                              : s2h::kappa_lambda(l / std::pow((double)B, J0 + k - 1), B);
+        }
+        if (p->fp64) {
+            p->kfac.push_back(dev_upload(fac, p->owned, err));
+        } else {
+            std::vector<float> ff(fac.begin(), fac.end());
+            p->kfac.push_back(dev_upload(ff, p->owned, err));
+        }
+        if (err) return err;
+    }
+    // per band-limit tables
+    std::vector<int> Ns = p->n_wav;
+    Ns.push_back(p->n_scal);
+    Ns.push_back(L);
+    std::sort(Ns.begin(), Ns.end());
+    Ns.erase(std::unique(Ns.begin(), Ns.end()), Ns.end());
+    int Mmax = 2;
+    for (int N : Ns) {
+        BandDev bd;
+        if ((err = build_band_dev(p.get(), N, bd))) return err;
+        Mmax = std::max(Mmax, bd.M);
+        p->bands[N] = bd;
+    }
+    set_smem_limits(Mmax);
+    // workspace: two L-rectangles of complex values per map
+    const size_t ws = (size_t)batch * nmi(p.get(), L) * L * 2 * elem_size(p.get());
+    if (cudaMalloc(&p->F, ws) != cudaSuccess) return S2LET_ERR_ALLOC;
+    p->owned.push_back(p->F);
+    if (cudaMalloc(&p->flm, ws) != cudaSuccess) return S2LET_ERR_ALLOC;
+    p->owned.push_back(p->flm);
+    if (cudaGetLastError() != cudaSuccess) return S2LET_ERR_CUDA;
+    *out = p.release();
+    return S2LET_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ C ABI
+extern "C" {
+
+int s2let_jmax(int L, int B)
+{
+    if (L < 2 || B < 2) return S2LET_ERR_ARG;
+    return s2h::jmax(L, B);
+}
+
+int s2let_plan_create(s2let_plan **plan, int L, int B, int J_min, int flags, int batch)
+{
+    if (!plan) return S2LET_ERR_ARG;
+    return plan_create(plan, L, B, J_min, flags, batch);
+}
+
+int s2let_plan_destroy(s2let_plan *plan)
+{
+    delete plan;
+    return S2LET_OK;
+}
+
+int s2let_plan_info(const s2let_plan *p, int *J, int *n_scales, int64_t *wav_elems, int64_t *scal_elems, int *N_scal)
+{
+    if (!p) return S2LET_ERR_ARG;
+    if (J) *J = p->J;
+    if (n_scales) *n_scales = (int)p->n_wav.size();
+    if (wav_elems) *wav_elems = p->wav_elems;
+    if (scal_elems) *scal_elems = p->scal_elems;
+    if (N_scal) *N_scal = p->n_scal;
+    return S2LET_OK;
+}
+
+int s2let_wav_layout(const s2let_plan *p, int j, int *N_j, int64_t *offset, int64_t *elems)
+{
+    if (!p) return S2LET_ERR_ARG;
+    if (j == -1) {
+        if (N_j) *N_j = p->n_scal;
+        if (offset) *offset = 0;
+        if (elems) *elems = p->scal_elems;
+        return S2LET_OK;
+    }
+    if (j < p->J0 || j > p->J) return S2LET_ERR_ARG;
+    const int i = j - p->J0;
+    if (N_j) *N_j = p->n_wav[i];
+    if (offset) *offset = p->wav_off[i];
+    if (elems) *elems = map_elems(p, p->n_wav[i]) * p->batch;
+    return S2LET_OK;
+}
+
+#define S2_DISPATCH(fn, ...) (p->fp64 ? fn<double>(__VA_ARGS__) : fn<float>(__VA_ARGS__))
+
+int s2let_analysis(s2let_plan *p, const void *f, void *f_wav, void *f_scal, void *stream)
+{
+    if (!p || !f || !f_wav || !f_scal) return S2LET_ERR_ARG;
+    return S2_DISPATCH(analysis_t, p, f, f_wav, f_scal, (cudaStream_t)stream);
+}
+
+int s2let_synthesis(s2let_plan *p, const void *f_wav, const void *f_scal, void *f, void *stream)
+{
+    if (!p || !f || !f_wav || !f_scal) return S2LET_ERR_ARG;
+    return S2_DISPATCH(synthesis_t, p, f_wav, f_scal, f, (cudaStream_t)stream);
+}
+
+int s2let_adjoint(s2let_plan *p, const void *g_wav, const void *g_scal, void *g_f, void *stream)
+{
+    if (!p || !g_wav || !g_scal || !g_f) return S2LET_ERR_ARG;
+    return S2_DISPATCH(adjoint_t, p, g_wav, g_scal, g_f, (cudaStream_t)stream);
+}
+
+int s2let_sht_forward(s2let_plan *p, const void *f, void *flm, void *stream)
+{
+    if (!p || !f || !flm) return S2LET_ERR_ARG;
+    return S2_DISPATCH(sht_forward_t, p, f, flm, (cudaStream_t)stream);
+}
+
+int s2let_sht_inverse(s2let_plan *p, const void *flm, void *f, void *stream)
+{
+    if (!p || !f || !flm) return S2LET_ERR_ARG;
+    return S2_DISPATCH(sht_inverse_t, p, flm, f, (cudaStream_t)stream);
+}
+
+const char *s2let_strerror(int s)
+{
+    switch (s) {
+    case S2LET_OK: return "ok";
+    case S2LET_ERR_ARG: return "invalid argument";
+    case S2LET_ERR_ALLOC: return "allocation failed";
+    case S2LET_ERR_CUDA: return "CUDA error";
+    case S2LET_ERR_TIMEOUT: return "device wait timed out";
+    case S2LET_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,147 @@
+"""Python face of the C ABI: a Plan object whose methods take torch CUDA
+tensors and pass their device pointers and the current CUDA stream to
+libs2let_gpu.so.  Every step of the transforms runs in the library's kernels;
+this module only checks shapes and dtypes and marshals arguments."""
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import (S2LET_COMPLEX, S2LET_MULTIRES, S2LET_PREC_FP32, S2LET_PREC_FP64,  # noqa: F401
+                   S2LET_QUAD_FP32, check)
+
+PRECISIONS = {"fp64": S2LET_PREC_FP64, "fp32": S2LET_PREC_FP32}
+
+
+def jmax(L, B):
+    r = _lib.lib().s2let_jmax(L, B)
+    if r < 0:
+        raise _lib.S2letError("s2let_jmax", r)
+    return r
+
+
+def _stream_handle(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """A batched transform plan: `batch` maps of band-limit L, dilation B,
+    lowest scale J_min (Sect. 2.2), real or complex, multiresolution or not,
+    precision "fp64" or "fp32"."""
+
+    def __init__(self, L, B, J_min, batch=1, real=True, multires=True, precision="fp64",
+                 quad_fp32=False, device=None):
+        flags = (0 if real else S2LET_COMPLEX) | (S2LET_MULTIRES if multires else 0) | PRECISIONS[precision]
+        if quad_fp32:
+            flags |= S2LET_QUAD_FP32
+        self.L, self.B, self.J_min, self.batch = L, B, J_min, batch
+        self.real, self.multires, self.precision = real, multires, precision
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self._h = ctypes.c_void_p()
+        lib = _lib.lib()
+        with torch.cuda.device(self.device):
+            check("s2let_plan_create", lib.s2let_plan_create(ctypes.byref(self._h), L, B, J_min, flags, batch))
+        J = ctypes.c_int()
+        ns = ctypes.c_int()
+        we = ctypes.c_int64()
+        se = ctypes.c_int64()
+        nsc = ctypes.c_int()
+        check("s2let_plan_info", lib.s2let_plan_info(self._h, ctypes.byref(J), ctypes.byref(ns), ctypes.byref(we),
+                                                     ctypes.byref(se), ctypes.byref(nsc)))
+        self.J, self.n_scales = J.value, ns.value
+        self.wav_elems, self.scal_elems, self.N_scal = we.value, se.value, nsc.value
+        self.scales = []
+        for j in range(J_min, self.J + 1):
+            n = ctypes.c_int()
+            off = ctypes.c_int64()
+            cnt = ctypes.c_int64()
+            check("s2let_wav_layout", lib.s2let_wav_layout(self._h, j, ctypes.byref(n), ctypes.byref(off),
+                                                           ctypes.byref(cnt)))
+            self.scales.append((j, n.value, off.value, cnt.value))
+
+    def close(self):
+        if self._h:
+            _lib.lib().s2let_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- shapes
+    def map_shape(self, N):
+        s = (self.batch, N, 2 * N - 1)
+        return s if self.real else s + (2,)
+
+    def empty_map(self, N=None):
+        return torch.empty(self.map_shape(self.L if N is None else N), dtype=self.dtype, device=self.device)
+
+    def empty_wavelets(self):
+        """(f_wav flat buffer, f_scal) as the library lays them out."""
+        fw = torch.empty(self.wav_elems, dtype=self.dtype, device=self.device)
+        fs = torch.empty(self.map_shape(self.N_scal), dtype=self.dtype, device=self.device)
+        return fw, fs
+
+    def wavelet_views(self, fw):
+        """Views of each scale's block of the flat f_wav buffer, scale J_min first."""
+        return [fw[off:off + cnt].view(self.map_shape(n)) for (_, n, off, cnt) in self.scales]
+
+    def flm_shape(self):
+        return (self.batch, self.L * self.L, 2)
+
+    def _chk(self, t, numel, name):
+        if not (t.is_cuda and t.dtype == self.dtype and t.is_contiguous() and t.numel() == numel):
+            raise ValueError("%s: need a contiguous %s CUDA tensor with %d elements" % (name, self.dtype, numel))
+        return ctypes.c_void_p(t.data_ptr())
+
+    def _map_numel(self, N):
+        n = self.batch * N * (2 * N - 1)
+        return n if self.real else 2 * n
+
+    # ---------------------------------------------------------------- transforms
+    def analysis(self, f, f_wav=None, f_scal=None, stream=None):
+        if f_wav is None:
+            f_wav, f_scal = self.empty_wavelets()
+        a = self._chk(f, self._map_numel(self.L), "f")
+        w = self._chk(f_wav, self.wav_elems, "f_wav")
+        s = self._chk(f_scal, self.scal_elems, "f_scal")
+        check("s2let_analysis", _lib.lib().s2let_analysis(self._h, a, w, s, _stream_handle(stream)))
+        return f_wav, f_scal
+
+    def synthesis(self, f_wav, f_scal, f=None, stream=None):
+        if f is None:
+            f = self.empty_map()
+        w = self._chk(f_wav, self.wav_elems, "f_wav")
+        s = self._chk(f_scal, self.scal_elems, "f_scal")
+        o = self._chk(f, self._map_numel(self.L), "f")
+        check("s2let_synthesis", _lib.lib().s2let_synthesis(self._h, w, s, o, _stream_handle(stream)))
+        return f
+
+    def adjoint(self, g_wav, g_scal, g_f=None, stream=None):
+        if g_f is None:
+            g_f = self.empty_map()
+        w = self._chk(g_wav, self.wav_elems, "g_wav")
+        s = self._chk(g_scal, self.scal_elems, "g_scal")
+        o = self._chk(g_f, self._map_numel(self.L), "g_f")
+        check("s2let_adjoint", _lib.lib().s2let_adjoint(self._h, w, s, o, _stream_handle(stream)))
+        return g_f
+
+    def sht_forward(self, f, flm=None, stream=None):
+        if flm is None:
+            flm = torch.empty(self.flm_shape(), dtype=self.dtype, device=self.device)
+        a = self._chk(f, self._map_numel(self.L), "f")
+        o = self._chk(flm, self.batch * self.L * self.L * 2, "flm")
+        check("s2let_sht_forward", _lib.lib().s2let_sht_forward(self._h, a, o, _stream_handle(stream)))
+        return flm
+
+    def sht_inverse(self, flm, f=None, stream=None):
+        if f is None:
+            f = self.empty_map()
+        a = self._chk(flm, self.batch * self.L * self.L * 2, "flm")
+        o = self._chk(f, self._map_numel(self.L), "f")
+        check("s2let_sht_inverse", _lib.lib().s2let_sht_inverse(self._h, a, o, _stream_handle(stream)))
+        return f

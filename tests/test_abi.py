@@ -1,0 +1,54 @@
+"""CPU checks of the C ABI library: it builds, loads without a GPU and exports
+every function include/s2let_gpu.h declares; host-only entry points work."""
+import os
+import re
+
+import pytest
+
+from paper_1211_1680_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "s2let_gpu.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(s2let_\w+)\s*\(", txt)))
+
+
+def test_library_builds_and_loads():
+    build.build()
+    assert os.path.exists(build.LIB)
+    assert _lib.lib() is not None
+
+
+def test_exports_every_declared_symbol():
+    names = _declared()
+    assert len(names) >= 10
+    L = _lib.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(_lib.SIGNATURES)
+
+
+def test_host_entry_points():
+    L = _lib.lib()
+    assert L.s2let_jmax(2048, 2) == 11
+    assert L.s2let_jmax(128, 3) == 5
+    assert L.s2let_jmax(3, 2) == 1
+    assert L.s2let_jmax(1, 2) == _lib.S2LET_ERR_ARG
+    assert L.s2let_strerror(0) == b"ok"
+
+
+def test_plan_argument_errors_need_no_gpu():
+    import ctypes
+    L = _lib.lib()
+    h = ctypes.c_void_p()
+    # J_min must be < J (Sect. 2.2); these are rejected before any CUDA call
+    assert L.s2let_plan_create(ctypes.byref(h), 32, 2, 5, 0, 1) == _lib.S2LET_ERR_ARG
+    assert L.s2let_plan_create(ctypes.byref(h), 2, 2, 0, 0, 1) == _lib.S2LET_ERR_ARG
+    assert L.s2let_plan_create(ctypes.byref(h), 32, 1, 0, 0, 1) == _lib.S2LET_ERR_ARG
+    assert L.s2let_plan_create(ctypes.byref(h), 32, 2, 0, 0x1000, 1) == _lib.S2LET_ERR_ARG
+    assert L.s2let_plan_create(ctypes.byref(h), 4096, 2, 0, 0, 1) == _lib.S2LET_ERR_ARG
+    assert L.s2let_plan_create(ctypes.byref(h), 32, 2, 0, 0, 0) == _lib.S2LET_ERR_ARG
+    assert not h.value

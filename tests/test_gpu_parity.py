@@ -1,0 +1,97 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the
+same seeded inputs.  Tolerances (max relative error, normwise per result):
+1e-10 for FP64 plans, 1e-5 for FP32 plans."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import kernels, sht, wavelet  # noqa: E402
+from paper_1211_1680_gb300 import inputs  # noqa: E402
+from paper_1211_1680_gb300.s2let import Plan  # noqa: E402
+from tests.gpu_util import TOL, flm_from_dev, flm_to_dev, from_dev_map, rel_err, to_dev_map  # noqa: E402
+
+
+def _maps(L, seeds, real, kind="white"):
+    return np.stack([sht.inverse(inputs.random_flm(L, s, real, kind), L, real=real) for s in seeds])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("real", [True, False])
+@pytest.mark.parametrize("L", [3, 4, 8, 17, 33, 64])
+def test_sht_forward_inverse(L, real, prec):
+    seeds = [11, 12, 13]
+    plan = Plan(L, 2, 0, batch=len(seeds), real=real, multires=True, precision=prec)
+    flm = np.stack([inputs.random_flm(L, s, real) for s in seeds])
+    f_ref = np.stack([sht.inverse(x, L, real=real) for x in flm])
+    # inverse
+    f_gpu = from_dev_map(plan.sht_inverse(flm_to_dev(flm, plan.dtype)), real)
+    assert rel_err(f_gpu, f_ref) < TOL[prec]
+    # forward of the oracle's maps
+    g = flm_from_dev(plan.sht_forward(to_dev_map(f_ref, plan.dtype, real)))
+    ref = np.stack([sht.forward(x, L) for x in f_ref])
+    assert rel_err(g, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sht_forward_not_bandlimited(prec):
+    """Any samples (pole ring not constant, no band-limit): same linear map."""
+    L = 24
+    x = np.stack([inputs.random_map((L, 2 * L - 1), s) for s in (5, 6)])
+    plan = Plan(L, 2, 0, batch=2, real=True, precision=prec)
+    g = flm_from_dev(plan.sht_forward(to_dev_map(x, plan.dtype, True)))
+    ref = np.stack([sht.forward(v, L) for v in x])
+    assert rel_err(g, ref) < TOL[prec]
+
+
+CASES = [  # L, B, J0, multires, real, prec
+    (32, 2, 0, False, True, "fp64"),      # full-resolution L=32 workload
+    (32, 2, 0, True, True, "fp64"),       # scaling map at band-limit 1
+    (32, 2, 0, False, True, "fp32"),
+    (40, 3, 1, True, False, "fp64"),
+    (27, 3, 2, False, False, "fp32"),
+    (65, 2, 5, True, True, "fp32"),       # J0 = J - 1
+    (3, 2, 0, True, True, "fp64"),        # smallest L
+    (96, 2, 2, True, True, "fp64"),
+]
+
+
+@pytest.mark.parametrize("L,B,J0,multires,real,prec", CASES)
+def test_wavelet_analysis_synthesis(L, B, J0, multires, real, prec):
+    seeds = [21, 22]
+    f = _maps(L, seeds, real)
+    plan = Plan(L, B, J0, batch=len(seeds), real=real, multires=multires, precision=prec)
+    fw_d, fs_d = plan.analysis(to_dev_map(f, plan.dtype, real))
+    ref = [wavelet.analysis(x, L, B, J0, multires, real) for x in f]
+    for i, view in enumerate(plan.wavelet_views(fw_d)):
+        got = from_dev_map(view, real)
+        want = np.stack([r[0][i] for r in ref])
+        assert rel_err(got, want) < TOL[prec], "scale %d" % (J0 + i)
+    got = from_dev_map(fs_d, real)
+    assert rel_err(got, np.stack([r[1] for r in ref])) < TOL[prec]
+    # synthesis of the oracle's wavelet maps
+    fw_in = torch.cat([to_dev_map(np.stack([r[0][i] for r in ref]), plan.dtype, real).reshape(-1)
+                       for i in range(len(ref[0][0]))])
+    fs_in = to_dev_map(np.stack([r[1] for r in ref]), plan.dtype, real)
+    rec = from_dev_map(plan.synthesis(fw_in, fs_in), real)
+    want = np.stack([wavelet.synthesis(r[0], r[1], L, B, J0, multires, real) for r in ref])
+    assert rel_err(rec, want) < TOL[prec]
+    assert rel_err(rec, f) < TOL[prec]
+
+
+@pytest.mark.parametrize("L,B,J0,multires,real,prec", [
+    (16, 2, 1, True, True, "fp64"), (16, 2, 0, False, False, "fp64"),
+    (24, 3, 1, True, True, "fp32"), (33, 2, 2, True, False, "fp32"),
+])
+def test_adjoint_against_oracle(L, B, J0, multires, real, prec):
+    plan = Plan(L, B, J0, batch=2, real=real, multires=multires, precision=prec)
+    n_scal, n_wav = kernels.bandlimits(L, B, J0, multires)
+    gws = [[inputs.random_map((n, 2 * n - 1), 100 * b + i, real) for i, n in enumerate(n_wav)] for b in range(2)]
+    gss = [inputs.random_map((n_scal, 2 * n_scal - 1), 77 + b, real) for b in range(2)]
+    fw = torch.cat([to_dev_map(np.stack([gw[i] for gw in gws]), plan.dtype, real).reshape(-1)
+                    for i in range(len(n_wav))])
+    fs = to_dev_map(np.stack(gss), plan.dtype, real)
+    got = from_dev_map(plan.adjoint(fw, fs), real)
+    want = np.stack([wavelet.analysis_adjoint(gws[b], gss[b], L, B, J0, multires, real) for b in range(2)])
+    assert rel_err(got, want) < TOL[prec]
