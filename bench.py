@@ -1,0 +1,386 @@
+#!/usr/bin/env python3
+"""Benchmark: batched axisymmetric wavelet round trips (analysis then synthesis)
+on MW-sampled spheres, one step = one round trip of a batch of real maps at
+L = 2048, B = 2, J_min = 2, multiresolution (64 maps per GPU).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Prints one JSON line (rank 0).  Inputs are seeded synthetic maps: Gaussian
+f_lm with C_l = 1/(l(l+1)), turned into maps by the library's inverse
+transform before timing (as the paper's validation does).  The map batch
+(2.1 GB in FP32) is far larger than the 129 MB L2, so no flush is needed.
+Multi-GPU: each rank transforms its own 64 maps (weak scaling, no collective
+on the data path); the elapsed time is the maximum over ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "wavelet round-trips/s, L=2048x64 maps, vs plain FP64 GPU path; max err vs oracle"
+UNIT = "map round-trips/s"
+SM_COUNT = 152
+FP32_LANES = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--quad-fp32", action="store_true", help="theta quadrature in FP32 (FP32 plans)")
+    ap.add_argument("--L", type=int, default=2048)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--B", type=int, default=2)
+    ap.add_argument("--J-min", type=int, default=2)
+    ap.add_argument("--fp64-batch", type=int, default=8)
+    ap.add_argument("--cpu-orders", type=int, default=128)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-check", action="store_true")
+    return ap.parse_args()
+
+
+def config(a):
+    return {"workload": "real maps, L=%d, B=%d, J_min=%d, multiresolution, %d maps per GPU, f_lm ~ C_l=1/(l(l+1))"
+                        % (a.L, a.B, a.J_min, a.batch),
+            "L": a.L, "B": a.B, "J_min": a.J_min, "maps_per_gpu": a.batch, "multires": True, "signal": "real",
+            "precision": a.precision + ("+quad_fp32" if a.quad_fp32 else ""),
+            "l2": "inputs larger than L2 (map batch %.2f GB)" % (a.batch * a.L * (2 * a.L - 1)
+                                                                   * (4 if a.precision == "fp32" else 8) / 1e9)}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------- oracle legs
+def oracle_sample_step(f, a, orders):
+    """One step of the CPU oracle: analysis then synthesis of one map at the
+    full workload size, restricted to the given orders m (both transforms act
+    on each order separately)."""
+    import oracle.wavelet as ow
+    fw, fs = ow.analysis(f, a.L, a.B, a.J_min, True, False, orders=orders)
+    ow.synthesis(fw, fs, a.L, a.B, a.J_min, True, False, orders=orders)
+
+
+def oracle_input(a, seed):
+    import oracle.sht as osht
+    from paper_1211_1680_gb300 import inputs
+    return osht.inverse(inputs.random_flm(a.L, seed, True, "cl"), a.L, real=True)
+
+
+def cpu_baseline(a, steps=1, warmup=1):
+    """Oracle timed on this host's cores on a bounded sample of the workload."""
+    import oracle.sht as osht
+    rng = np.random.default_rng(12345)
+    f = np.random.default_rng(7).standard_normal((a.L, 2 * a.L - 1))   # values do not change the cost
+    for N in sorted({a.L} | {min(a.L, a.B ** (j + 1)) for j in range(a.J_min, 20)} | {min(a.L, a.B ** a.J_min)}):
+        osht._quadrature_matrices(N)
+        osht._phase_matrix_phi(N)
+    all_orders = np.arange(-(a.L - 1), a.L)
+    for _ in range(warmup):
+        oracle_sample_step(f, a, rng.choice(all_orders, size=min(a.cpu_orders, len(all_orders)), replace=False))
+    t = 0.0
+    for _ in range(steps):
+        orders = rng.choice(all_orders, size=min(a.cpu_orders, len(all_orders)), replace=False)
+        t0 = time.perf_counter()
+        oracle_sample_step(f, a, orders)
+        t += time.perf_counter() - t0
+    frac = steps * len(orders) / len(all_orders)
+    value = frac / t
+    return {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "oracle analysis+synthesis of 1 map at L=%d restricted to %d random orders m of %d "
+                      "(every stage acts on each order separately); value = (orders/%d) / time; %d step(s); "
+                      "matrix products on %d rows run below their all-rows efficiency, so this understates "
+                      "the oracle" % (a.L, len(orders), len(all_orders), len(all_orders), steps, len(orders)),
+            "seconds": t}
+
+
+def run_reference(a, rank):
+    if rank != 0:
+        return 0
+    import oracle.sht as osht
+    rng = np.random.default_rng(4242)
+    f = np.random.default_rng(7).standard_normal((a.L, 2 * a.L - 1))
+    for N in sorted({a.L} | {min(a.L, a.B ** (j + 1)) for j in range(a.J_min, 20)} | {min(a.L, a.B ** a.J_min)}):
+        osht._quadrature_matrices(N)
+        osht._phase_matrix_phi(N)
+    all_orders = np.arange(-(a.L - 1), a.L)
+    k = min(a.cpu_orders, len(all_orders))
+    for _ in range(a.warmup):
+        oracle_sample_step(f, a, rng.choice(all_orders, size=k, replace=False))
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        oracle_sample_step(f, a, rng.choice(all_orders, size=k, replace=False))
+    t = time.perf_counter() - t0
+    value = a.steps * k / len(all_orders) / t
+    sample = ("each step: oracle analysis+synthesis of 1 map at L=%d restricted to %d random orders of %d; "
+              "value = (orders/%d) / time" % (a.L, k, len(all_orders), len(all_orders)))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 * t / a.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(a),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU leg
+def check_errors(plan, x, fw, fs, out, flm, a):
+    """Per-scale max relative error of map 0 against the oracle, on sampled rings:
+    W^j(theta_t, phi_p) = sum_lm kappa(l/B^j) f_lm Y_lm (Eq. wav2) from the
+    input coefficients; plus the round-trip reconstruction error."""
+    import oracle.sht as osht
+    import oracle.wavelet as ow
+    phi, psi = ow.tables(a.L, a.B, a.J_min)
+    res = {}
+    views = plan.wavelet_views(fw)
+    maps = [("scal", plan.N_scal, phi, fs)] + [("j%d" % j, n, p, v) for (j, n, _, _), p, v in
+                                               zip(plan.scales, psi, views)]
+    l_of = np.repeat(np.arange(a.L), 2 * np.arange(a.L) + 1)
+    norm = np.sqrt(4 * np.pi / (2 * l_of + 1))
+    for name, n, kern, v in maps:
+        wlm = (norm * flm * kern[l_of])[:n * n]
+        rings = sorted({0, 1, n // 3, n // 2, n - 2, n - 1} & set(range(n)))
+        ref = osht.inverse_at(wlm, n, rings, np.arange(2 * n - 1)).real
+        got = v[0].detach().double().cpu().numpy()[rings]
+        full = v[0].detach().double().abs().max().item()
+        res[name] = float(np.max(np.abs(got - ref)) / max(full, 1e-300))
+    rec = float(((out[0] - x[0]).abs().max() / x[0].abs().max()).item())
+    return {"max_rel_err_by_scale": res, "max_rel_err": max(res.values()), "round_trip_rel_err": rec,
+            "check": "map 0; rings {0,1,N/3,N/2,N-2,N-1} of every scale against the oracle's direct sum; "
+                     "error normalised by the scale map's max"}
+
+
+def run_gpu(a, rank, world, local_rank):
+    import torch
+    from paper_1211_1680_gb300 import inputs
+    from paper_1211_1680_gb300.s2let import Plan
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    seeds = [3000 + rank * a.batch + i for i in range(a.batch)]
+    flm = inputs.random_flm_batch(a.L, seeds, real=True, kind="cl")
+    plan = Plan(a.L, a.B, a.J_min, batch=a.batch, real=True, multires=True, precision=a.precision,
+                quad_fp32=a.quad_fp32)
+    flm_d = torch.from_numpy(np.stack([flm.real, flm.imag], -1)).to(device="cuda", dtype=plan.dtype).contiguous()
+    x = plan.sht_inverse(flm_d)
+    del flm_d
+    fw, fs = plan.empty_wavelets()
+    out = plan.empty_map()
+    stream = torch.cuda.current_stream()
+
+    def step(src=x):
+        plan.analysis(src, fw, fs)
+        plan.synthesis(fw, fs, out)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    plan.profile(True)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    stats = plan.stage_stats()
+    plan.profile(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        ms = float(t.item())
+    value = world * a.batch * a.steps / (ms / 1000.0)
+
+    # dominant kernel and its roofline
+    dom = max(stats, key=lambda k: stats[k]["ms"])
+    sd = stats[dom]
+    peaks = measured_peaks()
+    if dom in ("leg_anal", "leg_synth"):
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        if a.precision == "fp32":
+            peak = SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12
+            pdesc = "derived: %d SMs x %d FP32 lanes x 2 flop/FMA x %.0f MHz" % (SM_COUNT, FP32_LANES, mhz)
+        else:
+            peak = SM_COUNT * 2 * 2 * mhz * 1e6 / 1e12
+            pdesc = "derived: %d SMs x 2 FP64 FMA/clk x 2 flop x %.0f MHz (assumed FP64 rate)" % (SM_COUNT, mhz)
+        achieved = sd["flops"] / (sd["ms"] / 1000.0) / 1e12 if sd["ms"] > 0 else 0.0
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": dom, "peak_source": pdesc,
+                "flops_counted": "4 per (l, m, ring, map) product + 4 per recurrence value",
+                "avg_launch_ms": sd["ms"] / max(sd["timed"], 1)}
+    else:
+        peak = peaks.get("hbm_gbs", 6800.0)
+        achieved = sd["bytes"] / (sd["ms"] / 1000.0) / 1e9 if sd["ms"] > 0 else 0.0
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": dom, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "avg_launch_ms": sd["ms"] / max(sd["timed"], 1)}
+    total_ms = sum(s["ms"] for s in stats.values())
+    stage_share = {k: {"share": (s["ms"] / total_ms if total_ms else 0.0), "ms_per_step": s["ms"] / a.steps,
+                       "launches_per_step": s["launches"] / a.steps} for k, s in stats.items()}
+    launches = sum(s["launches"] for s in stats.values())
+
+    res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32" if a.precision == "fp32" else "f64", "data": "synthetic", "config": config(a),
+           "gpu_launches": launches, "roofline": roof, "stages": stage_share, "clocks": clk}
+
+    # end to end: pinned host maps in, host maps out, copies inside the timed region
+    if not a.skip_e2e:
+        xh = x.cpu().pin_memory()
+        oh = torch.empty_like(out, device="cpu").pin_memory()
+        xd = torch.empty_like(x)
+        step(xd.copy_(xh, non_blocking=True))
+        oh.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(a.e2e_steps):
+            xd.copy_(xh, non_blocking=True)
+            step(xd)
+            oh.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        res["e2e"] = {"value": world * a.batch * a.e2e_steps / te, "unit": UNIT,
+                      "h2d_bytes_per_step": xh.numel() * xh.element_size(),
+                      "d2h_bytes_per_step": oh.numel() * oh.element_size()}
+
+    if rank == 0 and not a.skip_check:
+        res.update(check_errors(plan, x, fw, fs, out, flm[0], a))
+
+    # the plain FP64 GPU path on the same workload (fewer maps per launch)
+    if rank == 0 and not a.skip_fp64 and a.precision != "fp64":
+        del fw, fs, out
+        nb = a.fp64_batch
+        p64 = Plan(a.L, a.B, a.J_min, batch=nb, real=True, multires=True, precision="fp64")
+        f64 = torch.from_numpy(np.stack([flm[:nb].real, flm[:nb].imag], -1)).cuda().contiguous()
+        x64 = p64.sht_inverse(f64)
+        w64, s64 = p64.empty_wavelets()
+        o64 = p64.empty_map()
+        p64.analysis(x64, w64, s64)
+        p64.synthesis(w64, s64, o64)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        p64.analysis(x64, w64, s64)
+        p64.synthesis(w64, s64, o64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1000.0
+        v64 = nb / t64
+        res["fp64_path"] = {"value": v64, "unit": UNIT, "maps": nb, "ms_per_round_trip": 1000 * t64,
+                            "note": "plain FP64 GPU path, same L/B/J_min, %d maps per launch, 1 timed round trip" % nb}
+        res["speedup_vs_fp64_path"] = value / world / v64
+        del p64
+
+    if rank == 0 and not a.skip_cpu:
+        res["cpu_baseline"] = cpu_baseline(a)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    return 0
+
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        return run_reference(a, rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl")
+    try:
+        return run_gpu(a, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

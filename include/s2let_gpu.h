@@ -115,6 +115,31 @@ int s2let_sht_forward(s2let_plan *plan, const void *f, void *flm, void *stream);
  * Sect. 2.1).  In: flm.  Out: f. */
 int s2let_sht_inverse(s2let_plan *plan, const void *flm, void *f, void *stream);
 
+/* ---- instrumentation (no counterpart in the paper) ----------------------
+ * Stages of the data path; every kernel launch belongs to one of them. */
+#define S2LET_STAGE_RING_FWD 0   /* ring DFT, samples -> F_m(theta_t)           */
+#define S2LET_STAGE_THETA_QUAD 1 /* MW theta quadrature, F_m -> G_m             */
+#define S2LET_STAGE_LEG_ANAL 2   /* Legendre sum over rings (forward transform) */
+#define S2LET_STAGE_LEG_SYNTH 3  /* Legendre sum over degrees (inverse)         */
+#define S2LET_STAGE_RING_INV 4   /* inverse ring DFT, F_m(theta_t) -> samples   */
+#define S2LET_STAGE_PACK 5       /* f_lm layout conversion                     */
+#define S2LET_N_STAGES 6
+
+/* enable = 1: clear the per-stage counters and, until called with enable = 0,
+ * record a CUDA event pair on the call's stream around every kernel launch
+ * (at most 8192 launches are timed; later ones are only counted).
+ * Launch counts are kept whether or not timing is enabled. */
+int s2let_plan_profile(s2let_plan *plan, int enable);
+
+/* Totals for one stage since the last s2let_plan_profile(plan, 1): kernel
+ * launches, device time in ms of the timed launches (this call synchronizes
+ * their events), and the algorithmic FP operations and DRAM bytes those timed
+ * launches stand for (Legendre stages: 4 flops per (l, m, ring, map) product
+ * plus 4 per recurrence value; FFT stages: bytes of their input and output
+ * arrays).  Any output pointer may be NULL. */
+int s2let_plan_stage_stats(s2let_plan *plan, int stage, int64_t *launches, int64_t *timed, double *ms,
+                           double *flops, double *bytes);
+
 /* Short text for a status code. */
 const char *s2let_strerror(int status);
 

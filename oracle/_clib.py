@@ -45,7 +45,7 @@ def lib():
         L.oracle_legendre_column.restype = None
         for name in ("oracle_legendre_inverse", "oracle_legendre_forward"):
             f = getattr(L, name)
-            f.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, dp, dp, dp]
+            f.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, dp, dp, ctypes.c_int, ip, dp]
             f.restype = None
         _lib = L
     return _lib

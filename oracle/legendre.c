@@ -147,13 +147,14 @@ void oracle_legendre_column(int m, int N, double sin_t, double sgn, double y,
 /*
  * Legendre part of the inverse transform, Eq. (harmonicssynthesis):
  *   F_m(theta_t) = sum_{l=|m|}^{N-1} f_lm lambda_{l,m}(theta_t)
- * for m = -(N-1) .. N-1 and t = 0 .. nt-1.  One column lambda_{l,|m|}(theta_t)
- * serves m and -m (lambda_{l,-m} = (-1)^m lambda_lm).
+ * for the n_ord orders m = orders[k] and t = 0 .. nt-1.  One column
+ * lambda_{l,|m|}(theta_t) serves m and -m (lambda_{l,-m} = (-1)^m lambda_lm).
  * flm: complex, interleaved re/im, index l*l + l + m (length N*N).
- * F:   complex, interleaved, [m + N - 1][t], (2N-1) x nt.
+ * F:   complex, interleaved, [k][t], n_ord x nt.
  */
 void oracle_legendre_inverse(int N, const double *flm, int nt, const double *sin_t,
-                             const double *sgn, const double *y, double *F)
+                             const double *sgn, const double *y, int n_ord, const int *orders,
+                             double *F)
 {
     if (N > 8192) return;
 #pragma omp parallel
@@ -161,20 +162,27 @@ void oracle_legendre_inverse(int N, const double *flm, int nt, const double *sin
         double lam[8192];
 #pragma omp for schedule(dynamic, 1)
         for (int am = 0; am < N; ++am) {
+            int kp = -1, kn = -1; /* positions of +am and -am in the list */
+            for (int k = 0; k < n_ord; ++k) {
+                if (orders[k] == am) kp = k;
+                if (am > 0 && orders[k] == -am) kn = k;
+            }
+            if (kp < 0 && kn < 0) continue;
             for (int t = 0; t < nt; ++t) {
                 oracle_legendre_column(am, N, sin_t[t], sgn[t], y[t], lam, 0, 0);
                 for (int s = 0; s < 2; ++s) {
-                    if (s == 1 && am == 0) break;
+                    int k = s ? kn : kp;
+                    if (k < 0) continue;
                     int m = s ? -am : am;
-                    double sgn = (s && (am & 1)) ? -1.0 : 1.0;
+                    double sg = (s && (am & 1)) ? -1.0 : 1.0;
                     double re = 0.0, im = 0.0;
                     for (int l = am; l < N; ++l) {
-                        double v = sgn * lam[l - am];
+                        double v = sg * lam[l - am];
                         size_t idx = (size_t)l * l + l + m;
                         re += flm[2 * idx] * v;
                         im += flm[2 * idx + 1] * v;
                     }
-                    size_t o = (size_t)(m + N - 1) * nt + t;
+                    size_t o = (size_t)k * nt + t;
                     F[2 * o] = re;
                     F[2 * o + 1] = im;
                 }
@@ -188,12 +196,14 @@ void oracle_legendre_inverse(int N, const double *flm, int nt, const double *sin
  * quadrature, Eq. (harmonicsanalysis) made a finite sum by the sampling
  * theorem of Sect. 2.1):
  *   out_lm = sum_{t=0}^{nt-1} lambda_{l,m}(theta_t) G_m(theta_t)
- * for all l < N, |m| <= l.  The caller applies the quadrature factor.
- * G:   complex, interleaved, [m + N - 1][t], (2N-1) x nt.
+ * for the n_ord orders m = orders[k] and l = |m| .. N-1; other entries of out
+ * are left as they are.  The caller applies the quadrature factor.
+ * G:   complex, interleaved, [k][t], n_ord x nt.
  * out: complex, interleaved, index l*l + l + m.
  */
 void oracle_legendre_forward(int N, const double *G, int nt, const double *sin_t,
-                             const double *sgn, const double *y, double *out)
+                             const double *sgn, const double *y, int n_ord, const int *orders,
+                             double *out)
 {
     if (N > 8192) return;
 #pragma omp parallel
@@ -201,8 +211,14 @@ void oracle_legendre_forward(int N, const double *G, int nt, const double *sin_t
         double lam[8192];
 #pragma omp for schedule(dynamic, 1)
         for (int am = 0; am < N; ++am) {
+            int kp = -1, kn = -1;
+            for (int k = 0; k < n_ord; ++k) {
+                if (orders[k] == am) kp = k;
+                if (am > 0 && orders[k] == -am) kn = k;
+            }
+            if (kp < 0 && kn < 0) continue;
             for (int s = 0; s < 2; ++s) {
-                if (s == 1 && am == 0) break;
+                if ((s ? kn : kp) < 0) continue;
                 int m = s ? -am : am;
                 for (int l = am; l < N; ++l) {
                     size_t idx = (size_t)l * l + l + m;
@@ -213,13 +229,14 @@ void oracle_legendre_forward(int N, const double *G, int nt, const double *sin_t
             for (int t = 0; t < nt; ++t) {
                 oracle_legendre_column(am, N, sin_t[t], sgn[t], y[t], lam, 0, 0);
                 for (int s = 0; s < 2; ++s) {
-                    if (s == 1 && am == 0) break;
+                    int k = s ? kn : kp;
+                    if (k < 0) continue;
                     int m = s ? -am : am;
-                    double sgn = (s && (am & 1)) ? -1.0 : 1.0;
-                    size_t o = (size_t)(m + N - 1) * nt + t;
+                    double sg = (s && (am & 1)) ? -1.0 : 1.0;
+                    size_t o = (size_t)k * nt + t;
                     double gre = G[2 * o], gim = G[2 * o + 1];
                     for (int l = am; l < N; ++l) {
-                        double v = sgn * lam[l - am];
+                        double v = sg * lam[l - am];
                         size_t idx = (size_t)l * l + l + m;
                         out[2 * idx] += v * gre;
                         out[2 * idx + 1] += v * gim;

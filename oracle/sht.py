@@ -122,6 +122,24 @@ def _phase_a_theta(a, t, P):
     return expi_pi(np.multiply.outer(np.asarray(a, dtype=np.int64), 2 * np.asarray(t, dtype=np.int64) + 1), P)
 
 
+# The constant matrices of one band-limit are built once per process.
+@functools.lru_cache(maxsize=8)
+def _phase_matrix_phi(N):
+    """e^{i m phi_p}, [m + N - 1, p]."""
+    return _phase_m_phi(m_range(N), np.arange(2 * N - 1), 2 * N - 1)
+
+
+@functools.lru_cache(maxsize=8)
+def _quadrature_matrices(N):
+    """e^{-i a theta_t} [t, a], w(a+b) [a, b] and e^{-i b theta_t} [b, t] on the full circle."""
+    P = 2 * N - 1
+    a = m_range(N)
+    E3 = np.ascontiguousarray(np.conj(_phase_a_theta(a, np.arange(P), P)).T)
+    W = weights(a[:, None] + a[None, :])
+    E5 = np.conj(_phase_a_theta(a, np.arange(P), P))
+    return E3, W, E5
+
+
 def legendre_column(m, N, sin_t, sgn, y):
     """lambda_lm(theta) for l = m..N-1 (m >= 0); cos(theta) = sgn (1 - y)."""
     out = np.zeros(N - m)
@@ -146,33 +164,44 @@ def legendre_at(m, N, t):
     return legendre_column(m, N, s[0], sg[0], y[0])
 
 
-def _legendre_inverse(flm, N, ts):
-    """F_m(theta_t) = sum_l f_lm lambda_lm(theta_t), shape [2N-1 (m), len(ts)]."""
+def _orders(N, orders):
+    m = m_range(N) if orders is None else np.asarray(orders, dtype=np.int64)
+    return m[np.abs(m) <= N - 1]
+
+
+def _legendre_inverse(flm, N, ts, orders=None):
+    """F_m(theta_t) = sum_l f_lm lambda_lm(theta_t), shape [len(orders), len(ts)]."""
+    m = _orders(N, orders)
     s, sg, yy = sin_cos_theta(N, ts)
     fl = np.ascontiguousarray(np.asarray(flm, dtype=complex)[:N * N]).view(np.float64)
-    out = np.zeros((2 * N - 1, len(ts)), dtype=complex)
+    out = np.zeros((len(m), len(ts)), dtype=complex)
+    mi = np.ascontiguousarray(m, dtype=np.int32)
     _clib.lib().oracle_legendre_inverse(N, _clib.dptr(fl), len(ts), _clib.dptr(s),
-                                        _clib.dptr(sg), _clib.dptr(yy),
+                                        _clib.dptr(sg), _clib.dptr(yy), len(mi), _clib.iptr(mi),
                                         _clib.dptr(out.view(np.float64)))
     return out
 
 
-def _legendre_forward(G, N):
-    """out_lm = sum_t lambda_lm(theta_t) G_m(theta_t); G has shape [2N-1 (m), N (t)]."""
+def _legendre_forward(G, N, orders=None):
+    """out_lm = sum_t lambda_lm(theta_t) G_m(theta_t); G has shape [len(orders), N (t)].
+    Coefficients of orders not listed are 0."""
+    m = _orders(N, orders)
     s, sg, yy = sin_cos_theta(N, np.arange(N))
     G = np.ascontiguousarray(G, dtype=complex)
     out = np.zeros(N * N, dtype=complex)
+    mi = np.ascontiguousarray(m, dtype=np.int32)
     _clib.lib().oracle_legendre_forward(N, _clib.dptr(G.view(np.float64)), N, _clib.dptr(s),
-                                        _clib.dptr(sg), _clib.dptr(yy),
+                                        _clib.dptr(sg), _clib.dptr(yy), len(mi), _clib.iptr(mi),
                                         _clib.dptr(out.view(np.float64)))
     return out
 
 
-def inverse(flm, N, real=False):
-    """Eq. (harmonicssynthesis): f(theta_t, phi_p) = sum_{l<N} sum_{|m|<=l} f_lm Y_lm."""
-    m = m_range(N)
-    F = _legendre_inverse(flm, N, np.arange(N))          # [m, t]
-    E = _phase_m_phi(m, np.arange(2 * N - 1), 2 * N - 1)  # e^{i m phi_p}, [m, p]
+def inverse(flm, N, real=False, orders=None):
+    """Eq. (harmonicssynthesis): f(theta_t, phi_p) = sum_{l<N} sum_{|m|<=l} f_lm Y_lm.
+    With `orders`, only the terms of those orders m are summed."""
+    m = _orders(N, orders)
+    F = _legendre_inverse(flm, N, np.arange(N), m)       # [m, t]
+    E = _phase_matrix_phi(N)[m + N - 1]                   # e^{i m phi_p}, [m, p]
     f = F.T @ E                                           # [t, p]
     return f.real.copy() if real else f
 
@@ -181,7 +210,7 @@ def inverse_at(flm, N, ts, ps):
     """The inverse transform evaluated only at rings ts and longitudes ps."""
     m = m_range(N)
     F = _legendre_inverse(flm, N, np.asarray(ts))
-    E = _phase_m_phi(m, np.asarray(ps), 2 * N - 1)
+    E = _phase_matrix_phi(N)[:, np.asarray(ps)]
     return F.T @ E
 
 
@@ -194,13 +223,13 @@ def _theta_quadrature(Fm, N, par):
     Ft[:, :N] = Fm
     if N > 1:
         Ft[:, N:] = par * Fm[:, N - 2::-1]
+    E3, W, E5 = _quadrature_matrices(N)
     # (3) F_{m,a} = (1/P) sum_{t<P} F~_m(theta_t) e^{-i a theta_t},  |a| <= N-1
-    a = m_range(N)
-    Fma = Ft @ np.conj(_phase_a_theta(a, np.arange(P), P)).T / P   # [m, a]
+    Fma = Ft @ E3 / P                                     # [m, a]
     # (4) H_{m,b} = sum_a F_{m,a} w(a+b)
-    H = Fma @ weights(a[:, None] + a[None, :])            # [m, b]
+    H = Fma @ W                                           # [m, b]
     # (5) h_m(theta_t) = sum_b H_{m,b} e^{-i b theta_t},  t < P
-    h = H @ np.conj(_phase_a_theta(a, np.arange(P), P))   # [m, t]
+    h = H @ E5                                            # [m, t]
     # (6) fold: G_m(theta_t) = h_m(theta_t) + (-1)^m h_m(theta_{P-1-t}) for t < N-1
     G = h[:, :N].copy()
     if N > 1:
@@ -212,17 +241,19 @@ def _parity(m):
     return np.where(np.asarray(m) % 2 == 0, 1.0, -1.0).reshape(-1, 1)
 
 
-def forward(f, N):
-    """Eq. (harmonicsanalysis) by the exact MW quadrature; returns f_lm, l < N."""
+def forward(f, N, orders=None):
+    """Eq. (harmonicsanalysis) by the exact MW quadrature; returns f_lm, l < N.
+    With `orders`, only coefficients of those orders m are computed (others 0):
+    every step below acts on each order separately."""
     P = 2 * N - 1
     f = np.asarray(f)
     assert f.shape == (N, P)
-    m = m_range(N)
+    m = _orders(N, orders)
     # (1) F_m(theta_t) = (1/P) sum_p f(theta_t, phi_p) e^{-i m phi_p}
-    Fm = (f @ np.conj(_phase_m_phi(m, np.arange(P), P)).T / P).T  # [m, t]
+    Fm = (f @ np.conj(_phase_matrix_phi(N)[m + N - 1]).T / P).T  # [m, t]
     G = _theta_quadrature(Fm, N, _parity(m))
     # (7) f_lm = (2 pi / P) sum_{t<N} lambda_lm(theta_t) G_m(theta_t)
-    return (2.0 * math.pi / P) * _legendre_forward(G, N)
+    return (2.0 * math.pi / P) * _legendre_forward(G, N, m)
 
 
 def forward_m(f, N, m):
@@ -240,13 +271,31 @@ def forward_m(f, N, m):
     return (2.0 * math.pi / P) * out
 
 
+def inverse_m(xlm, N, m, ts=None):
+    """Order-m part of the inverse transform before the ring DFT:
+    F_m(theta_t) = sum_{l=|m|}^{N-1} x_l lambda_lm(theta_t); xlm[l - |m|] = x_l."""
+    ts = np.arange(N) if ts is None else np.asarray(ts)
+    s, sg, yy = sin_cos_theta(N, ts)
+    am = abs(m)
+    sgn = (-1.0) ** am if m < 0 else 1.0
+    out = np.zeros(len(ts), dtype=complex)
+    for i in range(len(ts)):
+        out[i] = sgn * np.dot(legendre_column(am, N, s[i], sg[i], yy[i]), xlm)
+    return out
+
+
+def ring_synthesis_m(Fm, N, m):
+    """The order-m term of the inverse ring DFT: F_m(theta_t) e^{i m phi_p}, shape (N, 2N-1)."""
+    return np.outer(Fm, _phase_m_phi([m], np.arange(2 * N - 1), 2 * N - 1)[0])
+
+
 # ---------------------------------------------------------------- adjoints
 def inverse_adjoint(g, N):
     """Conjugate transpose of inverse(): out_lm = sum_{t,p} g(theta_t, phi_p)
     lambda_lm(theta_t) e^{-i m phi_p}."""
     m = m_range(N)
     g = np.asarray(g, dtype=complex)
-    Gm = (g @ np.conj(_phase_m_phi(m, np.arange(2 * N - 1), 2 * N - 1)).T).T  # [m, t]
+    Gm = (g @ np.conj(_phase_matrix_phi(N)).T).T          # [m, t]
     return _legendre_forward(Gm, N)
 
 

@@ -55,12 +55,15 @@ def analysis_lm(flm, L, B, J0, multires=True):
     return scal, wav
 
 
-def analysis(f, L, B, J0, multires=True, real=True):
-    flm = sht.forward(f, L)
+def analysis(f, L, B, J0, multires=True, real=True, orders=None):
+    """With `orders`, only the parts of those orders m are computed: every step
+    acts on each order separately, so the result is the order-m component of
+    the full analysis (used to time a bounded sample of one map)."""
+    flm = sht.forward(f, L, orders)
     scal_lm, wav_lm = analysis_lm(flm, L, B, J0, multires)
     n_scal, n_wav = kernels.bandlimits(L, B, J0, multires)
-    f_scal = sht.inverse(scal_lm, n_scal, real=real)
-    f_wav = [sht.inverse(w, n, real=real) for w, n in zip(wav_lm, n_wav)]
+    f_scal = sht.inverse(scal_lm, n_scal, real=real, orders=orders)
+    f_wav = [sht.inverse(w, n, real=real, orders=orders) for w, n in zip(wav_lm, n_wav)]
     return f_wav, f_scal
 
 
@@ -80,12 +83,13 @@ def synthesis_lm(scal_lm, wav_lm, L, B, J0):
     return flm
 
 
-def synthesis(f_wav, f_scal, L, B, J0, multires=True, real=True):
+def synthesis(f_wav, f_scal, L, B, J0, multires=True, real=True, orders=None):
+    """With `orders`, only the parts of those orders m (see analysis())."""
     n_scal, n_wav = kernels.bandlimits(L, B, J0, multires)
-    scal_lm = sht.forward(f_scal, n_scal)
-    wav_lm = [sht.forward(w, n) for w, n in zip(f_wav, n_wav)]
+    scal_lm = sht.forward(f_scal, n_scal, orders)
+    wav_lm = [sht.forward(w, n, orders) for w, n in zip(f_wav, n_wav)]
     flm = synthesis_lm(scal_lm, wav_lm, L, B, J0)
-    return sht.inverse(flm, L, real=real)
+    return sht.inverse(flm, L, real=real, orders=orders)
 
 
 def analysis_adjoint(g_wav, g_scal, L, B, J0, multires=True, real=True):

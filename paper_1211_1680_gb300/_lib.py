@@ -38,8 +38,13 @@ SIGNATURES = {
     "s2let_adjoint": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "s2let_sht_forward": (_i, [_vp, _vp, _vp, _vp]),
     "s2let_sht_inverse": (_i, [_vp, _vp, _vp, _vp]),
+    "s2let_plan_profile": (_i, [_vp, _i]),
+    "s2let_plan_stage_stats": (_i, [_vp, _i, _i64p, _i64p, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "s2let_strerror": (ctypes.c_char_p, [_i]),
 }
+
+STAGES = ["ring_fwd", "theta_quad", "leg_anal", "leg_synth", "ring_inv", "pack"]
 
 _lib = None
 

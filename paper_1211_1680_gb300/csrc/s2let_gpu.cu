@@ -83,8 +83,20 @@ struct s2let_plan {
     std::vector<void *> kfac;               // per map: scaling first, then scales J0..J (R[L])
     void *F = nullptr, *flm = nullptr;      // workspace
     std::vector<void *> owned;
+    // instrumentation
+    struct Rec {
+        int stage;
+        cudaEvent_t a, b;
+        double flops, bytes;
+    };
+    mutable bool prof = false;
+    mutable std::vector<Rec> recs;
+    mutable std::vector<cudaEvent_t> evpool;
+    mutable size_t evnext = 0;
+    mutable int64_t launches[S2LET_N_STAGES] = {0, 0, 0, 0, 0, 0};
     ~s2let_plan()
     {
+        for (cudaEvent_t e : evpool) cudaEventDestroy(e);
         for (void *p : owned) cudaFree(p);
     }
 };
@@ -99,6 +111,36 @@ int64_t map_elems(const s2let_plan *p, int N) { return (int64_t)N * (2 * N - 1) 
     do {                                                       \
         if (cudaGetLastError() != cudaSuccess) return S2LET_ERR_CUDA; \
     } while (0)
+
+// Counts a launch of `stage` and, when profiling, brackets it with an event pair.
+struct StageScope {
+    const s2let_plan *p;
+    cudaStream_t st;
+    long slot = -1;
+    StageScope(const s2let_plan *p_, int stage, cudaStream_t st_, double flops, double bytes) : p(p_), st(st_)
+    {
+        p->launches[stage]++;
+        if (p->prof && p->evnext + 2 <= p->evpool.size()) {
+            s2let_plan::Rec r{stage, p->evpool[p->evnext], p->evpool[p->evnext + 1], flops, bytes};
+            p->evnext += 2;
+            slot = (long)p->recs.size();
+            p->recs.push_back(r);
+            cudaEventRecord(r.a, st);
+        }
+    }
+    ~StageScope()
+    {
+        if (slot >= 0) cudaEventRecord(p->recs[slot].b, st);
+    }
+};
+
+double legendre_flops(const s2let_plan *p, int N)
+{
+    const double pairs = p->cplx ? (double)N * N : 0.5 * (double)N * (N + 1);
+    return 4.0 * pairs * N * p->batch + 4.0 * 0.5 * (double)N * (N + 1) * N;
+}
+double spectrum_bytes(const s2let_plan *p, int N) { return (double)p->batch * nmi(p, N) * N * 2 * elem_size(p); }
+double map_bytes(const s2let_plan *p, int N) { return (double)p->batch * map_elems(p, N) * elem_size(p); }
 
 template <typename R> const FftTab<cplx_t<R>> &fft_tab(const BandDev &b);
 template <> const FftTab<double2> &fft_tab<double>(const BandDev &b) { return b.fd; }
@@ -133,6 +175,7 @@ int run_ring_fwd(const s2let_plan *p, const BandDev &bd, const void *f, void *F,
     const auto &T = fft_tab<R>(bd);
     const size_t sm = (size_t)bd.M * sizeof(cplx_t<R>);
     const int th = fft_threads(bd.M);
+    StageScope sc(p, S2LET_STAGE_RING_FWD, st, 0.0, map_bytes(p, bd.N) + spectrum_bytes(p, bd.N));
     if (p->cplx) {
         k_ring_fwd_cplx<R><<<dim3(bd.N, p->batch), th, sm, st>>>((const cplx_t<R> *)f, (cplx_t<R> *)F, (R)scale, T);
     } else {
@@ -148,6 +191,7 @@ int run_ring_inv(const s2let_plan *p, const BandDev &bd, const void *F, void *f,
     const auto &T = fft_tab<R>(bd);
     const size_t sm = (size_t)bd.M * sizeof(cplx_t<R>);
     const int th = fft_threads(bd.M);
+    StageScope sc(p, S2LET_STAGE_RING_INV, st, 0.0, map_bytes(p, bd.N) + spectrum_bytes(p, bd.N));
     if (p->cplx) {
         k_ring_inv_cplx<R><<<dim3(bd.N, p->batch), th, sm, st>>>((const cplx_t<R> *)F, (cplx_t<R> *)f, (R)scale, T);
     } else {
@@ -163,6 +207,7 @@ int run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream_t
     const int n = nmi(p, bd.N);
     const int off = p->cplx ? bd.N - 1 : 0;
     const int th = fft_threads(bd.M);
+    StageScope sc(p, S2LET_STAGE_THETA_QUAD, st, 0.0, 2.0 * spectrum_bytes(p, bd.N));
     if (p->quad64) {
         const size_t sm = (size_t)bd.M * sizeof(double2);
         k_theta_quad<double, R, 16><<<dim3(n, p->batch), th, sm, st>>>((const cplx_t<R> *)F, (cplx_t<R> *)F, n, off,
@@ -193,6 +238,7 @@ int run_synth(const s2let_plan *p, const BandDev &bd, const void *src, const voi
               cudaStream_t st)
 {
     constexpr int BT = std::is_same<R, double>::value ? 4 : 8;
+    StageScope sc(p, S2LET_STAGE_LEG_SYNTH, st, legendre_flops(p, bd.N), 0.0);
     if (p->cplx) launch_synth<R, BT, true>(p, bd, src, kfac, scale, dst, st);
     else launch_synth<R, BT, false>(p, bd, src, kfac, scale, dst, st);
     S2_LAUNCH_CHECK();
@@ -226,6 +272,7 @@ int run_anal(const s2let_plan *p, const BandDev &bd, const void *G, const void *
              void *dst, cudaStream_t st)
 {
     constexpr int BT = std::is_same<R, double>::value ? 2 : 4;
+    StageScope sc(p, S2LET_STAGE_LEG_ANAL, st, legendre_flops(p, bd.N), 0.0);
     if (p->cplx) launch_anal_rpt<R, BT, true>(p, bd, G, kfac, scale, acc, dst, st);
     else launch_anal_rpt<R, BT, false>(p, bd, G, kfac, scale, acc, dst, st);
     S2_LAUNCH_CHECK();
@@ -293,6 +340,7 @@ template <typename R> int sht_forward_t(s2let_plan *p, const void *f, void *flm,
     int e = sht_fwd_to_rect<R>(p, f, st);
     if (e) return e;
     const size_t n = (size_t)p->batch * p->L * p->L;
+    StageScope sc(p, S2LET_STAGE_PACK, st, 0.0, 0.0);
     k_pack<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const cplx_t<R> *)p->flm, (cplx_t<R> *)flm, p->L,
                                                            p->cplx, p->batch);
     S2_LAUNCH_CHECK();
@@ -303,8 +351,11 @@ template <typename R> int sht_inverse_t(s2let_plan *p, const void *flm, void *f,
 {
     const BandDev &bd = p->bands.at(p->L);
     const size_t n = (size_t)p->batch * nmi(p, p->L) * p->L;
+    {
+    StageScope sc(p, S2LET_STAGE_PACK, st, 0.0, 0.0);
     k_unpack<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const cplx_t<R> *)flm, (cplx_t<R> *)p->flm, p->L,
                                                              p->cplx, p->batch);
+    }
     S2_LAUNCH_CHECK();
     int e;
     if ((e = run_synth<R>(p, bd, p->flm, nullptr, 1.0, p->F, st))) return e;
@@ -645,6 +696,48 @@ int s2let_sht_inverse(s2let_plan *p, const void *flm, void *f, void *stream)
 {
     if (!p || !f || !flm) return S2LET_ERR_ARG;
     return S2_DISPATCH(sht_inverse_t, p, flm, f, (cudaStream_t)stream);
+}
+
+int s2let_plan_profile(s2let_plan *p, int enable)
+{
+    if (!p) return S2LET_ERR_ARG;
+    if (enable) {
+        const size_t want = 2 * 8192;
+        while (p->evpool.size() < want) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return S2LET_ERR_CUDA;
+            p->evpool.push_back(e);
+        }
+        p->recs.clear();
+        p->evnext = 0;
+        for (int i = 0; i < S2LET_N_STAGES; ++i) p->launches[i] = 0;
+    }
+    p->prof = enable != 0;
+    return S2LET_OK;
+}
+
+int s2let_plan_stage_stats(s2let_plan *p, int stage, int64_t *launches, int64_t *timed, double *ms, double *flops,
+                           double *bytes)
+{
+    if (!p || stage < 0 || stage >= S2LET_N_STAGES) return S2LET_ERR_ARG;
+    double t = 0.0, f = 0.0, b = 0.0;
+    int64_t n = 0;
+    for (const auto &r : p->recs) {
+        if (r.stage != stage) continue;
+        if (cudaEventSynchronize(r.b) != cudaSuccess) return S2LET_ERR_CUDA;
+        float x = 0.0f;
+        if (cudaEventElapsedTime(&x, r.a, r.b) != cudaSuccess) return S2LET_ERR_CUDA;
+        t += x;
+        f += r.flops;
+        b += r.bytes;
+        ++n;
+    }
+    if (launches) *launches = p->launches[stage];
+    if (timed) *timed = n;
+    if (ms) *ms = t;
+    if (flops) *flops = f;
+    if (bytes) *bytes = b;
+    return S2LET_OK;
 }
 
 const char *s2let_strerror(int s)

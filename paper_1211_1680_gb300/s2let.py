@@ -72,6 +72,25 @@ class Plan:
         except Exception:
             pass
 
+    # ---------------------------------------------------------------- instrumentation
+    def profile(self, enable=True):
+        """Start (clearing counters) or stop per-stage event timing."""
+        check("s2let_plan_profile", _lib.lib().s2let_plan_profile(self._h, 1 if enable else 0))
+
+    def stage_stats(self):
+        """{stage: dict(launches, timed, ms, flops, bytes)} since profile(True)."""
+        out = {}
+        for i, name in enumerate(_lib.STAGES):
+            n = ctypes.c_int64()
+            tm = ctypes.c_int64()
+            ms = ctypes.c_double()
+            fl = ctypes.c_double()
+            by = ctypes.c_double()
+            check("s2let_plan_stage_stats", _lib.lib().s2let_plan_stage_stats(
+                self._h, i, ctypes.byref(n), ctypes.byref(tm), ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(by)))
+            out[name] = dict(launches=n.value, timed=tm.value, ms=ms.value, flops=fl.value, bytes=by.value)
+        return out
+
     # ---------------------------------------------------------------- shapes
     def map_shape(self, N):
         s = (self.batch, N, 2 * N - 1)

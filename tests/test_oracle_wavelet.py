@@ -123,3 +123,33 @@ def test_white_noise_variance():
     for i, p in enumerate(psi):
         if n_wav[i] >= 16:
             assert acc[i] == pytest.approx(np.sum(p ** 2), rel=0.08)
+
+
+def test_round_trip_by_orders():
+    """Analysis and synthesis restricted to a set of orders give exactly the
+    order-restricted components of the full transforms."""
+    L, B, J0 = 12, 2, 1
+    f = sht.inverse(inputs.random_flm(L, 17, real=True), L, real=True)
+    fw, fs = wavelet.analysis(f, L, B, J0, True, True)
+    allm = list(range(-(L - 1), L))
+    fw_o, fs_o = wavelet.analysis(f, L, B, J0, True, False, orders=allm)
+    assert np.max(np.abs(fs_o - fs)) < 1e-13
+    for a, b in zip(fw_o, fw):
+        assert np.max(np.abs(a - b)) < 1e-13
+    sub = [-5, 0, 3, 11]
+    fw_s, fs_s = wavelet.analysis(f, L, B, J0, True, False, orders=sub)
+    rec = wavelet.synthesis(fw_s, fs_s, L, B, J0, True, False, orders=sub)
+    flm = sht.forward(f, L)
+    keep = np.zeros(L * L, complex)
+    for l in range(L):
+        for m in sub:
+            if abs(m) <= l:
+                keep[l * l + l + m] = flm[l * l + l + m]
+    assert np.max(np.abs(rec - sht.inverse(keep, L))) < 1e-13
+    # the sampled wavelet maps are the order-restricted parts of the full ones
+    n_scal, n_wav = kernels.bandlimits(L, B, J0, True)
+    for w_s, w, n in zip(fw_s, fw, n_wav):
+        ref = sht.inverse(np.where(np.isin(np.arange(n * n) - np.repeat(np.arange(n), 2 * np.arange(n) + 1) ** 2
+                                           - np.repeat(np.arange(n), 2 * np.arange(n) + 1), sub),
+                                   sht.forward(w, n), 0), n)
+        assert np.max(np.abs(w_s - ref)) < 1e-13
