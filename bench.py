@@ -32,6 +32,11 @@ METRIC = "wavelet round-trips/s, L=2048x64 maps, vs plain FP64 GPU path; max err
 UNIT = "map round-trips/s"
 SM_COUNT = 152
 FP32_LANES = 128
+FLOPS_COUNTED = {
+    "leg_anal": "4 per (l, m, ring, map) product + 4 per recurrence value (l, m, ring)",
+    "leg_synth": "4 per (l, m, ring, map) product + 4 per recurrence value (l, m, ring)",
+    "theta_quad": "2 N^2 per real column (2 per map and order): the dense product G = Q F",
+}
 
 
 def parse():
@@ -41,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
-    ap.add_argument("--quad-fp32", action="store_true", help="theta quadrature in FP32 (FP32 plans)")
+    ap.add_argument("--quad-fft64", action="store_true", help="FP32 plans: theta quadrature by FP64 FFTs")
     ap.add_argument("--L", type=int, default=2048)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--B", type=int, default=2)
@@ -60,7 +65,7 @@ def config(a):
     return {"workload": "real maps, L=%d, B=%d, J_min=%d, multiresolution, %d maps per GPU, f_lm ~ C_l=1/(l(l+1))"
                         % (a.L, a.B, a.J_min, a.batch),
             "L": a.L, "B": a.B, "J_min": a.J_min, "maps_per_gpu": a.batch, "multires": True, "signal": "real",
-            "precision": a.precision + ("+quad_fp32" if a.quad_fp32 else ""),
+            "precision": a.precision + ("+quad_fft64" if a.quad_fft64 else ""),
             "l2": "inputs larger than L2 (map batch %.2f GB)" % (a.batch * a.L * (2 * a.L - 1)
                                                                    * (4 if a.precision == "fp32" else 8) / 1e9)}
 
@@ -233,7 +238,7 @@ def run_gpu(a, rank, world, local_rank):
     seeds = [3000 + rank * a.batch + i for i in range(a.batch)]
     flm = inputs.random_flm_batch(a.L, seeds, real=True, kind="cl")
     plan = Plan(a.L, a.B, a.J_min, batch=a.batch, real=True, multires=True, precision=a.precision,
-                quad_fp32=a.quad_fp32)
+                quad_fft64=a.quad_fft64)
     flm_d = torch.from_numpy(np.stack([flm.real, flm.imag], -1)).to(device="cuda", dtype=plan.dtype).contiguous()
     x = plan.sht_inverse(flm_d)
     del flm_d
@@ -276,18 +281,20 @@ def run_gpu(a, rank, world, local_rank):
     dom = max(stats, key=lambda k: stats[k]["ms"])
     sd = stats[dom]
     peaks = measured_peaks()
-    if dom in ("leg_anal", "leg_synth"):
+    if sd["flops"] > 0:
+        # a contraction stage: FP32 (or FP64) FMA pipe; peak derived from unit counts and clock
         mhz = peaks.get("sm_max_mhz", 2070.0)
         if a.precision == "fp32":
             peak = SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12
-            pdesc = "derived: %d SMs x %d FP32 lanes x 2 flop/FMA x %.0f MHz" % (SM_COUNT, FP32_LANES, mhz)
+            pdesc = "derived: %d SMs x %d FP32 lanes x 2 flop/FMA x %.0f MHz (max SM clock)" % (
+                SM_COUNT, FP32_LANES, mhz)
         else:
             peak = SM_COUNT * 2 * 2 * mhz * 1e6 / 1e12
             pdesc = "derived: %d SMs x 2 FP64 FMA/clk x 2 flop x %.0f MHz (assumed FP64 rate)" % (SM_COUNT, mhz)
         achieved = sd["flops"] / (sd["ms"] / 1000.0) / 1e12 if sd["ms"] > 0 else 0.0
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "kernel": dom, "peak_source": pdesc,
-                "flops_counted": "4 per (l, m, ring, map) product + 4 per recurrence value",
+                "flops_counted": FLOPS_COUNTED.get(dom, ""),
                 "avg_launch_ms": sd["ms"] / max(sd["timed"], 1)}
     else:
         peak = peaks.get("hbm_gbs", 6800.0)
@@ -295,6 +302,14 @@ def run_gpu(a, rank, world, local_rank):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None, "kernel": dom, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                 "avg_launch_ms": sd["ms"] / max(sd["timed"], 1)}
+    # every contraction stage against the same pipe peak, for context
+    pipe = roof["peak"] if roof["bound"] == "alu" else SM_COUNT * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) / 1e6
+    roof["all_stages"] = {k: {"ms_per_step": v["ms"] / a.steps,
+                              "tflops": (v["flops"] / (v["ms"] / 1000.0) / 1e12 if v["ms"] > 0 and v["flops"] else None),
+                              "frac_of_pipe": (v["flops"] / (v["ms"] / 1000.0) / 1e12 / pipe
+                                               if v["ms"] > 0 and v["flops"] else None),
+                              "gbs": (v["bytes"] / (v["ms"] / 1000.0) / 1e9 if v["ms"] > 0 and v["bytes"] else None)}
+                          for k, v in stats.items() if v["launches"]}
     total_ms = sum(s["ms"] for s in stats.values())
     stage_share = {k: {"share": (s["ms"] / total_ms if total_ms else 0.0), "ms_per_step": s["ms"] / a.steps,
                        "launches_per_step": s["launches"] / a.steps} for k, s in stats.items()}

@@ -53,11 +53,13 @@ extern "C" {
 #define S2LET_COMPLEX 0x1        /* complex maps                               */
 #define S2LET_MULTIRES 0x2       /* multiresolution band-limits, Sect. 3.1     */
 #define S2LET_PREC_FP64 0x00     /* every stage in FP64                        */
-#define S2LET_PREC_FP32 0x10     /* FP32 storage and Legendre sums, float-float
-                                    recurrence, FP64 seeds and theta quadrature */
+#define S2LET_PREC_FP32 0x10     /* FP32 storage and sums, float-float Legendre
+                                    recurrence, FP64 seeds; theta quadrature as a
+                                    dense FP32 product with its matrix built in
+                                    FP64                                       */
 #define S2LET_PREC_MASK 0xf0
-#define S2LET_QUAD_FP32 0x100    /* FP32 plans only: run the theta quadrature in
-                                    FP32 instead of FP64                       */
+#define S2LET_QUAD_FFT64 0x100   /* FP32 plans only: theta quadrature by FP64 FFTs
+                                    instead of the dense FP32 product          */
 
 typedef struct s2let_plan s2let_plan;
 

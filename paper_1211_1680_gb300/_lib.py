@@ -20,7 +20,7 @@ S2LET_COMPLEX = 0x1
 S2LET_MULTIRES = 0x2
 S2LET_PREC_FP64 = 0x00
 S2LET_PREC_FP32 = 0x10
-S2LET_QUAD_FP32 = 0x100
+S2LET_QUAD_FFT64 = 0x100
 
 # every symbol the header declares, with (restype, argtypes)
 _vp = ctypes.c_void_p

@@ -219,9 +219,10 @@ __global__ void k_ring_inv_cplx(const cplx_t<R> *__restrict__ F, cplx_t<R> *__re
 // DFTs (Bluestein) with a phase; (c) is a circular convolution of length M.
 // The linear map x -> G is real and symmetric, so the same kernel also applies
 // its transpose.  Q is the compute type (FP64 by default), R the storage type.
+// parity < 0: sigma from m = mi - m_offset; parity 0 / 1: sigma = +1 / -1 for every row.
 template <typename Q, typename R, int VPT>
 __global__ void k_theta_quad(const cplx_t<R> *__restrict__ Fin, cplx_t<R> *__restrict__ Gout,
-                             int nmi, int m_offset, Q qscale, FftTab<cplx_t<Q>> T)
+                             int nmi, int m_offset, Q qscale, FftTab<cplx_t<Q>> T, int parity)
 {
     using C = cplx_t<Q>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -229,7 +230,7 @@ __global__ void k_theta_quad(const cplx_t<R> *__restrict__ Fin, cplx_t<R> *__res
     const int N = T.N, P = T.P, M = T.M;
     const int mi = blockIdx.x, b = blockIdx.y;
     const int m = mi - m_offset;
-    const Q sigma = (m & 1) ? (Q)-1 : (Q)1;
+    const Q sigma = (parity < 0 ? (m & 1) : parity) ? (Q)-1 : (Q)1;
     const cplx_t<R> *x = Fin + ((size_t)b * nmi + mi) * N;
     cplx_t<R> *g = Gout + ((size_t)b * nmi + mi) * N;
     const Q invM = (Q)1 / (Q)M;

@@ -251,9 +251,12 @@ __global__ void __launch_bounds__(TT) k_leg_synth(const cplx_t<R> *__restrict__ 
 // ---------------------------------------------------------------- analysis (S3)
 // out_l = scale * kfac[l] * sum_t lambda_{l|m|}(theta_t) G[b][mi(m)][t], written
 // (or added, when accumulate) to dst[b][mi_dst(m)][l], l = |m|..N-1.  One block
-// holds every ring of one order (RPT rings per thread) and one batch tile;
-// the sum over rings is a warp-shuffle reduction per degree.
-template <typename R, int BT, bool CPLX, int RPT, int TPB>
+// holds every ring of one order (RPT rings per thread) and one batch tile.
+// Degrees are processed in chunks of LCH; each lane accumulates V = LCH x
+// (values per degree) partial sums over its rings, then a transposed butterfly
+// (each shuffle step halves the values a lane holds) sums them over the warp
+// with V - V/32 shuffles, and the warps' totals are added in shared memory.
+template <typename R, int BT, bool CPLX, int RPT, int TPB, int V>
 __global__ void __launch_bounds__(TPB) k_leg_anal(const cplx_t<R> *__restrict__ G, int N,
                                                   const R *__restrict__ kfac, R scale, int accumulate,
                                                   cplx_t<R> *__restrict__ dst, int ldd, int nmi_dst,
@@ -261,10 +264,13 @@ __global__ void __launch_bounds__(TPB) k_leg_anal(const cplx_t<R> *__restrict__ 
 {
     using C = cplx_t<R>;
     using Rec = RecT<R>;
-    constexpr int LCH = 8;
     constexpr int NS = CPLX ? 2 : 1;
+    constexpr int PER_L = NS * BT * 2;
+    constexpr int LCH = V / PER_L;
+    static_assert(V % 32 == 0 && LCH >= 1 && LCH * PER_L == V, "chunk shape");
     constexpr int NW = TPB / 32;
-    __shared__ R red[NW][LCH][NS][BT][2];
+    constexpr int VPL = V / 32;
+    __shared__ R red[NW][V];
     __shared__ typename Rec::Coef sc[LCH];
 
     const int m = blockIdx.x;
@@ -306,53 +312,60 @@ __global__ void __launch_bounds__(TPB) k_leg_anal(const cplx_t<R> *__restrict__ 
             if (l0 + lc < N) sc[lc] = tab.coef[(size_t)m * tab.ldc + l0 + lc];
         __syncthreads();
         const int nl = min(LCH, N - l0);
-        for (int lc = 0; lc < nl; ++lc) {
-            const int l = l0 + lc;
-            R part[NS][BT][2];
+        R part[V];
 #pragma unroll
-            for (int s = 0; s < NS; ++s)
+        for (int v = 0; v < V; ++v) part[v] = (R)0;
 #pragma unroll
-                for (int i = 0; i < BT; ++i) part[s][i][0] = part[s][i][1] = (R)0;
+        for (int lc = 0; lc < LCH; ++lc) {
+            if (lc < nl) {
+                const int l = l0 + lc;
 #pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                R lam;
-                if (l < myls[k]) {
-                    lam = (R)0;
-                } else if (l == myls[k]) {
-                    rec[k].seed(tab.seed[(size_t)m * N + threadIdx.x + k * TPB]);
-                    lam = rec[k].value();
-                } else {
-                    lam = rec[k].step(sc[lc]);
+                for (int k = 0; k < RPT; ++k) {
+                    R lam;
+                    if (l < myls[k]) {
+                        lam = (R)0;
+                    } else if (l == myls[k]) {
+                        rec[k].seed(tab.seed[(size_t)m * N + threadIdx.x + k * TPB]);
+                        lam = rec[k].value();
+                    } else {
+                        lam = rec[k].step(sc[lc]);
+                    }
+#pragma unroll
+                    for (int s = 0; s < NS; ++s)
+#pragma unroll
+                        for (int i = 0; i < BT; ++i) {
+                            part[((lc * NS + s) * BT + i) * 2 + 0] += lam * g[k][s][i][0];
+                            part[((lc * NS + s) * BT + i) * 2 + 1] += lam * g[k][s][i][1];
+                        }
                 }
-#pragma unroll
-                for (int s = 0; s < NS; ++s)
-#pragma unroll
-                    for (int i = 0; i < BT; ++i) {
-                        part[s][i][0] += lam * g[k][s][i][0];
-                        part[s][i][1] += lam * g[k][s][i][1];
-                    }
             }
-#pragma unroll
-            for (int s = 0; s < NS; ++s)
-#pragma unroll
-                for (int i = 0; i < BT; ++i)
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        R v = part[s][i][c];
-                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                        if (lane == 0) red[warp][lc][s][i][c] = v;
-                    }
         }
+        // transposed butterfly: after the step with offset o a lane keeps the
+        // half selected by (lane & o); at the end lane L holds values [L*VPL, L*VPL+VPL)
+#pragma unroll
+        for (int st = 0; st < 5; ++st) {
+            const int o = 16 >> st;
+            const int h = V >> (st + 1);
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const R send = up ? part[i] : part[i + h];
+                const R keep = up ? part[i + h] : part[i];
+                part[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < VPL; ++j) red[warp][lane * VPL + j] = part[j];
         __syncthreads();
-        for (int idx = threadIdx.x; idx < nl * NS * BT; idx += TPB) {
-            const int lc = idx / (NS * BT);
-            const int s = (idx / BT) % NS;
-            const int i = idx % BT;
+        for (int q = threadIdx.x; q < nl * NS * BT; q += TPB) {
+            const int lc = q / (NS * BT);
+            const int s = (q / BT) % NS;
+            const int i = q % BT;
             if (b0 + i >= B || (s == 1 && !two)) continue;
             R sx = 0, sy = 0;
             for (int w = 0; w < NW; ++w) {
-                sx += red[w][lc][s][i][0];
-                sy += red[w][lc][s][i][1];
+                sx += red[w][2 * q];
+                sy += red[w][2 * q + 1];
             }
             const int l = l0 + lc;
             R f = scale * (kfac ? kfac[l] : (R)1);

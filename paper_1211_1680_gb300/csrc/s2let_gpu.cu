@@ -23,6 +23,7 @@
 
 #include "../../include/s2let_gpu.h"
 #include "fft.cuh"
+#include "gemm_fp32.cuh"
 #include "host_tables.h"
 #include "legendre.cuh"
 
@@ -66,6 +67,7 @@ struct BandDev {
     double2 *seed = nullptr;
     RingD *ringd = nullptr;
     RingF *ringf = nullptr;
+    float *Qe = nullptr, *Qo = nullptr;     // FP32 plans: quadrature matrices, even / odd m
 };
 
 }  // namespace
@@ -81,7 +83,8 @@ struct s2let_plan {
     double2 *coefd = nullptr;               // [m][l] (a, a b), FP64
     float4 *coeff = nullptr;                // [m][l] float-float
     std::vector<void *> kfac;               // per map: scaling first, then scales J0..J (R[L])
-    void *F = nullptr, *flm = nullptr;      // workspace
+    void *F = nullptr, *flm = nullptr, *G = nullptr;   // workspace
+    bool quad_gemm = false;                 // FP32 plans: theta quadrature as a dense FP32 product
     std::vector<void *> owned;
     // instrumentation
     struct Rec {
@@ -201,24 +204,43 @@ int run_ring_inv(const s2let_plan *p, const BandDev &bd, const void *F, void *f,
     return S2LET_OK;
 }
 
+// S2.  Returns the buffer that holds G: F itself (in-place FFT quadrature) or
+// the plan's G buffer (dense-matrix quadrature of FP32 plans).
 template <typename R>
-int run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream_t st)
+void *run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream_t st, int *err)
 {
     const int n = nmi(p, bd.N);
     const int off = p->cplx ? bd.N - 1 : 0;
+    *err = S2LET_OK;
+    if (std::is_same<R, float>::value && p->quad_gemm) {
+        // two products, one per parity of m
+        StageScope sc(p, S2LET_STAGE_THETA_QUAD, st, 2.0 * bd.N * (double)bd.N * n * 2 * p->batch,
+                      2.0 * spectrum_bytes(p, bd.N));
+        for (int par = 0; par < 2; ++par) {
+            int mi0 = p->cplx ? (((bd.N - 1) & 1) ^ par) : par;
+            if (mi0 >= n) continue;
+            const int nj = (n - 1 - mi0) / 2 + 1;
+            const int npairs = nj * p->batch;
+            dim3 grid((bd.N + QG_BM - 1) / QG_BM, (npairs + QG_BN / 2 - 1) / (QG_BN / 2));
+            k_quad_gemm<<<grid, 256, 0, st>>>(par ? bd.Qo : bd.Qe, (const float2 *)F, (float2 *)p->G, bd.N, n, mi0,
+                                              nj, npairs);
+        }
+        if (cudaGetLastError() != cudaSuccess) *err = S2LET_ERR_CUDA;
+        return p->G;
+    }
     const int th = fft_threads(bd.M);
     StageScope sc(p, S2LET_STAGE_THETA_QUAD, st, 0.0, 2.0 * spectrum_bytes(p, bd.N));
     if (p->quad64) {
         const size_t sm = (size_t)bd.M * sizeof(double2);
         k_theta_quad<double, R, 16><<<dim3(n, p->batch), th, sm, st>>>((const cplx_t<R> *)F, (cplx_t<R> *)F, n, off,
-                                                                       1.0, bd.fd);
+                                                                       1.0, bd.fd, -1);
     } else {
         const size_t sm = (size_t)bd.M * sizeof(float2);
         k_theta_quad<float, R, 16><<<dim3(n, p->batch), th, sm, st>>>((const cplx_t<R> *)F, (cplx_t<R> *)F, n, off,
-                                                                      1.0f, bd.ff);
+                                                                      1.0f, bd.ff, -1);
     }
-    S2_LAUNCH_CHECK();
-    return S2LET_OK;
+    if (cudaGetLastError() != cudaSuccess) *err = S2LET_ERR_CUDA;
+    return F;
 }
 
 template <typename R, int BT, bool CPLX>
@@ -239,10 +261,28 @@ int run_synth(const s2let_plan *p, const BandDev &bd, const void *src, const voi
 {
     constexpr int BT = std::is_same<R, double>::value ? 4 : 8;
     StageScope sc(p, S2LET_STAGE_LEG_SYNTH, st, legendre_flops(p, bd.N), 0.0);
-    if (p->cplx) launch_synth<R, BT, true>(p, bd, src, kfac, scale, dst, st);
-    else launch_synth<R, BT, false>(p, bd, src, kfac, scale, dst, st);
+    if (std::is_same<R, float>::value) {
+        const int bt = p->cplx ? LegCols<true>::BT : LegCols<false>::BT;
+        dim3 grid(bd.N, (bd.N + LS_RT - 1) / LS_RT, (p->batch + bt - 1) / bt);
+        const LegTab<float> tab = leg_tab<float>(p, bd);
+        if (p->cplx)
+            k_leg_synth_gemm<true><<<grid, 256, 0, st>>>((const float2 *)src, p->L, (const float *)kfac, (float)scale,
+                                                         (float2 *)dst, bd.N, p->batch, tab);
+        else
+            k_leg_synth_gemm<false><<<grid, 256, 0, st>>>((const float2 *)src, p->L, (const float *)kfac, (float)scale,
+                                                          (float2 *)dst, bd.N, p->batch, tab);
+    } else if (p->cplx) {
+        launch_synth<R, BT, true>(p, bd, src, kfac, scale, dst, st);
+    } else {
+        launch_synth<R, BT, false>(p, bd, src, kfac, scale, dst, st);
+    }
     S2_LAUNCH_CHECK();
     return S2LET_OK;
+}
+
+size_t anal_gemm_smem(int N)
+{
+    return (size_t)(LA_LT * LA_RG + LA_RG * 128) * sizeof(float) + (size_t)N * (sizeof(float4) + sizeof(int));
 }
 
 template <typename R, int BT, bool CPLX, int RPT>
@@ -250,8 +290,9 @@ void launch_anal(const s2let_plan *p, const BandDev &bd, const void *G, const vo
                  void *dst, cudaStream_t st)
 {
     constexpr int TPB = 256;
+    constexpr int V = std::is_same<R, double>::value ? 32 : 64;
     dim3 grid(bd.N, (p->batch + BT - 1) / BT);
-    k_leg_anal<R, BT, CPLX, RPT, TPB><<<grid, TPB, 0, st>>>((const cplx_t<R> *)G, bd.N, (const R *)kfac, (R)scale,
+    k_leg_anal<R, BT, CPLX, RPT, TPB, V><<<grid, TPB, 0, st>>>((const cplx_t<R> *)G, bd.N, (const R *)kfac, (R)scale,
                                                             acc, (cplx_t<R> *)dst, p->L, nmi(p, p->L), p->L,
                                                             p->batch, leg_tab<R>(p, bd));
 }
@@ -273,8 +314,22 @@ int run_anal(const s2let_plan *p, const BandDev &bd, const void *G, const void *
 {
     constexpr int BT = std::is_same<R, double>::value ? 2 : 4;
     StageScope sc(p, S2LET_STAGE_LEG_ANAL, st, legendre_flops(p, bd.N), 0.0);
-    if (p->cplx) launch_anal_rpt<R, BT, true>(p, bd, G, kfac, scale, acc, dst, st);
-    else launch_anal_rpt<R, BT, false>(p, bd, G, kfac, scale, acc, dst, st);
+    if (std::is_same<R, float>::value) {
+        const int bt = p->cplx ? LegCols<true>::BT : LegCols<false>::BT;
+        dim3 grid(bd.N, (p->batch + bt - 1) / bt);
+        const size_t sm = anal_gemm_smem(bd.N);
+        const LegTab<float> tab = leg_tab<float>(p, bd);
+        if (p->cplx)
+            k_leg_anal_gemm<true><<<grid, 256, sm, st>>>((const float2 *)G, bd.N, (const float *)kfac, (float)scale,
+                                                         acc, (float2 *)dst, p->L, p->batch, tab);
+        else
+            k_leg_anal_gemm<false><<<grid, 256, sm, st>>>((const float2 *)G, bd.N, (const float *)kfac, (float)scale,
+                                                          acc, (float2 *)dst, p->L, p->batch, tab);
+    } else if (p->cplx) {
+        launch_anal_rpt<R, BT, true>(p, bd, G, kfac, scale, acc, dst, st);
+    } else {
+        launch_anal_rpt<R, BT, false>(p, bd, G, kfac, scale, acc, dst, st);
+    }
     S2_LAUNCH_CHECK();
     return S2LET_OK;
 }
@@ -331,8 +386,9 @@ template <typename R> int sht_fwd_to_rect(s2let_plan *p, const void *f, cudaStre
     const BandDev &bd = p->bands.at(p->L);
     int e;
     if ((e = run_ring_fwd<R>(p, bd, f, p->F, 1.0 / bd.P, st))) return e;
-    if ((e = run_theta_quad<R>(p, bd, p->F, st))) return e;
-    return run_anal<R>(p, bd, p->F, nullptr, 2.0 * M_PI / bd.P, 0, p->flm, st);
+    void *G = run_theta_quad<R>(p, bd, p->F, st, &e);
+    if (e) return e;
+    return run_anal<R>(p, bd, G, nullptr, 2.0 * M_PI / bd.P, 0, p->flm, st);
 }
 
 template <typename R> int sht_forward_t(s2let_plan *p, const void *f, void *flm, cudaStream_t st)
@@ -402,8 +458,9 @@ template <typename R> int synthesis_t(s2let_plan *p, const void *fw, const void 
         const BandDev &bd = p->bands.at(mr.N);
         const char *in = mr.scal ? (const char *)fs : (const char *)fw + mr.off * es;
         if ((e = run_ring_fwd<R>(p, bd, in, p->F, 1.0 / bd.P, st))) return e;
-        if ((e = run_theta_quad<R>(p, bd, p->F, st))) return e;
-        if ((e = run_anal<R>(p, bd, p->F, p->kfac[mr.k], 2.0 * M_PI / bd.P, first ? 0 : 1, p->flm, st))) return e;
+        void *G = run_theta_quad<R>(p, bd, p->F, st, &e);
+        if (e) return e;
+        if ((e = run_anal<R>(p, bd, G, p->kfac[mr.k], 2.0 * M_PI / bd.P, first ? 0 : 1, p->flm, st))) return e;
         first = 0;
     }
     const BandDev &bl = p->bands.at(p->L);
@@ -426,8 +483,9 @@ template <typename R> int adjoint_t(s2let_plan *p, const void *gw, const void *g
     // forward-transform adjoint: Legendre sum (2 pi / P), quadrature (symmetric), ring DFT (1/P)
     const BandDev &bl = p->bands.at(p->L);
     if ((e = run_synth<R>(p, bl, p->flm, nullptr, 2.0 * M_PI / bl.P, p->F, st))) return e;
-    if ((e = run_theta_quad<R>(p, bl, p->F, st))) return e;
-    return run_ring_inv<R>(p, bl, p->F, gf, 1.0 / bl.P, st);
+    void *G = run_theta_quad<R>(p, bl, p->F, st, &e);
+    if (e) return e;
+    return run_ring_inv<R>(p, bl, G, gf, 1.0 / bl.P, st);
 }
 
 // ------------------------------------------------------------ plan construction
@@ -447,9 +505,55 @@ void set_smem_limits(int Mmax)
     allow_smem(k_ring_fwd_cplx<float>, f);
     allow_smem(k_ring_inv_real<float>, f);
     allow_smem(k_ring_inv_cplx<float>, f);
+    allow_smem(k_leg_anal_gemm<false>, anal_gemm_smem(kMaxL));
+    allow_smem(k_leg_anal_gemm<true>, anal_gemm_smem(kMaxL));
     allow_smem(k_theta_quad<double, double, 16>, d);
     allow_smem(k_theta_quad<double, float, 16>, d);
     allow_smem(k_theta_quad<float, float, 16>, f);
+}
+
+__global__ void k_unit_rows(double2 *X, int N)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)N * N) return;
+    const int r = (int)(i / N), c = (int)(i % N);
+    X[i] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+}
+
+__global__ void k_real_to_float(const double2 *X, float *Q, size_t n)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) Q[i] = (float)X[i].x;
+}
+
+// Q_sigma (N x N, symmetric) by the FP64 theta quadrature applied to unit vectors:
+// row i of the output is Q_sigma e_i.
+int build_quad_matrices(s2let_plan *p, BandDev &bd)
+{
+    const int N = bd.N;
+    const size_t nn = (size_t)N * N;
+    double2 *X = nullptr;
+    if (cudaMalloc(&X, nn * sizeof(double2)) != cudaSuccess) return S2LET_ERR_ALLOC;
+    cudaFuncSetAttribute(k_theta_quad<double, double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(bd.M * sizeof(double2)));
+    int err = S2LET_OK;
+    for (int par = 0; par < 2 && !err; ++par) {
+        float *Q = nullptr;
+        if (cudaMalloc(&Q, nn * sizeof(float)) != cudaSuccess) {
+            err = S2LET_ERR_ALLOC;
+            break;
+        }
+        p->owned.push_back(Q);
+        (par ? bd.Qo : bd.Qe) = Q;
+        k_unit_rows<<<(unsigned)((nn + 255) / 256), 256>>>(X, N);
+        k_theta_quad<double, double, 16><<<dim3(N, 1), fft_threads(bd.M), bd.M * sizeof(double2)>>>(
+            X, X, N, 0, 1.0, bd.fd, par);
+        k_real_to_float<<<(unsigned)((nn + 255) / 256), 256>>>(X, Q, nn);
+        if (cudaGetLastError() != cudaSuccess) err = S2LET_ERR_CUDA;
+    }
+    if (!err && cudaDeviceSynchronize() != cudaSuccess) err = S2LET_ERR_CUDA;
+    cudaFree(X);
+    return err;
 }
 
 int build_band_dev(s2let_plan *p, int N, BandDev &bd)
@@ -512,6 +616,13 @@ int build_band_dev(s2let_plan *p, int N, BandDev &bd)
     o.push_back(seed);
     bd.ls = (int *)ls;
     bd.seed = (double2 *)seed;
+    if (p->quad_gemm) {
+        if ((err = build_quad_matrices(p, bd))) {
+            cudaFree(mant);
+            cudaFree(expo);
+            return err;
+        }
+    }
     k_sectoral<<<(N + 127) / 128, 128>>>(N, sinth, mant, expo);
     k_seed_start<<<(unsigned)((nn + 127) / 128), 128>>>(N, mant, expo, bd.ringd, p->coefd, p->L, bd.ls, bd.seed);
     cudaError_t ce = cudaGetLastError();
@@ -529,8 +640,8 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
     if (J0 < 0 || J0 >= J) return S2LET_ERR_ARG;
     const int prec = flags & S2LET_PREC_MASK;
     if (prec != S2LET_PREC_FP64 && prec != S2LET_PREC_FP32) return S2LET_ERR_ARG;
-    if (flags & ~(S2LET_COMPLEX | S2LET_MULTIRES | S2LET_PREC_MASK | S2LET_QUAD_FP32)) return S2LET_ERR_ARG;
-    if ((flags & S2LET_QUAD_FP32) && prec == S2LET_PREC_FP64) return S2LET_ERR_ARG;
+    if (flags & ~(S2LET_COMPLEX | S2LET_MULTIRES | S2LET_PREC_MASK | S2LET_QUAD_FFT64)) return S2LET_ERR_ARG;
+    if ((flags & S2LET_QUAD_FFT64) && prec == S2LET_PREC_FP64) return S2LET_ERR_ARG;
 
     std::unique_ptr<s2let_plan> p(new (std::nothrow) s2let_plan());
     if (!p) return S2LET_ERR_ALLOC;
@@ -543,7 +654,8 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
     p->cplx = flags & S2LET_COMPLEX;
     p->multires = flags & S2LET_MULTIRES;
     p->fp64 = prec == S2LET_PREC_FP64;
-    p->quad64 = !(flags & S2LET_QUAD_FP32);
+    p->quad64 = true;
+    p->quad_gemm = prec == S2LET_PREC_FP32 && !(flags & S2LET_QUAD_FFT64);
     // band-limits (Sect. 3.1)
     auto ipow = [](long long b, int e) {
         long long r = 1;
@@ -610,6 +722,10 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
     p->owned.push_back(p->F);
     if (cudaMalloc(&p->flm, ws) != cudaSuccess) return S2LET_ERR_ALLOC;
     p->owned.push_back(p->flm);
+    if (p->quad_gemm) {
+        if (cudaMalloc(&p->G, ws) != cudaSuccess) return S2LET_ERR_ALLOC;
+        p->owned.push_back(p->G);
+    }
     if (cudaGetLastError() != cudaSuccess) return S2LET_ERR_CUDA;
     *out = p.release();
     return S2LET_OK;
