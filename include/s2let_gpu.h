@@ -142,6 +142,35 @@ int s2let_plan_profile(s2let_plan *plan, int enable);
 int s2let_plan_stage_stats(s2let_plan *plan, int stage, int64_t *launches, int64_t *timed, double *ms,
                            double *flops, double *bytes);
 
+/* ---- allocation-free inverse transform (no counterpart in the paper) -----
+ * For callers that cannot allocate device memory: code that runs while a
+ * stream is being captured (cudaMalloc is not allowed then), applications
+ * whose device memory is handed out once by a framework or a fixed budget, and
+ * real-time or embedded hosts that forbid allocation after start-up.  It
+ * computes the same inverse MW transform as s2let_sht_inverse of an FP32 plan
+ * (Eq. harmonicssynthesis, Sect. 2.1) without a plan and without calling
+ * cudaMalloc, cudaFree or any allocating library routine: its tables and work
+ * buffers live in one statically sized device array inside the library
+ * (S2LET_NOALLOC_SCRATCH_BYTES), which every GPU that loads the library holds
+ * until the process exits.
+ *   L:      band-limit, 2 <= L <= S2LET_NOALLOC_MAX_L (else S2LET_ERR_ARG)
+ *   batch:  number of maps, 1 <= batch <= S2LET_NOALLOC_MAX_BATCH (else S2LET_ERR_ARG)
+ *   flags:  S2LET_PREC_FP32, optionally | S2LET_COMPLEX (anything else: S2LET_ERR_ARG)
+ *   flm:    device, batch x L*L complex float (index l*l + l + m), read only
+ *   f:      device, batch maps of L x (2L-1) float (complex: interleaved), written
+ * Set-up: the first call on a device, and every call whose (L, batch, complex)
+ * differs from the previous call on that device, looks up the array's device
+ * address (cudaGetSymbolAddress), copies tables into it and computes Legendre
+ * seeds, synchronising the device; make that first call before any stream
+ * capture.  The other calls only launch kernels on `stream`.
+ * The array is shared by every call on a device and keeps the last call's
+ * contents; calls whose kernels overlap on the GPU (different streams, no
+ * ordering) race on it and must be serialised by the caller. */
+#define S2LET_NOALLOC_MAX_L 128
+#define S2LET_NOALLOC_MAX_BATCH 8
+#define S2LET_NOALLOC_SCRATCH_BYTES (8u << 20)
+int s2let_sht_inverse_noalloc(int L, int batch, int flags, const void *flm, void *f, void *stream);
+
 /* Short text for a status code. */
 const char *s2let_strerror(int status);
 

@@ -41,6 +41,7 @@ SIGNATURES = {
     "s2let_plan_profile": (_i, [_vp, _i]),
     "s2let_plan_stage_stats": (_i, [_vp, _i, _i64p, _i64p, ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "s2let_sht_inverse_noalloc": (_i, [_i, _i, _i, _vp, _vp, _vp]),
     "s2let_strerror": (ctypes.c_char_p, [_i]),
 }
 

@@ -20,7 +20,7 @@ namespace s2g {
 // Tiles: 128 rows (t) x 128 columns (64 (b, mi) pairs x re/im) x 16 (t').
 constexpr int QG_BM = 128, QG_BN = 128, QG_BK = 16;
 
-__global__ void __launch_bounds__(256) k_quad_gemm(const float *__restrict__ Q, const float2 *__restrict__ F,
+static __global__ void __launch_bounds__(256) k_quad_gemm(const float *__restrict__ Q, const float2 *__restrict__ F,
                                                    float2 *__restrict__ G, int N, int nmi, int mi0, int nj,
                                                    int npairs)
 {

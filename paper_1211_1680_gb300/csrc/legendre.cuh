@@ -77,7 +77,7 @@ template <> struct RecT<float> {
 // ---------------------------------------------------------------- seeds (FP64)
 // Sectoral values lambda_mm(theta_t) = -sqrt((2m+1)/(2m)) sin(theta) lambda_{m-1,m-1},
 // lambda_00 = 1/sqrt(4 pi), kept as mantissa * 2^exponent.  One thread per ring.
-__global__ void k_sectoral(int N, const double *__restrict__ sinth, double *__restrict__ mant,
+static __global__ void k_sectoral(int N, const double *__restrict__ sinth, double *__restrict__ mant,
                            int *__restrict__ expo)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -101,7 +101,7 @@ __global__ void k_sectoral(int N, const double *__restrict__ sinth, double *__re
 
 // First degree l_s >= m with |lambda_lm(theta_t)| >= 2^-SEED_EXP, and the pair
 // (lambda_{l_s-1}, lambda_{l_s}); l_s = N when there is none.  One thread per (m, t).
-__global__ void k_seed_start(int N, const double *__restrict__ mant, const int *__restrict__ expo,
+static __global__ void k_seed_start(int N, const double *__restrict__ mant, const int *__restrict__ expo,
                              const RingD *__restrict__ ring, const double2 *__restrict__ coef, int ldc,
                              int *__restrict__ ls, double2 *__restrict__ seed)
 {
