@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "tf32x3", "fp64"], default="fp32")
     ap.add_argument("--quad-fft64", action="store_true", help="FP32 plans: theta quadrature by FP64 FFTs")
     ap.add_argument("--L", type=int, default=2048)
     ap.add_argument("--batch", type=int, default=64)
@@ -67,7 +67,7 @@ def config(a):
             "L": a.L, "B": a.B, "J_min": a.J_min, "maps_per_gpu": a.batch, "multires": True, "signal": "real",
             "precision": a.precision + ("+quad_fft64" if a.quad_fft64 else ""),
             "l2": "inputs larger than L2 (map batch %.2f GB)" % (a.batch * a.L * (2 * a.L - 1)
-                                                                   * (4 if a.precision == "fp32" else 8) / 1e9)}
+                                                                   * (8 if a.precision == "fp64" else 4) / 1e9)}
 
 
 # ---------------------------------------------------------------- clocks
@@ -284,7 +284,7 @@ def run_gpu(a, rank, world, local_rank):
     if sd["flops"] > 0:
         # a contraction stage: FP32 (or FP64) FMA pipe; peak derived from unit counts and clock
         mhz = peaks.get("sm_max_mhz", 2070.0)
-        if a.precision == "fp32":
+        if a.precision in ("fp32", "tf32x3"):
             peak = SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12
             pdesc = "derived: %d SMs x %d FP32 lanes x 2 flop/FMA x %.0f MHz (max SM clock)" % (
                 SM_COUNT, FP32_LANES, mhz)
@@ -317,7 +317,8 @@ def run_gpu(a, rank, world, local_rank):
 
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
            "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32" if a.precision == "fp32" else "f64", "data": "synthetic", "config": config(a),
+           "dtype": {"fp32": "f32", "tf32x3": "tf32x3+f32", "fp64": "f64"}[a.precision], "data": "synthetic",
+           "config": config(a),
            "gpu_launches": launches, "roofline": roof, "stages": stage_share, "clocks": clk}
 
     # end to end: pinned host maps in, host maps out, copies inside the timed region

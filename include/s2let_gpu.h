@@ -57,6 +57,9 @@ extern "C" {
                                     recurrence, FP64 seeds; theta quadrature as a
                                     dense FP32 product with its matrix built in
                                     FP64                                       */
+#define S2LET_PREC_TF32X3 0x20   /* as FP32, with the dense products on the tensor
+                                    cores (tcgen05, TF32 split into hi + lo,
+                                    3 products, FP32 accumulation)            */
 #define S2LET_PREC_MASK 0xf0
 #define S2LET_QUAD_FFT64 0x100   /* FP32 plans only: theta quadrature by FP64 FFTs
                                     instead of the dense FP32 product          */
@@ -170,6 +173,11 @@ int s2let_plan_stage_stats(s2let_plan *plan, int stage, int64_t *launches, int64
 #define S2LET_NOALLOC_MAX_BATCH 8
 #define S2LET_NOALLOC_SCRATCH_BYTES (8u << 20)
 int s2let_sht_inverse_noalloc(int L, int batch, int flags, const void *flm, void *f, void *stream);
+
+/* Device-side status of a plan: S2LET_ERR_TIMEOUT if a bounded wait inside a
+ * tensor-core kernel gave up since the plan was created (its results are then
+ * not valid), else S2LET_OK.  Synchronises the device. */
+int s2let_plan_status(s2let_plan *plan);
 
 /* Short text for a status code. */
 const char *s2let_strerror(int status);

@@ -20,6 +20,7 @@ S2LET_COMPLEX = 0x1
 S2LET_MULTIRES = 0x2
 S2LET_PREC_FP64 = 0x00
 S2LET_PREC_FP32 = 0x10
+S2LET_PREC_TF32X3 = 0x20
 S2LET_QUAD_FFT64 = 0x100
 
 # every symbol the header declares, with (restype, argtypes)
@@ -38,6 +39,7 @@ SIGNATURES = {
     "s2let_adjoint": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "s2let_sht_forward": (_i, [_vp, _vp, _vp, _vp]),
     "s2let_sht_inverse": (_i, [_vp, _vp, _vp, _vp]),
+    "s2let_plan_status": (_i, [_vp]),
     "s2let_plan_profile": (_i, [_vp, _i]),
     "s2let_plan_stage_stats": (_i, [_vp, _i, _i64p, _i64p, ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),

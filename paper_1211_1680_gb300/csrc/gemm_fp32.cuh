@@ -20,7 +20,7 @@ namespace s2g {
 // Tiles: 128 rows (t) x 128 columns (64 (b, mi) pairs x re/im) x 16 (t').
 constexpr int QG_BM = 128, QG_BN = 128, QG_BK = 16;
 
-static __global__ void __launch_bounds__(256) k_quad_gemm(const float *__restrict__ Q, const float2 *__restrict__ F,
+static __global__ void __launch_bounds__(256, 2) k_quad_gemm(const float *__restrict__ Q, const float2 *__restrict__ F,
                                                    float2 *__restrict__ G, int N, int nmi, int mi0, int nj,
                                                    int npairs)
 {
@@ -283,7 +283,9 @@ __global__ void __launch_bounds__(256) k_leg_anal_gemm(const float2 *__restrict_
     }
 }
 
-// Synthesis.  One block per (order m, tile of RT = 128 rings, batch tile).
+// Synthesis.  One block per (tile of RT = 128 rings, order m, batch tile); the
+// ring tiles of one order are adjacent in the grid so they share its
+// coefficient rows in L2.
 // Degrees in chunks of LK = 32: each of the first RT threads advances its ring
 // LK steps writing lambda[l][t]; coefficient tile a[l][c] = c_l f_lm staged from
 // the source; all 256 threads accumulate acc[t][c] += lambda[l][t] a[l][c].
@@ -301,8 +303,8 @@ __global__ void __launch_bounds__(256) k_leg_synth_gemm(const float2 *__restrict
     __shared__ float4 sc[LS_LK];
     __shared__ int smin[8];
 
-    const int m = blockIdx.x;
-    const int t0 = blockIdx.y * LS_RT;
+    const int m = blockIdx.y;
+    const int t0 = blockIdx.x * LS_RT;
     const int b0 = blockIdx.z * BT;
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;

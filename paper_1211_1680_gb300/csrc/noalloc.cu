@@ -194,7 +194,7 @@ extern "C" int s2let_sht_inverse_noalloc(int L, int batch, int flags, const void
     tab.coef = (const float4 *)(b + o.coeff);
     tab.ldc = L;
     const int bt = cplx ? LegCols<true>::BT : LegCols<false>::BT;
-    dim3 grid(L, (L + LS_RT - 1) / LS_RT, (batch + bt - 1) / bt);
+    dim3 grid((L + LS_RT - 1) / LS_RT, L, (batch + bt - 1) / bt);
     if (cplx)
         k_leg_synth_gemm<true><<<grid, 256, 0, st>>>(rect, L, nullptr, 1.0f, F, L, batch, tab);
     else

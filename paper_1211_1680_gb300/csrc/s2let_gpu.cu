@@ -24,6 +24,7 @@
 #include "../../include/s2let_gpu.h"
 #include "fft.cuh"
 #include "gemm_fp32.cuh"
+#include "tc_kernels.cuh"
 #include "host_tables.h"
 #include "legendre.cuh"
 
@@ -68,6 +69,7 @@ struct BandDev {
     RingD *ringd = nullptr;
     RingF *ringf = nullptr;
     float *Qe = nullptr, *Qo = nullptr;     // FP32 plans: quadrature matrices, even / odd m
+    float *Qe3 = nullptr, *Qo3 = nullptr;   // TF32X3 plans: the same, split into three TF32 planes
 };
 
 }  // namespace
@@ -85,6 +87,8 @@ struct s2let_plan {
     std::vector<void *> kfac;               // per map: scaling first, then scales J0..J (R[L])
     void *F = nullptr, *flm = nullptr, *G = nullptr;   // workspace
     bool quad_gemm = false;                 // FP32 plans: theta quadrature as a dense FP32 product
+    bool tc = false;                        // TF32X3 plans: dense products on the tensor cores
+    int *d_err = nullptr;                   // device error word (bounded waits)
     std::vector<void *> owned;
     // instrumentation
     struct Rec {
@@ -222,8 +226,12 @@ void *run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream
             const int nj = (n - 1 - mi0) / 2 + 1;
             const int npairs = nj * p->batch;
             dim3 grid((bd.N + QG_BM - 1) / QG_BM, (npairs + QG_BN / 2 - 1) / (QG_BN / 2));
-            k_quad_gemm<<<grid, 256, 0, st>>>(par ? bd.Qo : bd.Qe, (const float2 *)F, (float2 *)p->G, bd.N, n, mi0,
-                                              nj, npairs);
+            if (p->tc)
+                k_quad_tc<<<grid, TQ_THREADS, TQ_SMEM, st>>>(par ? bd.Qo3 : bd.Qe3, (const float2 *)F,
+                                                             (float2 *)p->G, bd.N, n, mi0, nj, npairs, p->d_err);
+            else
+                k_quad_gemm<<<grid, 256, 0, st>>>(par ? bd.Qo : bd.Qe, (const float2 *)F, (float2 *)p->G, bd.N, n,
+                                                  mi0, nj, npairs);
         }
         if (cudaGetLastError() != cudaSuccess) *err = S2LET_ERR_CUDA;
         return p->G;
@@ -263,7 +271,7 @@ int run_synth(const s2let_plan *p, const BandDev &bd, const void *src, const voi
     StageScope sc(p, S2LET_STAGE_LEG_SYNTH, st, legendre_flops(p, bd.N), 0.0);
     if (std::is_same<R, float>::value) {
         const int bt = p->cplx ? LegCols<true>::BT : LegCols<false>::BT;
-        dim3 grid(bd.N, (bd.N + LS_RT - 1) / LS_RT, (p->batch + bt - 1) / bt);
+        dim3 grid((bd.N + LS_RT - 1) / LS_RT, bd.N, (p->batch + bt - 1) / bt);
         const LegTab<float> tab = leg_tab<float>(p, bd);
         if (p->cplx)
             k_leg_synth_gemm<true><<<grid, 256, 0, st>>>((const float2 *)src, p->L, (const float *)kfac, (float)scale,
@@ -505,6 +513,7 @@ void set_smem_limits(int Mmax)
     allow_smem(k_ring_fwd_cplx<float>, f);
     allow_smem(k_ring_inv_real<float>, f);
     allow_smem(k_ring_inv_cplx<float>, f);
+    allow_smem(k_quad_tc, TQ_SMEM);
     allow_smem(k_leg_anal_gemm<false>, anal_gemm_smem(kMaxL));
     allow_smem(k_leg_anal_gemm<true>, anal_gemm_smem(kMaxL));
     allow_smem(k_theta_quad<double, double, 16>, d);
@@ -549,6 +558,16 @@ int build_quad_matrices(s2let_plan *p, BandDev &bd)
         k_theta_quad<double, double, 16><<<dim3(N, 1), fft_threads(bd.M), bd.M * sizeof(double2)>>>(
             X, X, N, 0, 1.0, bd.fd, par);
         k_real_to_float<<<(unsigned)((nn + 255) / 256), 256>>>(X, Q, nn);
+        if (p->tc) {
+            float *Q3 = nullptr;
+            if (cudaMalloc(&Q3, 3 * nn * sizeof(float)) != cudaSuccess) {
+                err = S2LET_ERR_ALLOC;
+                break;
+            }
+            p->owned.push_back(Q3);
+            (par ? bd.Qo3 : bd.Qe3) = Q3;
+            k_split3_planes<<<(unsigned)((nn + 255) / 256), 256>>>(Q, Q3, nn);
+        }
         if (cudaGetLastError() != cudaSuccess) err = S2LET_ERR_CUDA;
     }
     if (!err && cudaDeviceSynchronize() != cudaSuccess) err = S2LET_ERR_CUDA;
@@ -639,7 +658,7 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
     const int J = s2h::jmax(L, B);
     if (J0 < 0 || J0 >= J) return S2LET_ERR_ARG;
     const int prec = flags & S2LET_PREC_MASK;
-    if (prec != S2LET_PREC_FP64 && prec != S2LET_PREC_FP32) return S2LET_ERR_ARG;
+    if (prec != S2LET_PREC_FP64 && prec != S2LET_PREC_FP32 && prec != S2LET_PREC_TF32X3) return S2LET_ERR_ARG;
     if (flags & ~(S2LET_COMPLEX | S2LET_MULTIRES | S2LET_PREC_MASK | S2LET_QUAD_FFT64)) return S2LET_ERR_ARG;
     if ((flags & S2LET_QUAD_FFT64) && prec == S2LET_PREC_FP64) return S2LET_ERR_ARG;
 
@@ -655,7 +674,8 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
     p->multires = flags & S2LET_MULTIRES;
     p->fp64 = prec == S2LET_PREC_FP64;
     p->quad64 = true;
-    p->quad_gemm = prec == S2LET_PREC_FP32 && !(flags & S2LET_QUAD_FFT64);
+    p->tc = prec == S2LET_PREC_TF32X3;
+    p->quad_gemm = (prec == S2LET_PREC_FP32 || p->tc) && !(flags & S2LET_QUAD_FFT64);
     // band-limits (Sect. 3.1)
     auto ipow = [](long long b, int e) {
         long long r = 1;
@@ -674,6 +694,9 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
     p->scal_elems = map_elems(p.get(), p->n_scal) * batch;
 
     int err = S2LET_OK;
+    if (cudaMalloc(&p->d_err, sizeof(int)) != cudaSuccess) return S2LET_ERR_ALLOC;
+    p->owned.push_back(p->d_err);
+    if (cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess) return S2LET_ERR_CUDA;
     // recurrence coefficients for degrees and orders < L
     std::vector<double> a, ab;
     s2h::legendre_coefs(L, a, ab);
@@ -812,6 +835,14 @@ int s2let_sht_inverse(s2let_plan *p, const void *flm, void *f, void *stream)
 {
     if (!p || !f || !flm) return S2LET_ERR_ARG;
     return S2_DISPATCH(sht_inverse_t, p, flm, f, (cudaStream_t)stream);
+}
+
+int s2let_plan_status(s2let_plan *p)
+{
+    if (!p) return S2LET_ERR_ARG;
+    int h = 0;
+    if (cudaMemcpy(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return S2LET_ERR_CUDA;
+    return h ? S2LET_ERR_TIMEOUT : S2LET_OK;
 }
 
 int s2let_plan_profile(s2let_plan *p, int enable)

@@ -8,9 +8,9 @@ import torch
 
 from . import _lib
 from ._lib import (S2LET_COMPLEX, S2LET_MULTIRES, S2LET_PREC_FP32, S2LET_PREC_FP64,  # noqa: F401
-                   S2LET_QUAD_FFT64, check)
+                   S2LET_PREC_TF32X3, S2LET_QUAD_FFT64, check)
 
-PRECISIONS = {"fp64": S2LET_PREC_FP64, "fp32": S2LET_PREC_FP32}
+PRECISIONS = {"fp64": S2LET_PREC_FP64, "fp32": S2LET_PREC_FP32, "tf32x3": S2LET_PREC_TF32X3}
 
 
 def jmax(L, B):
@@ -60,6 +60,10 @@ class Plan:
             check("s2let_wav_layout", lib.s2let_wav_layout(self._h, j, ctypes.byref(n), ctypes.byref(off),
                                                            ctypes.byref(cnt)))
             self.scales.append((j, n.value, off.value, cnt.value))
+
+    def status(self):
+        """S2LET_OK, or S2LET_ERR_TIMEOUT if a bounded device wait gave up (synchronises)."""
+        return _lib.lib().s2let_plan_status(self._h)
 
     def close(self):
         if self._h:

@@ -17,9 +17,9 @@ def _maps(L, seeds, real, kind="white"):
     return np.stack([sht.inverse(inputs.random_flm(L, s, real, kind), L, real=real) for s in seeds])
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 @pytest.mark.parametrize("real", [True, False])
-@pytest.mark.parametrize("L", [3, 4, 8, 17, 33, 64])
+@pytest.mark.parametrize("L", [3, 4, 8, 17, 33, 64, 130])
 def test_sht_forward_inverse(L, real, prec):
     seeds = [11, 12, 13]
     plan = Plan(L, 2, 0, batch=len(seeds), real=real, multires=True, precision=prec)
@@ -34,7 +34,7 @@ def test_sht_forward_inverse(L, real, prec):
     assert rel_err(g, ref) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 def test_sht_forward_not_bandlimited(prec):
     """Any samples (pole ring not constant, no band-limit): same linear map."""
     L = 24
@@ -54,6 +54,8 @@ CASES = [  # L, B, J0, multires, real, prec
     (65, 2, 5, True, True, "fp32"),       # J0 = J - 1
     (3, 2, 0, True, True, "fp64"),        # smallest L
     (96, 2, 2, True, True, "fp64"),
+    (96, 2, 2, True, True, "tf32x3"),
+    (40, 3, 1, True, False, "tf32x3"),
 ]
 
 
