@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-check", action="store_true")
+    ap.add_argument("--workload", choices=["l2048x64", "batch256"], default="l2048x64",
+                    help="batch256: 256 complex maps of uneven L in {128..2048} and B in {2, 3}, J_min=1, "
+                         "one graph launch per round trip")
     return ap.parse_args()
 
 
@@ -380,6 +383,65 @@ def run_gpu(a, rank, world, local_rank):
     return 0
 
 
+def run_batch256(a, rank, world, local_rank):
+    """256 complex maps, L ~ {128: .3, 256: .3, 512: .2, 1024: .1, 2048: .1}, B ~ {2, 3}, J_min = 1,
+    FP32; every round trip of the whole uneven batch is one CUDA graph launch."""
+    import ctypes
+    import torch
+    from paper_1211_1680_gb300 import _lib, inputs
+    from paper_1211_1680_gb300.s2let import BatchPlan
+
+    torch.cuda.set_device(local_rank)
+    rng = np.random.Generator(np.random.PCG64(4 + rank))
+    Ls = rng.choice([128, 256, 512, 1024, 2048], size=256, p=[0.3, 0.3, 0.2, 0.1, 0.1]).tolist()
+    Bs = rng.choice([2, 3], size=256).tolist()
+    prec = a.precision
+    bp = BatchPlan(Ls, Bs, 1, real=False, multires=True, precision=prec)
+    f, fw, fs, fo = bp.buffers()
+    lib = _lib.lib()
+    # inputs: per group, seeded complex Gaussian f_lm -> maps with the group plan's inverse transform
+    for g, (ph, f_off, _, _) in enumerate(bp.groups):
+        members = [i for i in range(256) if bp.layout[i][2] == g]
+        L = Ls[members[0]]
+        flm = np.stack([inputs.random_flm(L, 4000 + rank * 256 + i, real=False) for i in members])
+        fl = torch.from_numpy(np.stack([flm.real, flm.imag], -1)).to("cuda", bp.dtype).contiguous()
+        n = len(members) * L * (2 * L - 1) * 2
+        check = lib.s2let_sht_inverse(ctypes.c_void_p(ph), ctypes.c_void_p(fl.data_ptr()),
+                                      ctypes.c_void_p(f[f_off:f_off + n].data_ptr()), None)
+        assert check == 0
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(a.warmup):
+            bp.round_trip(f, fw, fs, fo)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        clocks = ClockSampler(local_rank)
+        clocks.start()
+        e0.record(stream)
+        for _ in range(a.steps):
+            bp.round_trip(f, fw, fs, fo)
+        e1.record(stream)
+        stream.synchronize()
+        clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    err = max(float(((bp.map_view(fo, i) - bp.map_view(f, i)).abs().max() / bp.map_view(f, i).abs().max()).item())
+              for i in range(256))
+    hist = {int(L): Ls.count(L) for L in sorted(set(Ls))}
+    res = {"metric": "uneven-batch wavelet round-trips/s (256 complex maps, one graph launch per round trip)",
+           "value": world * 256 * a.steps / (ms / 1000.0), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": {"fp32": "f32", "tf32x3": "tf32x3+f32", "fp64": "f64"}[prec],
+           "data": "synthetic",
+           "config": {"workload": "256 complex maps, L histogram %s, B in {2,3}, J_min=1, multiresolution" % hist,
+                      "groups": bp.n_groups, "graph_launches_per_step": 1},
+           "round_trip_rel_err": err, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     a = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -391,6 +453,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group(backend="nccl")
     try:
+        if a.workload == "batch256":
+            return run_batch256(a, rank, world, local_rank)
         return run_gpu(a, rank, world, local_rank)
     finally:
         if world > 1:

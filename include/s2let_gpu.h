@@ -120,6 +120,41 @@ int s2let_sht_forward(s2let_plan *plan, const void *f, void *flm, void *stream);
  * Sect. 2.1).  In: flm.  Out: f. */
 int s2let_sht_inverse(s2let_plan *plan, const void *flm, void *f, void *stream);
 
+/* ---- batches of maps of uneven band-limit and dilation ------------------
+ * (no counterpart in the paper: its transforms take one map at a time)
+ * A batch groups its maps by (L, B) into plans (same J_min and flags for all).
+ * The buffers f, f_wav, f_scal, f_out of a batch are the concatenation of the
+ * groups' buffers, group by group; s2let_batch_map_layout tells where map i
+ * (in the caller's order) lives.  Limits as for s2let_plan_create. */
+typedef struct s2let_batch s2let_batch;
+
+int s2let_batch_create(s2let_batch **batch, int n_maps, const int *L, const int *B, int J_min, int flags);
+int s2let_batch_destroy(s2let_batch *batch);
+
+/* Total element counts (in real numbers of the plans' type) of f (= f_out),
+ * f_wav and f_scal, and the number of (L, B) groups.  Outputs may be NULL. */
+int s2let_batch_sizes(const s2let_batch *batch, int64_t *f_elems, int64_t *wav_elems, int64_t *scal_elems,
+                      int *n_groups);
+
+/* Where map i lives: element offsets of its samples in f, of its scaling map in
+ * f_scal, its group index and its index inside the group; inside f_wav a
+ * group's block holds, scale by scale, `group size` maps (see
+ * s2let_wav_layout of the group's plan, returned by s2let_batch_group_plan). */
+int s2let_batch_map_layout(const s2let_batch *batch, int i, int64_t *f_off, int64_t *scal_off, int *group,
+                           int *index_in_group);
+
+/* The plan of group g and the element offsets of its blocks in f, f_wav, f_scal. */
+int s2let_batch_group_plan(const s2let_batch *batch, int g, s2let_plan **plan, int64_t *f_off, int64_t *wav_off,
+                           int64_t *scal_off);
+
+/* Analysis then synthesis of every map (f -> f_wav, f_scal -> f_out).  The
+ * first call for a given set of pointers and stream captures the work of all
+ * groups, each group on its own forked stream, into one CUDA graph; later
+ * calls with the same pointers replay it with a single cudaGraphLaunch on
+ * `stream`.  Graphs for up to 8 pointer sets are kept. */
+int s2let_batch_round_trip(s2let_batch *batch, const void *f, void *f_wav, void *f_scal, void *f_out,
+                           void *stream);
+
 /* ---- instrumentation (no counterpart in the paper) ----------------------
  * Stages of the data path; every kernel launch belongs to one of them. */
 #define S2LET_STAGE_RING_FWD 0   /* ring DFT, samples -> F_m(theta_t)           */

@@ -44,6 +44,12 @@ SIGNATURES = {
     "s2let_plan_stage_stats": (_i, [_vp, _i, _i64p, _i64p, ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "s2let_sht_inverse_noalloc": (_i, [_i, _i, _i, _vp, _vp, _vp]),
+    "s2let_batch_create": (_i, [ctypes.POINTER(_vp), _i, _ip, _ip, _i, _i]),
+    "s2let_batch_destroy": (_i, [_vp]),
+    "s2let_batch_sizes": (_i, [_vp, _i64p, _i64p, _i64p, _ip]),
+    "s2let_batch_map_layout": (_i, [_vp, _i, _i64p, _i64p, _ip, _ip]),
+    "s2let_batch_group_plan": (_i, [_vp, _i, ctypes.POINTER(_vp), _i64p, _i64p, _i64p]),
+    "s2let_batch_round_trip": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "s2let_strerror": (ctypes.c_char_p, [_i]),
 }
 

@@ -33,6 +33,7 @@ using namespace s2g;
 namespace {
 
 constexpr int kMaxL = 2048;
+constexpr int kMaxM = 8192;   // FFT length for kMaxL (next power of two >= 4 kMaxL - 3)
 
 int fft_threads(int M) { return std::max(32, std::min(1024, M / 16)); }
 
@@ -738,7 +739,10 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
         Mmax = std::max(Mmax, bd.M);
         p->bands[N] = bd;
     }
-    set_smem_limits(Mmax);
+    // kernel attributes are process-wide: set them for the largest supported
+    // transform, so that a later, smaller plan cannot lower them under an earlier one
+    (void)Mmax;
+    set_smem_limits(kMaxM);
     // workspace: two L-rectangles of complex values per map
     const size_t ws = (size_t)batch * nmi(p.get(), L) * L * 2 * elem_size(p.get());
     if (cudaMalloc(&p->F, ws) != cudaSuccess) return S2LET_ERR_ALLOC;

@@ -168,3 +168,84 @@ class Plan:
         o = self._chk(f, self._map_numel(self.L), "f")
         check("s2let_sht_inverse", _lib.lib().s2let_sht_inverse(self._h, a, o, _stream_handle(stream)))
         return f
+
+
+class BatchPlan:
+    """Maps of uneven band-limit L_i and dilation B_i (same J_min, real/complex and
+    precision), transformed together: one plan per (L, B) group, and one CUDA
+    graph (captured on the first call for a set of buffers) replays the round
+    trip of every group with a single launch."""
+
+    def __init__(self, Ls, Bs, J_min, real=True, multires=True, precision="fp32", device=None):
+        Ls = [int(x) for x in Ls]
+        Bs = [int(x) for x in Bs]
+        if len(Ls) != len(Bs) or not Ls:
+            raise ValueError("need equally long, non-empty L and B lists")
+        flags = (0 if real else S2LET_COMPLEX) | (S2LET_MULTIRES if multires else 0) | PRECISIONS[precision]
+        self.Ls, self.Bs, self.J_min, self.real = Ls, Bs, J_min, real
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self._h = ctypes.c_void_p()
+        lib = _lib.lib()
+        arrL = (ctypes.c_int * len(Ls))(*Ls)
+        arrB = (ctypes.c_int * len(Bs))(*Bs)
+        with torch.cuda.device(self.device):
+            check("s2let_batch_create", lib.s2let_batch_create(ctypes.byref(self._h), len(Ls), arrL, arrB, J_min,
+                                                               flags))
+        fe, we, se, ng = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        check("s2let_batch_sizes", lib.s2let_batch_sizes(self._h, ctypes.byref(fe), ctypes.byref(we),
+                                                         ctypes.byref(se), ctypes.byref(ng)))
+        self.f_elems, self.wav_elems, self.scal_elems, self.n_groups = fe.value, we.value, se.value, ng.value
+        self.layout = []
+        for i in range(len(Ls)):
+            fo, so, g, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+            check("s2let_batch_map_layout", lib.s2let_batch_map_layout(self._h, i, ctypes.byref(fo), ctypes.byref(so),
+                                                                       ctypes.byref(g), ctypes.byref(k)))
+            self.layout.append((fo.value, so.value, g.value, k.value))
+        self.groups = []
+        for g in range(self.n_groups):
+            ph, fo, wo, so = ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+            check("s2let_batch_group_plan", lib.s2let_batch_group_plan(self._h, g, ctypes.byref(ph), ctypes.byref(fo),
+                                                                       ctypes.byref(wo), ctypes.byref(so)))
+            self.groups.append((ph.value, fo.value, wo.value, so.value))
+
+    def close(self):
+        if self._h:
+            _lib.lib().s2let_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def map_numel(self, L):
+        n = L * (2 * L - 1)
+        return n if self.real else 2 * n
+
+    def buffers(self):
+        """Flat (f, f_wav, f_scal, f_out) device buffers in the batch layout."""
+        mk = lambda n: torch.empty(n, dtype=self.dtype, device=self.device)  # noqa: E731
+        return mk(self.f_elems), mk(self.wav_elems), mk(self.scal_elems), mk(self.f_elems)
+
+    def map_view(self, flat, i):
+        """Map i of a flat f / f_out buffer, shaped (L, 2L-1[, 2])."""
+        L = self.Ls[i]
+        off = self.layout[i][0]
+        shape = (L, 2 * L - 1) if self.real else (L, 2 * L - 1, 2)
+        return flat[off:off + self.map_numel(L)].view(shape)
+
+    def round_trip(self, f, f_wav, f_scal, f_out, stream=None):
+        """Analysis then synthesis of every map, as one graph launch."""
+        for t, n, name in ((f, self.f_elems, "f"), (f_wav, self.wav_elems, "f_wav"), (f_scal, self.scal_elems, "f_scal"),
+                           (f_out, self.f_elems, "f_out")):
+            if not (t.is_cuda and t.dtype == self.dtype and t.is_contiguous() and t.numel() == n):
+                raise ValueError("%s: need a contiguous %s CUDA tensor with %d elements" % (name, self.dtype, n))
+        s = stream if stream is not None else torch.cuda.current_stream()
+        if s == torch.cuda.default_stream(self.device):
+            raise ValueError("round_trip needs a non-default stream (the work is captured into a CUDA graph)")
+        check("s2let_batch_round_trip", _lib.lib().s2let_batch_round_trip(
+            self._h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(f_wav.data_ptr()),
+            ctypes.c_void_p(f_scal.data_ptr()), ctypes.c_void_p(f_out.data_ptr()), ctypes.c_void_p(s.cuda_stream)))
+        return f_out

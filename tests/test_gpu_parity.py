@@ -97,3 +97,13 @@ def test_adjoint_against_oracle(L, B, J0, multires, real, prec):
     got = from_dev_map(plan.adjoint(fw, fs), real)
     want = np.stack([wavelet.analysis_adjoint(gws[b], gss[b], L, B, J0, multires, real) for b in range(2)])
     assert rel_err(got, want) < TOL[prec]
+
+
+def test_plans_of_different_sizes_coexist():
+    """A smaller plan created after a larger one must not break the larger one."""
+    big = Plan(200, 2, 1, batch=1, real=True, precision="fp32")
+    small = Plan(8, 2, 1, batch=1, real=True, precision="fp32")
+    for plan, L in ((big, 200), (small, 8), (big, 200)):
+        flm = inputs.random_flm(L, 3, True)
+        f = from_dev_map(plan.sht_inverse(flm_to_dev(flm[None], plan.dtype)), True)
+        assert rel_err(f[0], sht.inverse(flm, L, real=True)) < TOL["fp32"]
