@@ -5,8 +5,9 @@
 //
 // Tables per band-limit N (all precomputed on the host in FP64):
 //   chirp[n]  = e^{i pi n^2 / P},               n < P
-//   bhat[k]   = FFT_M(b), b_j = chirp_|j| for |j| < P (indices mod M)
-//   what[k]   = FFT_M(v), v_s = w(s) = int_0^pi e^{i s theta} sin theta dtheta, |s| <= 2N-2
+//   bhat[k]   = FFT_M(b), b_j = chirp_|j| for |j| < P (indices mod M), stored bit-reversed
+//   what[k]   = FFT_M(v), v_s = w(s) = int_0^pi e^{i s theta} sin theta dtheta, |s| <= 2N-2,
+//               stored bit-reversed
 //   tw[k]     = e^{-2 pi i k / M},              k < M/2
 //   phase[k+N-1] = e^{i pi k / P},              |k| <= N-1
 // M = next power of two >= max(4N-3, 2) serves both the Bluestein DFTs and
@@ -25,22 +26,34 @@ template <typename C> struct FftTab {
     int N, P, M, logM;
 };
 
-// In-place radix-2 decimation-in-time FFT of length M in shared memory.
-// INV = false: sum_j a_j e^{-2 pi i jk/M}; INV = true: e^{+...}; unnormalised.
-template <typename C, bool INV>
-__device__ void smem_fft(C *a, int M, int logM, const C *__restrict__ tw)
+// In-place radix-2 FFTs of length M in shared memory, without a permutation
+// pass: the forward transform is decimation in frequency (natural-order input,
+// bit-reversed output), the inverse is decimation in time (bit-reversed input,
+// natural-order output), and the pointwise product between them uses kernel
+// tables stored in bit-reversed order.  Unnormalised.
+// fft_dif: b_k = sum_j a_j e^{-2 pi i jk/M}, stored at position bitrev(k).
+template <typename C>
+__device__ void fft_dif(C *a, int M, int logM, const C *__restrict__ tw)
 {
-    if (logM > 0) {
-        for (int i = threadIdx.x; i < M; i += blockDim.x) {
-            int j = (int)(__brev((unsigned)i) >> (32 - logM));
-            if (i < j) {
-                C t = a[i];
-                a[i] = a[j];
-                a[j] = t;
-            }
+    for (int s = 1; s <= logM; ++s) {
+        const int lh = logM - s;           // half = 2^lh
+        const int half = 1 << lh;
+        for (int j = threadIdx.x; j < (M >> 1); j += blockDim.x) {
+            const int k = j & (half - 1);
+            const int i1 = ((j >> lh) << (lh + 1)) + k;
+            const int i2 = i1 + half;
+            const C u = a[i1], v = a[i2];
+            a[i1] = cadd(u, v);
+            a[i2] = cmul(csub(u, v), tw[k << (s - 1)]);   // e^{-2 pi i k / (2 half)}
         }
+        __syncthreads();
     }
-    __syncthreads();
+}
+
+// ifft_dit: a_j = sum_k b_k e^{+2 pi i jk/M} from b stored in bit-reversed order.
+template <typename C>
+__device__ void ifft_dit(C *a, int M, int logM, const C *__restrict__ tw)
+{
     for (int s = 1; s <= logM; ++s) {
         const int half = 1 << (s - 1);
         const int stride = M >> s;
@@ -48,10 +61,8 @@ __device__ void smem_fft(C *a, int M, int logM, const C *__restrict__ tw)
             const int k = j & (half - 1);
             const int i1 = ((j >> (s - 1)) << s) + k;
             const int i2 = i1 + half;
-            C w = tw[k * stride];
-            if (INV) w.y = -w.y;
-            C u = a[i1];
-            C v = cmul(w, a[i2]);
+            const C u = a[i1];
+            const C v = cmulc(a[i2], tw[k * stride]);           // times e^{+2 pi i k / (2 half)}
             a[i1] = cadd(u, v);
             a[i2] = csub(u, v);
         }
@@ -59,17 +70,18 @@ __device__ void smem_fft(C *a, int M, int logM, const C *__restrict__ tw)
     }
 }
 
-// buf := IFFT_M( FFT_M(buf) * K ), K = khat or conj(khat); unnormalised.
+// buf := IFFT_M( FFT_M(buf) * K ), K = khat or conj(khat) (khat stored bit-reversed); unnormalised.
 template <typename C, bool CONJ_K>
 __device__ void conv_core(C *buf, const FftTab<C> &T, const C *__restrict__ khat)
 {
-    smem_fft<C, false>(buf, T.M, T.logM, T.tw);
+    __syncthreads();
+    fft_dif<C>(buf, T.M, T.logM, T.tw);
     for (int i = threadIdx.x; i < T.M; i += blockDim.x) {
         C k = khat[i];
         buf[i] = CONJ_K ? cmulc(buf[i], k) : cmul(buf[i], k);
     }
     __syncthreads();
-    smem_fft<C, true>(buf, T.M, T.logM, T.tw);
+    ifft_dit<C>(buf, T.M, T.logM, T.tw);
 }
 
 template <typename R> __device__ __forceinline__ R inv_m(int M) { return (R)1 / (R)M; }

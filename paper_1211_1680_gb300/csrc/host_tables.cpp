@@ -145,6 +145,22 @@ int jmax(int L, int B)
 }
 
 // ------------------------------------------------------------ band tables
+// out[bitrev(k)] = a[k]: the layout the device FFTs multiply in.
+static std::vector<cd> bit_reversed(const std::vector<cd> &a)
+{
+    const size_t n = a.size();
+    int bits = 0;
+    while (((size_t)1 << bits) < n) ++bits;
+    std::vector<cd> out(n);
+    for (size_t k = 0; k < n; ++k) {
+        size_t r = 0;
+        for (int b = 0; b < bits; ++b)
+            if (k & ((size_t)1 << b)) r |= (size_t)1 << (bits - 1 - b);
+        out[r] = a[k];
+    }
+    return out;
+}
+
 void build_band(int N, Band &bd)
 {
     const int P = 2 * N - 1;
@@ -167,7 +183,7 @@ void build_band(int N, Band &bd)
     for (int j = 0; j < P; ++j) b[j] = bd.chirp[j];
     for (int j = 1; j < P; ++j) b[M - j] = bd.chirp[j];
     fft_pow2(b, -1);
-    bd.bhat = b;
+    bd.bhat = bit_reversed(b);
     // w(p) = int_0^pi e^{i p theta} sin(theta) dtheta
     std::vector<cd> v(M, cd(0.0, 0.0));
     for (int p = -(2 * N - 2); p <= 2 * N - 2; ++p) {
@@ -178,7 +194,7 @@ void build_band(int N, Band &bd)
         v[((p % M) + M) % M] = w;
     }
     fft_pow2(v, -1);
-    bd.what = v;
+    bd.what = bit_reversed(v);
     bd.tw.resize(M / 2);
     for (int k = 0; k < M / 2; ++k) {
         sincospi_rat(2 * (int64_t)k, M, &s, &c);

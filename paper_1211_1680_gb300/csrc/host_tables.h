@@ -21,7 +21,8 @@ double kappa_lambda(double t, double lam);
 double eta_lambda(double t, double lam);
 int jmax(int L, int B);
 
-// Per band-limit tables (see fft.cuh and legendre.cuh for their meaning).
+// Per band-limit tables (see fft.cuh and legendre.cuh for their meaning);
+// bhat and what are stored in bit-reversed order.
 struct Band {
     int N, P, M, logM;
     std::vector<cd> chirp, bhat, what, tw, phase;

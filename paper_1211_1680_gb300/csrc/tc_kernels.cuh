@@ -22,7 +22,7 @@ namespace s2g {
 constexpr int TQ_M = 128, TQ_N = 128, TQ_K = 32, TQ_THREADS = 256;
 constexpr int TQ_TILE = TQ_M * TQ_K * 4;          // bytes of one operand plane tile (16 KB)
 constexpr int TQ_STAGE = 6 * TQ_TILE;             // A1 A2 A3 B1 B2 B3
-constexpr int TQ_SMEM = 2 * TQ_STAGE + 64;        // + two mbarriers and the TMEM address
+constexpr int TQ_SMEM = 2 * TQ_STAGE + 64 + 1024; // + two mbarriers, the TMEM address, 1024-byte alignment
 
 __device__ __forceinline__ void split3(float x, float &a, float &b, float &c)
 {
@@ -41,7 +41,9 @@ static __global__ void __launch_bounds__(TQ_THREADS, 1) k_quad_tc(const float *_
                                                                   float2 *__restrict__ G, int N, int nmi, int mi0,
                                                                   int nj, int npairs, int *err)
 {
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem_dyn[];
+    // operand tiles need 1024-byte alignment for the 128-byte swizzle
+    unsigned char *smem = smem_dyn + ((1024 - (tc::smem_addr(smem_dyn) & 1023)) & 1023);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * TQ_STAGE);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + 2 * TQ_STAGE + 16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -87,16 +89,23 @@ static __global__ void __launch_bounds__(TQ_THREADS, 1) k_quad_tc(const float *_
         unsigned char *st = smem + s * TQ_STAGE;
         if (c >= 2) drain(c - 2);        // frees shared stage s and TMEM buffer s
         const int k0 = c * TQ_K;
-        // A planes: one (plane, row, group of 4 K) per step, straight copies
-        for (int u = tid; u < 3 * TQ_M * (TQ_K / 4); u += TQ_THREADS) {
-            const int pl = u / (TQ_M * 8), rem = u % (TQ_M * 8);
-            const int r = rem >> 3, kg = rem & 7;
+        // all global loads of this chunk first (8 consecutive threads read 128 or
+        // 256 contiguous bytes), then the split and the swizzled stores, which
+        // are conflict-free for the same 8 threads
+        constexpr int NA = 3 * TQ_M * (TQ_K / 4) / TQ_THREADS;       // 12 float4 of Q3 per thread
+        constexpr int NB = (TQ_N / 2) * (TQ_K / 4) / TQ_THREADS;     // 2 (pair, group of 4 K) per thread
+        float4 av[NA];
+        float2 bv[NB][4];
+#pragma unroll
+        for (int i = 0; i < NA; ++i) {
+            const int u = tid + i * TQ_THREADS;
+            const int kg = u & 7, r = (u >> 3) & (TQ_M - 1), pl = u >> 10;
             const int rr = row0 + r, kk = k0 + kg * 4;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (rr < N) {
                 const float *q = Q3 + pl * plane + (size_t)rr * N + kk;
                 if (vec && kk + 3 < N) {
-                    v = *reinterpret_cast<const float4 *>(q);
+                    v = __ldg(reinterpret_cast<const float4 *>(q));
                 } else {
                     v.x = kk < N ? q[0] : 0.f;
                     v.y = kk + 1 < N ? q[1] : 0.f;
@@ -104,34 +113,43 @@ static __global__ void __launch_bounds__(TQ_THREADS, 1) k_quad_tc(const float *_
                     v.w = kk + 3 < N ? q[3] : 0.f;
                 }
             }
-            *reinterpret_cast<float4 *>(st + pl * TQ_TILE + tc::kmajor_off(r, kg * 4)) = v;
+            av[i] = v;
         }
-        // B planes: columns 2p (re) and 2p+1 (im) of pair p, one (pair, group of 4 K) per step
-        for (int u = tid; u < (TQ_N / 2) * (TQ_K / 4); u += TQ_THREADS) {
-            const int p = u & 63, kg = u >> 6;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int u = tid + i * TQ_THREADS;
+            const int kg = u & 7, p = u >> 3;
             const int pp = pair0 + p, kk = k0 + kg * 4;
-            float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) bv[i][q] = make_float2(0.f, 0.f);
             if (pp < npairs) {
                 const int b = pp / nj, j = pp % nj;
                 const float2 *row = F + ((size_t)b * nmi + mi0 + 2 * j) * N + kk;
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    if (kk + q < N) {
-                        const float2 v = row[q];
-                        re[q] = v.x;
-                        im[q] = v.y;
-                    }
+                    if (kk + q < N) bv[i][q] = row[q];
             }
+        }
+#pragma unroll
+        for (int i = 0; i < NA; ++i) {
+            const int u = tid + i * TQ_THREADS;
+            const int kg = u & 7, r = (u >> 3) & (TQ_M - 1), pl = u >> 10;
+            *reinterpret_cast<float4 *>(st + pl * TQ_TILE + tc::sw128_off(r, kg * 4)) = av[i];
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int u = tid + i * TQ_THREADS;
+            const int kg = u & 7, p = u >> 3;
             float4 r1, r2, r3, i1, i2, i3;
-            split3(re[0], r1.x, r2.x, r3.x);
-            split3(re[1], r1.y, r2.y, r3.y);
-            split3(re[2], r1.z, r2.z, r3.z);
-            split3(re[3], r1.w, r2.w, r3.w);
-            split3(im[0], i1.x, i2.x, i3.x);
-            split3(im[1], i1.y, i2.y, i3.y);
-            split3(im[2], i1.z, i2.z, i3.z);
-            split3(im[3], i1.w, i2.w, i3.w);
-            const uint32_t o0 = tc::kmajor_off(2 * p, kg * 4), o1 = tc::kmajor_off(2 * p + 1, kg * 4);
+            split3(bv[i][0].x, r1.x, r2.x, r3.x);
+            split3(bv[i][1].x, r1.y, r2.y, r3.y);
+            split3(bv[i][2].x, r1.z, r2.z, r3.z);
+            split3(bv[i][3].x, r1.w, r2.w, r3.w);
+            split3(bv[i][0].y, i1.x, i2.x, i3.x);
+            split3(bv[i][1].y, i1.y, i2.y, i3.y);
+            split3(bv[i][2].y, i1.z, i2.z, i3.z);
+            split3(bv[i][3].y, i1.w, i2.w, i3.w);
+            const uint32_t o0 = tc::sw128_off(2 * p, kg * 4), o1 = tc::sw128_off(2 * p + 1, kg * 4);
             *reinterpret_cast<float4 *>(st + 3 * TQ_TILE + o0) = r1;
             *reinterpret_cast<float4 *>(st + 4 * TQ_TILE + o0) = r2;
             *reinterpret_cast<float4 *>(st + 5 * TQ_TILE + o0) = r3;
@@ -148,12 +166,12 @@ static __global__ void __launch_bounds__(TQ_THREADS, 1) k_quad_tc(const float *_
             const uint32_t acc = tmem + (uint32_t)(s * TQ_N);
 #pragma unroll
             for (int ks = 0; ks < TQ_K / 8; ++ks) {
-                const uint32_t ko = ks * 256;              // K = 8 per MMA = two 128-byte core matrices
+                const uint32_t ko = ks * 32;               // K = 8 FP32 per MMA = 32 bytes of the 128-byte row
                 uint64_t a[3], bb[3];
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    a[i] = tc::smem_desc(base + i * TQ_TILE + ko, 128, 1024);
-                    bb[i] = tc::smem_desc(base + (3 + i) * TQ_TILE + ko, 128, 1024);
+                    a[i] = tc::smem_desc_sw128(base + i * TQ_TILE + ko);
+                    bb[i] = tc::smem_desc_sw128(base + (3 + i) * TQ_TILE + ko);
                 }
                 // smallest terms first
                 tc::mma_tf32(acc, a[0], bb[2], IDESC, ks > 0 ? 1u : 0u);

@@ -20,6 +20,28 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)
 // byte offset of element (row r, k) in a K-major no-swizzle tile with K = 32 per row group
 __device__ __forceinline__ uint32_t kmajor_off(int r, int k) { return (r >> 3) * 1024 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4; }
 
+// byte offset of element (row r, k) in a K-major tile with the 128-byte swizzle:
+// rows of 32 FP32 values (128 bytes), 8-row atoms of 1024 bytes, the 16-byte
+// chunk index XORed with the row index inside the atom.  Tile base 1024-aligned.
+__device__ __forceinline__ uint32_t sw128_off(int r, int k)
+{
+    return (r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 2) ^ r) & 7) << 4) + (k & 3) * 4;
+}
+
+// Descriptor of a K-major SWIZZLE_128B tile: SBO = 1024 (8-row atoms), LBO
+// unused (1), layout type 2.  A K step inside the 128-byte row adds its byte
+// offset to the start address.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
 // 64-bit shared memory matrix descriptor (sm_100 layout): start address,
 // leading byte offset, stride byte offset (all >> 4), version 1, no swizzle.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)

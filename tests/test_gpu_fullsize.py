@@ -1,0 +1,77 @@
+"""Parity at the full L = 2048 x 64-map size, in the launch configuration that
+bench.py times (FP32 plan, B = 2, J_min = 2, multiresolution).  Inputs come from
+the oracle's inverse transform: slot b holds map (b mod 2) times a factor
+c_b = (-1)^b (1 + b/64) that differs from slot to slot, so a mix-up of slots
+shows.  Checked: wavelet maps
+on sampled rings against the oracle's direct sum of Eq. wav2 from the input
+coefficients, harmonic coefficients of sampled orders against the oracle's
+forward transform, and the exact reconstruction of every map."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import sht, wavelet  # noqa: E402
+from paper_1211_1680_gb300 import inputs  # noqa: E402
+from paper_1211_1680_gb300.s2let import Plan  # noqa: E402
+from tests.gpu_util import TOL, rel_err  # noqa: E402
+
+L, B, J0, NB = 2048, 2, 2, 64
+
+
+def _factor(b):
+    return (-1.0) ** b * (1.0 + b / NB)
+
+
+@pytest.fixture(scope="module")
+def case():
+    flm = [inputs.random_flm(L, 3000 + i, True, "cl") for i in range(2)]
+    maps = [sht.inverse(x, L, real=True) for x in flm]
+    host = np.empty((NB, L, 2 * L - 1), dtype=np.float32)
+    for b in range(NB):
+        host[b] = _factor(b) * maps[b % 2]
+    plan = Plan(L, B, J0, batch=NB, real=True, multires=True, precision="fp32")
+    x = torch.from_numpy(host).cuda()
+    fw, fs = plan.analysis(x)
+    rec = plan.synthesis(fw, fs)
+    flm_gpu = plan.sht_forward(x)
+    torch.cuda.synchronize()
+    return flm, maps, plan, x, fw, fs, rec, flm_gpu
+
+
+def test_wavelet_maps_on_sampled_rings(case):
+    flm, maps, plan, x, fw, fs, rec, _ = case
+    phi, psi = wavelet.tables(L, B, J0)
+    l_of = np.repeat(np.arange(L), 2 * np.arange(L) + 1)
+    norm = np.sqrt(4 * np.pi / (2 * l_of + 1))
+    views = plan.wavelet_views(fw)
+    kerns = [(plan.N_scal, phi, fs)] + [(n, p, v) for (_, n, _, _), p, v in zip(plan.scales, psi, views)]
+    for b in (0, 1, 30, NB - 1):
+        src = b % 2
+        for n, kern, v in kerns:
+            rings = sorted({0, 1, n // 4, n // 2, n - 2, n - 1} & set(range(n)))
+            wlm = _factor(b) * (norm * flm[src] * kern[l_of])[:n * n]
+            ref = sht.inverse_at(wlm, n, rings, np.arange(2 * n - 1)).real
+            full = v[b].double().abs().max().item()
+            got = v[b].double().cpu().numpy()[rings]
+            assert np.max(np.abs(got - ref)) / full < TOL["fp32"], (b, n)
+
+
+def test_coefficients_of_sampled_orders(case):
+    flm, maps, plan, x, fw, fs, rec, flm_gpu = case
+    g = flm_gpu[0].double().cpu().numpy()
+    g = g[:, 0] + 1j * g[:, 1]
+    for m in (0, 1, 2, 17, 640, 1500, 2046, 2047):
+        ref = sht.forward_m(maps[0], L, m)
+        l = np.arange(m, L)
+        got = g[l * l + l + m]
+        # normwise over all coefficients of the map (small high-l coefficients
+        # carry the same absolute error as large ones)
+        assert np.max(np.abs(got - ref)) / np.max(np.abs(flm[0])) < TOL["fp32"], m
+
+
+def test_reconstruction_of_every_map(case):
+    _, _, plan, x, fw, fs, rec, _ = case
+    err = ((rec - x).abs().amax(dim=(1, 2)) / x.abs().amax(dim=(1, 2))).max().item()
+    assert err < TOL["fp32"]
