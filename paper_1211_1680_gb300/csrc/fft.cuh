@@ -31,43 +31,101 @@ template <typename C> struct FftTab {
 // bit-reversed output), the inverse is decimation in time (bit-reversed input,
 // natural-order output), and the pointwise product between them uses kernel
 // tables stored in bit-reversed order.  Unnormalised.
+// Stages are fused RB at a time (RB <= 3): a thread loads the 2^RB elements one
+// butterfly group of the fused stages touches, runs the RB radix-2 stages in
+// registers and stores them back, so shared memory is read and written once per
+// three stages.  The arithmetic and the output order are those of the plain
+// radix-2 algorithms.
+// DIF pass over stages s .. s+RB-1 (first half h = 2^(logM-s)).
+template <typename C, int RB>
+__device__ __forceinline__ void dif_pass(C *a, int M, int logM, int s, const C *__restrict__ tw)
+{
+    constexpr int R = 1 << RB;
+    const int h = 1 << (logM - s);
+    const int sub = h >> (RB - 1);            // distance between the group's elements
+    for (int j = threadIdx.x; j < M / R; j += blockDim.x) {
+        const int g = j / sub, k = j - g * sub;
+        const int base = g * 2 * h + k;
+        C x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = a[base + q * sub];
+#pragma unroll
+        for (int t = 0; t < RB; ++t) {
+            const int half = h >> t;
+            const int span = R >> (t + 1);
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                if (q & span) continue;
+                const int pos = base + q * sub;
+                const C u = x[q], v = x[q + span];
+                x[q] = cadd(u, v);
+                x[q + span] = cmul(csub(u, v), tw[(pos & (half - 1)) << (s + t - 1)]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) a[base + q * sub] = x[q];
+    }
+    __syncthreads();
+}
+
+// DIT pass over stages s .. s+RB-1 (first half 2^(s-1)).
+template <typename C, int RB>
+__device__ __forceinline__ void dit_pass(C *a, int M, int logM, int s, const C *__restrict__ tw)
+{
+    constexpr int R = 1 << RB;
+    const int sub = 1 << (s - 1);             // distance between the group's elements
+    const int block = sub * R;
+    for (int j = threadIdx.x; j < M / R; j += blockDim.x) {
+        const int g = j / sub, k = j - g * sub;
+        const int base = g * block + k;
+        C x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = a[base + q * sub];
+#pragma unroll
+        for (int t = 0; t < RB; ++t) {
+            const int half = sub << t;
+            const int span = 1 << t;
+            const int stride = M >> (s + t);
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                if (q & span) continue;
+                const int pos = base + q * sub;
+                const C u = x[q];
+                const C v = cmulc(x[q + span], tw[(pos & (half - 1)) * stride]);
+                x[q] = cadd(u, v);
+                x[q + span] = csub(u, v);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) a[base + q * sub] = x[q];
+    }
+    __syncthreads();
+}
+
 // fft_dif: b_k = sum_j a_j e^{-2 pi i jk/M}, stored at position bitrev(k).
 template <typename C>
 __device__ void fft_dif(C *a, int M, int logM, const C *__restrict__ tw)
 {
-    for (int s = 1; s <= logM; ++s) {
-        const int lh = logM - s;           // half = 2^lh
-        const int half = 1 << lh;
-        for (int j = threadIdx.x; j < (M >> 1); j += blockDim.x) {
-            const int k = j & (half - 1);
-            const int i1 = ((j >> lh) << (lh + 1)) + k;
-            const int i2 = i1 + half;
-            const C u = a[i1], v = a[i2];
-            a[i1] = cadd(u, v);
-            a[i2] = cmul(csub(u, v), tw[k << (s - 1)]);   // e^{-2 pi i k / (2 half)}
-        }
-        __syncthreads();
+    int s = 1;
+    for (; s + 2 <= logM; s += 3) dif_pass<C, 3>(a, M, logM, s, tw);
+    if (s + 1 <= logM) {
+        dif_pass<C, 2>(a, M, logM, s, tw);
+        s += 2;
     }
+    if (s <= logM) dif_pass<C, 1>(a, M, logM, s, tw);
 }
 
 // ifft_dit: a_j = sum_k b_k e^{+2 pi i jk/M} from b stored in bit-reversed order.
 template <typename C>
 __device__ void ifft_dit(C *a, int M, int logM, const C *__restrict__ tw)
 {
-    for (int s = 1; s <= logM; ++s) {
-        const int half = 1 << (s - 1);
-        const int stride = M >> s;
-        for (int j = threadIdx.x; j < (M >> 1); j += blockDim.x) {
-            const int k = j & (half - 1);
-            const int i1 = ((j >> (s - 1)) << s) + k;
-            const int i2 = i1 + half;
-            const C u = a[i1];
-            const C v = cmulc(a[i2], tw[k * stride]);           // times e^{+2 pi i k / (2 half)}
-            a[i1] = cadd(u, v);
-            a[i2] = csub(u, v);
-        }
-        __syncthreads();
+    int s = 1;
+    for (; s + 2 <= logM; s += 3) dit_pass<C, 3>(a, M, logM, s, tw);
+    if (s + 1 <= logM) {
+        dit_pass<C, 2>(a, M, logM, s, tw);
+        s += 2;
     }
+    if (s <= logM) dit_pass<C, 1>(a, M, logM, s, tw);
 }
 
 // buf := IFFT_M( FFT_M(buf) * K ), K = khat or conj(khat) (khat stored bit-reversed); unnormalised.
