@@ -8,7 +8,9 @@
 //   bhat[k]   = FFT_M(b), b_j = chirp_|j| for |j| < P (indices mod M), stored bit-reversed
 //   what[k]   = FFT_M(v), v_s = w(s) = int_0^pi e^{i s theta} sin theta dtheta, |s| <= 2N-2,
 //               stored bit-reversed
-//   tw[k]     = e^{-2 pi i k / M},              k < M/2
+//   tw        per-stage twiddles, stacked: tw[M - 2h + k] = e^{-2 pi i k/(2h)}, k < h,
+//             for h = M/2, M/4, ..., 1 (M - 1 entries), so that the threads of a
+//             stage read consecutive (or equal) entries
 //   phase[k+N-1] = e^{i pi k / P},              |k| <= N-1
 // M = next power of two >= max(4N-3, 2) serves both the Bluestein DFTs and
 // the w-convolution (|a+b| <= 2N-2 for |a|, |b| <= N-1 needs M >= 4N-3).
@@ -16,6 +18,11 @@
 #include "common.cuh"
 
 namespace s2g {
+
+// Shared-memory index with one padding element after every 16, which breaks
+// the power-of-two strides of the late FFT stages across the banks.
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int padded_len(int M) { return M + (M >> 4); }
 
 template <typename C> struct FftTab {
     const C *chirp;
@@ -48,7 +55,7 @@ __device__ __forceinline__ void dif_pass(C *a, int M, int logM, int s, const C *
         const int base = g * 2 * h + k;
         C x[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) x[q] = a[base + q * sub];
+        for (int q = 0; q < R; ++q) x[q] = a[pad16(base + q * sub)];
 #pragma unroll
         for (int t = 0; t < RB; ++t) {
             const int half = h >> t;
@@ -59,11 +66,11 @@ __device__ __forceinline__ void dif_pass(C *a, int M, int logM, int s, const C *
                 const int pos = base + q * sub;
                 const C u = x[q], v = x[q + span];
                 x[q] = cadd(u, v);
-                x[q + span] = cmul(csub(u, v), tw[(pos & (half - 1)) << (s + t - 1)]);
+                x[q + span] = cmul(csub(u, v), tw[M - 2 * half + (pos & (half - 1))]);
             }
         }
 #pragma unroll
-        for (int q = 0; q < R; ++q) a[base + q * sub] = x[q];
+        for (int q = 0; q < R; ++q) a[pad16(base + q * sub)] = x[q];
     }
     __syncthreads();
 }
@@ -80,24 +87,23 @@ __device__ __forceinline__ void dit_pass(C *a, int M, int logM, int s, const C *
         const int base = g * block + k;
         C x[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) x[q] = a[base + q * sub];
+        for (int q = 0; q < R; ++q) x[q] = a[pad16(base + q * sub)];
 #pragma unroll
         for (int t = 0; t < RB; ++t) {
             const int half = sub << t;
             const int span = 1 << t;
-            const int stride = M >> (s + t);
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 if (q & span) continue;
                 const int pos = base + q * sub;
                 const C u = x[q];
-                const C v = cmulc(x[q + span], tw[(pos & (half - 1)) * stride]);
+                const C v = cmulc(x[q + span], tw[M - 2 * half + (pos & (half - 1))]);
                 x[q] = cadd(u, v);
                 x[q + span] = csub(u, v);
             }
         }
 #pragma unroll
-        for (int q = 0; q < R; ++q) a[base + q * sub] = x[q];
+        for (int q = 0; q < R; ++q) a[pad16(base + q * sub)] = x[q];
     }
     __syncthreads();
 }
@@ -136,7 +142,8 @@ __device__ void conv_core(C *buf, const FftTab<C> &T, const C *__restrict__ khat
     fft_dif<C>(buf, T.M, T.logM, T.tw);
     for (int i = threadIdx.x; i < T.M; i += blockDim.x) {
         C k = khat[i];
-        buf[i] = CONJ_K ? cmulc(buf[i], k) : cmul(buf[i], k);
+        const int pi = pad16(i);
+        buf[pi] = CONJ_K ? cmulc(buf[pi], k) : cmul(buf[pi], k);
     }
     __syncthreads();
     ifft_dit<C>(buf, T.M, T.logM, T.tw);
@@ -165,7 +172,7 @@ __global__ void k_ring_fwd_real(const R *__restrict__ f, cplx_t<R> *__restrict__
     for (int n = threadIdx.x; n < M; n += blockDim.x) {
         C v = mk((R)0, (R)0);
         if (n < P) v = cmulc(mk(r0[n], has1 ? r1[n] : (R)0), T.chirp[n]);
-        buf[n] = v;
+        buf[pad16(n)] = v;
     }
     __syncthreads();
     conv_core<C, false>(buf, T, T.bhat);
@@ -173,8 +180,8 @@ __global__ void k_ring_fwd_real(const R *__restrict__ f, cplx_t<R> *__restrict__
     C *out = F + (size_t)b * N * N;
     for (int m = threadIdx.x; m < N; m += blockDim.x) {
         const int mp = (m == 0) ? 0 : P - m;
-        C zk = cmulc(buf[m], T.chirp[m]);    // conj(c_k) * buf[k]
-        C zp = cmulc(buf[mp], T.chirp[mp]);
+        C zk = cmulc(buf[pad16(m)], T.chirp[m]);    // conj(c_k) * buf[k]
+        C zp = cmulc(buf[pad16(mp)], T.chirp[mp]);
         // X0 = (Zk + conj(Zp)) / 2, X1 = (Zk - conj(Zp)) / (2i)
         C x0 = mk((zk.x + zp.x) * s, (zk.y - zp.y) * s);
         out[(size_t)m * N + t0] = x0;
@@ -196,7 +203,7 @@ __global__ void k_ring_fwd_cplx(const cplx_t<R> *__restrict__ f, cplx_t<R> *__re
     const int b = blockIdx.y, t = blockIdx.x;
     const C *row = f + ((size_t)b * N + t) * P;
     for (int n = threadIdx.x; n < M; n += blockDim.x)
-        buf[n] = (n < P) ? cmulc(row[n], T.chirp[n]) : mk((R)0, (R)0);
+        buf[pad16(n)] = (n < P) ? cmulc(row[n], T.chirp[n]) : mk((R)0, (R)0);
     __syncthreads();
     conv_core<C, false>(buf, T, T.bhat);
     const R s = scale * inv_m<R>(M);
@@ -205,7 +212,7 @@ __global__ void k_ring_fwd_cplx(const cplx_t<R> *__restrict__ f, cplx_t<R> *__re
     for (int mi = threadIdx.x; mi < nm; mi += blockDim.x) {
         const int m = mi - (N - 1);
         const int k = m >= 0 ? m : m + P;
-        out[(size_t)mi * N + t] = cscale(cmulc(buf[k], T.chirp[k]), s);
+        out[(size_t)mi * N + t] = cscale(cmulc(buf[pad16(k)], T.chirp[k]), s);
     }
 }
 
@@ -238,7 +245,7 @@ __global__ void k_ring_inv_real(const cplx_t<R> *__restrict__ F, R *__restrict__
             C z = mk(a.x - c.y, a.y + c.x);   // a + i c
             v = cmul(z, T.chirp[k]);
         }
-        buf[k] = v;
+        buf[pad16(k)] = v;
     }
     __syncthreads();
     conv_core<C, true>(buf, T, T.bhat);
@@ -246,7 +253,7 @@ __global__ void k_ring_inv_real(const cplx_t<R> *__restrict__ F, R *__restrict__
     R *o0 = f + ((size_t)b * N + t0) * P;
     R *o1 = f + ((size_t)b * N + t1) * P;
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
-        C v = cmul(buf[p], T.chirp[p]);
+        C v = cmul(buf[pad16(p)], T.chirp[p]);
         o0[p] = v.x * s;
         if (has1) o1[p] = v.y * s;
     }
@@ -269,13 +276,13 @@ __global__ void k_ring_inv_cplx(const cplx_t<R> *__restrict__ F, cplx_t<R> *__re
             const int m = k < N ? k : k - P;
             v = cmul(in[(size_t)(m + N - 1) * N + t], T.chirp[k]);
         }
-        buf[k] = v;
+        buf[pad16(k)] = v;
     }
     __syncthreads();
     conv_core<C, true>(buf, T, T.bhat);
     const R s = scale * inv_m<R>(M);
     C *o = f + ((size_t)b * N + t) * P;
-    for (int p = threadIdx.x; p < P; p += blockDim.x) o[p] = cscale(cmul(buf[p], T.chirp[p]), s);
+    for (int p = threadIdx.x; p < P; p += blockDim.x) o[p] = cscale(cmul(buf[pad16(p)], T.chirp[p]), s);
 }
 
 // ---------------------------------------------------------------- S2: theta quadrature
@@ -314,7 +321,7 @@ __global__ void k_theta_quad(const cplx_t<R> *__restrict__ Fin, cplx_t<R> *__res
             v = cscale(ccast<C>(x[P - 1 - n]), sigma);
         }
         if (n < P) v = cmulc(v, T.chirp[n]);
-        buf[n] = v;
+        buf[pad16(n)] = v;
     }
     __syncthreads();
     conv_core<C, false>(buf, T, T.bhat);
@@ -334,14 +341,14 @@ __global__ void k_theta_quad(const cplx_t<R> *__restrict__ Fin, cplx_t<R> *__res
             if (ok) {
                 int src = (-k) % P;
                 if (src < 0) src += P;
-                v = cmul(cmulc(buf[src], T.chirp[src]), T.phase[k + N - 1]);
+                v = cmul(cmulc(buf[pad16(src)], T.chirp[src]), T.phase[k + N - 1]);
                 v = cscale(v, s);
             }
             hold[r] = v;
         }
         __syncthreads();
         r = 0;
-        for (int j = threadIdx.x; j < M; j += blockDim.x, ++r) buf[j] = hold[r];
+        for (int j = threadIdx.x; j < M; j += blockDim.x, ++r) buf[pad16(j)] = hold[r];
         __syncthreads();
     }
     conv_core<C, false>(buf, T, T.what);
@@ -353,23 +360,23 @@ __global__ void k_theta_quad(const cplx_t<R> *__restrict__ Fin, cplx_t<R> *__res
             if (n < P) {
                 const int bb = (n <= N - 1) ? n : n - P;
                 const int src = bb >= 0 ? bb : bb + M;
-                v = cmulc(cscale(buf[src], invM), T.phase[bb + N - 1]);   // H_b e^{-i pi b/P}
+                v = cmulc(cscale(buf[pad16(src)], invM), T.phase[bb + N - 1]);   // H_b e^{-i pi b/P}
                 v = cmulc(v, T.chirp[n]);
             }
             hold[r] = v;
         }
         __syncthreads();
         r = 0;
-        for (int n = threadIdx.x; n < M; n += blockDim.x, ++r) buf[n] = hold[r];
+        for (int n = threadIdx.x; n < M; n += blockDim.x, ++r) buf[pad16(n)] = hold[r];
         __syncthreads();
     }
     conv_core<C, false>(buf, T, T.bhat);
     // h_t = conj(c_t) buf_t / M; (e) fold
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
-        C h = cscale(cmulc(buf[t], T.chirp[t]), invM);
+        C h = cscale(cmulc(buf[pad16(t)], T.chirp[t]), invM);
         if (t < N - 1) {
             const int u = P - 1 - t;
-            C h2 = cscale(cmulc(buf[u], T.chirp[u]), invM);
+            C h2 = cscale(cmulc(buf[pad16(u)], T.chirp[u]), invM);
             h = cadd(h, cscale(h2, sigma));
         }
         h = cscale(h, qscale);

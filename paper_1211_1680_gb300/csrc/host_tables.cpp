@@ -195,11 +195,13 @@ void build_band(int N, Band &bd)
     }
     fft_pow2(v, -1);
     bd.what = bit_reversed(v);
-    bd.tw.resize(M / 2);
-    for (int k = 0; k < M / 2; ++k) {
-        sincospi_rat(2 * (int64_t)k, M, &s, &c);
-        bd.tw[k] = cd(c, -s);
-    }
+    // per-stage twiddles, stacked: tw[M - 2h + k] = e^{-2 pi i k / (2h)}, k < h, h = M/2 .. 1
+    bd.tw.assign(M, cd(0.0, 0.0));
+    for (int h = M / 2; h >= 1; h >>= 1)
+        for (int k = 0; k < h; ++k) {
+            sincospi_rat((int64_t)k, h, &s, &c);     // angle pi k / h = 2 pi k / (2h)
+            bd.tw[M - 2 * h + k] = cd(c, -s);
+        }
     bd.phase.resize(2 * N - 1);
     for (int k = -(N - 1); k <= N - 1; ++k) {
         sincospi_rat(k, P, &s, &c);

@@ -48,7 +48,7 @@ Layout layout(int N, int nm, int batch, int M)
     o.F = take((size_t)batch * nm * N * sizeof(float2));
     o.chirp = take((size_t)(2 * N - 1) * sizeof(float2));
     o.bhat = take((size_t)M * sizeof(float2));
-    o.tw = take((size_t)(M / 2) * sizeof(float2));
+    o.tw = take((size_t)M * sizeof(float2));
     o.phase = take((size_t)(2 * N - 1) * sizeof(float2));
     o.ls = take(nn * sizeof(int));
     o.seed = take(nn * sizeof(double2));
@@ -211,7 +211,7 @@ extern "C" int s2let_sht_inverse_noalloc(int L, int batch, int flags, const void
     T.M = d.M;
     T.logM = d.logM;
     const int th = std::max(32, std::min(1024, d.M / 16));
-    const size_t sm = (size_t)d.M * sizeof(float2);
+    const size_t sm = (size_t)padded_len(d.M) * sizeof(float2);
     if (cplx)
         k_ring_inv_cplx<float><<<dim3(L, batch), th, sm, st>>>(F, (float2 *)f, 1.0f, T);
     else

@@ -181,7 +181,7 @@ template <typename R>
 int run_ring_fwd(const s2let_plan *p, const BandDev &bd, const void *f, void *F, double scale, cudaStream_t st)
 {
     const auto &T = fft_tab<R>(bd);
-    const size_t sm = (size_t)bd.M * sizeof(cplx_t<R>);
+    const size_t sm = (size_t)padded_len(bd.M) * sizeof(cplx_t<R>);
     const int th = fft_threads(bd.M);
     StageScope sc(p, S2LET_STAGE_RING_FWD, st, 0.0, map_bytes(p, bd.N) + spectrum_bytes(p, bd.N));
     if (p->cplx) {
@@ -197,7 +197,7 @@ template <typename R>
 int run_ring_inv(const s2let_plan *p, const BandDev &bd, const void *F, void *f, double scale, cudaStream_t st)
 {
     const auto &T = fft_tab<R>(bd);
-    const size_t sm = (size_t)bd.M * sizeof(cplx_t<R>);
+    const size_t sm = (size_t)padded_len(bd.M) * sizeof(cplx_t<R>);
     const int th = fft_threads(bd.M);
     StageScope sc(p, S2LET_STAGE_RING_INV, st, 0.0, map_bytes(p, bd.N) + spectrum_bytes(p, bd.N));
     if (p->cplx) {
@@ -240,11 +240,11 @@ void *run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream
     const int th = fft_threads(bd.M);
     StageScope sc(p, S2LET_STAGE_THETA_QUAD, st, 0.0, 2.0 * spectrum_bytes(p, bd.N));
     if (p->quad64) {
-        const size_t sm = (size_t)bd.M * sizeof(double2);
+        const size_t sm = (size_t)padded_len(bd.M) * sizeof(double2);
         k_theta_quad<double, R, 16><<<dim3(n, p->batch), th, sm, st>>>((const cplx_t<R> *)F, (cplx_t<R> *)F, n, off,
                                                                        1.0, bd.fd, -1);
     } else {
-        const size_t sm = (size_t)bd.M * sizeof(float2);
+        const size_t sm = (size_t)padded_len(bd.M) * sizeof(float2);
         k_theta_quad<float, R, 16><<<dim3(n, p->batch), th, sm, st>>>((const cplx_t<R> *)F, (cplx_t<R> *)F, n, off,
                                                                       1.0f, bd.ff, -1);
     }
@@ -505,7 +505,7 @@ template <typename K> void allow_smem(K kernel, size_t bytes)
 
 void set_smem_limits(int Mmax)
 {
-    const size_t d = (size_t)Mmax * sizeof(double2), f = (size_t)Mmax * sizeof(float2);
+    const size_t d = (size_t)padded_len(Mmax) * sizeof(double2), f = (size_t)padded_len(Mmax) * sizeof(float2);
     allow_smem(k_ring_fwd_real<double>, d);
     allow_smem(k_ring_fwd_cplx<double>, d);
     allow_smem(k_ring_inv_real<double>, d);
@@ -545,7 +545,7 @@ int build_quad_matrices(s2let_plan *p, BandDev &bd)
     double2 *X = nullptr;
     if (cudaMalloc(&X, nn * sizeof(double2)) != cudaSuccess) return S2LET_ERR_ALLOC;
     cudaFuncSetAttribute(k_theta_quad<double, double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(bd.M * sizeof(double2)));
+                         (int)(padded_len(bd.M) * sizeof(double2)));
     int err = S2LET_OK;
     for (int par = 0; par < 2 && !err; ++par) {
         float *Q = nullptr;
@@ -556,7 +556,7 @@ int build_quad_matrices(s2let_plan *p, BandDev &bd)
         p->owned.push_back(Q);
         (par ? bd.Qo : bd.Qe) = Q;
         k_unit_rows<<<(unsigned)((nn + 255) / 256), 256>>>(X, N);
-        k_theta_quad<double, double, 16><<<dim3(N, 1), fft_threads(bd.M), bd.M * sizeof(double2)>>>(
+        k_theta_quad<double, double, 16><<<dim3(N, 1), fft_threads(bd.M), padded_len(bd.M) * sizeof(double2)>>>(
             X, X, N, 0, 1.0, bd.fd, par);
         k_real_to_float<<<(unsigned)((nn + 255) / 256), 256>>>(X, Q, nn);
         if (p->tc) {
