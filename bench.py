@@ -45,8 +45,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--precision", choices=["fp32", "tf32x3", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "tf32x3", "fp64"], default="tf32x3")
     ap.add_argument("--quad-fft64", action="store_true", help="FP32 plans: theta quadrature by FP64 FFTs")
+    ap.add_argument("--tc-split3", action="store_true", help="tf32x3 plans: two-part TF32 split (3 MMAs)")
     ap.add_argument("--L", type=int, default=2048)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--B", type=int, default=2)
@@ -68,7 +69,7 @@ def config(a):
     return {"workload": "real maps, L=%d, B=%d, J_min=%d, multiresolution, %d maps per GPU, f_lm ~ C_l=1/(l(l+1))"
                         % (a.L, a.B, a.J_min, a.batch),
             "L": a.L, "B": a.B, "J_min": a.J_min, "maps_per_gpu": a.batch, "multires": True, "signal": "real",
-            "precision": a.precision + ("+quad_fft64" if a.quad_fft64 else ""),
+            "precision": a.precision + ("+quad_fft64" if a.quad_fft64 else "") + ("+split3" if a.tc_split3 else ""),
             "l2": "inputs larger than L2 (map batch %.2f GB)" % (a.batch * a.L * (2 * a.L - 1)
                                                                    * (8 if a.precision == "fp64" else 4) / 1e9)}
 
@@ -241,7 +242,7 @@ def run_gpu(a, rank, world, local_rank):
     seeds = [3000 + rank * a.batch + i for i in range(a.batch)]
     flm = inputs.random_flm_batch(a.L, seeds, real=True, kind="cl")
     plan = Plan(a.L, a.B, a.J_min, batch=a.batch, real=True, multires=True, precision=a.precision,
-                quad_fft64=a.quad_fft64)
+                quad_fft64=a.quad_fft64, tc_split3=a.tc_split3)
     flm_d = torch.from_numpy(np.stack([flm.real, flm.imag], -1)).to(device="cuda", dtype=plan.dtype).contiguous()
     x = plan.sht_inverse(flm_d)
     del flm_d

@@ -57,12 +57,16 @@ extern "C" {
                                     recurrence, FP64 seeds; theta quadrature as a
                                     dense FP32 product with its matrix built in
                                     FP64                                       */
-#define S2LET_PREC_TF32X3 0x20   /* as FP32, with the dense products on the tensor
-                                    cores (tcgen05, TF32 split into hi + lo,
-                                    3 products, FP32 accumulation)            */
+#define S2LET_PREC_TF32X3 0x20   /* as FP32, with the dense quadrature product on
+                                    the tensor cores (tcgen05): operands split in
+                                    TF32 hi + lo, 3 MMAs per product, per-chunk
+                                    TMEM sums added in FP32 registers          */
 #define S2LET_PREC_MASK 0xf0
 #define S2LET_QUAD_FFT64 0x100   /* FP32 plans only: theta quadrature by FP64 FFTs
                                     instead of the dense FP32 product          */
+#define S2LET_TC_SPLIT3 0x200    /* TF32X3 plans only: split operands in three
+                                    TF32 parts (6 MMAs per product) instead of
+                                    two (3 MMAs)                               */
 
 typedef struct s2let_plan s2let_plan;
 

@@ -22,6 +22,7 @@ S2LET_PREC_FP64 = 0x00
 S2LET_PREC_FP32 = 0x10
 S2LET_PREC_TF32X3 = 0x20
 S2LET_QUAD_FFT64 = 0x100
+S2LET_TC_SPLIT3 = 0x200
 
 # every symbol the header declares, with (restype, argtypes)
 _vp = ctypes.c_void_p

@@ -89,6 +89,7 @@ struct s2let_plan {
     void *F = nullptr, *flm = nullptr, *G = nullptr;   // workspace
     bool quad_gemm = false;                 // FP32 plans: theta quadrature as a dense FP32 product
     bool tc = false;                        // TF32X3 plans: dense products on the tensor cores
+    int tc_split = 2;                       // TF32 parts per operand in the tensor-core products
     int *d_err = nullptr;                   // device error word (bounded waits)
     std::vector<void *> owned;
     // instrumentation
@@ -227,9 +228,12 @@ void *run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream
             const int nj = (n - 1 - mi0) / 2 + 1;
             const int npairs = nj * p->batch;
             dim3 grid((bd.N + QG_BM - 1) / QG_BM, (npairs + QG_BN / 2 - 1) / (QG_BN / 2));
-            if (p->tc)
-                k_quad_tc<<<grid, TQ_THREADS, TQ_SMEM, st>>>(par ? bd.Qo3 : bd.Qe3, (const float2 *)F,
-                                                             (float2 *)p->G, bd.N, n, mi0, nj, npairs, p->d_err);
+            if (p->tc && p->tc_split == 2)
+                k_quad_tc<2, 3><<<grid, TQ_THREADS, TqShape<2, 3>::SMEM, st>>>(
+                    par ? bd.Qo3 : bd.Qe3, (const float2 *)F, (float2 *)p->G, bd.N, n, mi0, nj, npairs, p->d_err);
+            else if (p->tc)
+                k_quad_tc<3, 2><<<grid, TQ_THREADS, TqShape<3, 2>::SMEM, st>>>(
+                    par ? bd.Qo3 : bd.Qe3, (const float2 *)F, (float2 *)p->G, bd.N, n, mi0, nj, npairs, p->d_err);
             else
                 k_quad_gemm<<<grid, 256, 0, st>>>(par ? bd.Qo : bd.Qe, (const float2 *)F, (float2 *)p->G, bd.N, n,
                                                   mi0, nj, npairs);
@@ -514,7 +518,8 @@ void set_smem_limits(int Mmax)
     allow_smem(k_ring_fwd_cplx<float>, f);
     allow_smem(k_ring_inv_real<float>, f);
     allow_smem(k_ring_inv_cplx<float>, f);
-    allow_smem(k_quad_tc, TQ_SMEM);
+    allow_smem(k_quad_tc<2, 3>, TqShape<2, 3>::SMEM);
+    allow_smem(k_quad_tc<3, 2>, TqShape<3, 2>::SMEM);
     allow_smem(k_leg_anal_gemm<false>, anal_gemm_smem(kMaxL));
     allow_smem(k_leg_anal_gemm<true>, anal_gemm_smem(kMaxL));
     allow_smem(k_theta_quad<double, double, 16>, d);
@@ -660,7 +665,9 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
     if (J0 < 0 || J0 >= J) return S2LET_ERR_ARG;
     const int prec = flags & S2LET_PREC_MASK;
     if (prec != S2LET_PREC_FP64 && prec != S2LET_PREC_FP32 && prec != S2LET_PREC_TF32X3) return S2LET_ERR_ARG;
-    if (flags & ~(S2LET_COMPLEX | S2LET_MULTIRES | S2LET_PREC_MASK | S2LET_QUAD_FFT64)) return S2LET_ERR_ARG;
+    if (flags & ~(S2LET_COMPLEX | S2LET_MULTIRES | S2LET_PREC_MASK | S2LET_QUAD_FFT64 | S2LET_TC_SPLIT3))
+        return S2LET_ERR_ARG;
+    if ((flags & S2LET_TC_SPLIT3) && prec != S2LET_PREC_TF32X3) return S2LET_ERR_ARG;
     if ((flags & S2LET_QUAD_FFT64) && prec == S2LET_PREC_FP64) return S2LET_ERR_ARG;
 
     std::unique_ptr<s2let_plan> p(new (std::nothrow) s2let_plan());
@@ -676,6 +683,7 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
     p->fp64 = prec == S2LET_PREC_FP64;
     p->quad64 = true;
     p->tc = prec == S2LET_PREC_TF32X3;
+    p->tc_split = (flags & S2LET_TC_SPLIT3) ? 3 : 2;
     p->quad_gemm = (prec == S2LET_PREC_FP32 || p->tc) && !(flags & S2LET_QUAD_FFT64);
     // band-limits (Sect. 3.1)
     auto ipow = [](long long b, int e) {

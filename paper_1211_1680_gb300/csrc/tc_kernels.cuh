@@ -12,17 +12,24 @@ namespace s2g {
 
 // ---------------------------------------------------------------- quadrature product
 // G[b][mi][t] = sum_t' Q[t][t'] F[b][mi][t'] for the orders mi = mi0, mi0 + 2, ...
-// Operands split three ways, x = x1 + x2 + x3 (each TF32), products kept down to
-// 2^-22 relative: x1 y1 + x1 y2 + x2 y1 + x1 y3 + x2 y2 + x3 y1 (6 MMAs per K step).
-// Q arrives pre-split (Q3 = three N x N planes, built once per plan); F is split
-// while it is stored to shared memory.
+// Operands split into S TF32 parts (x = x1 + x2 [+ x3]); the MMAs keep the
+// products down to 2^-11 (S = 2: x1 y1, x1 y2, x2 y1) or 2^-22 relative
+// (S = 3: the six products with i + j <= 4).  Q arrives pre-split (three N x N
+// planes, built once per plan); F is split while it is stored to shared memory.
 // Block: 256 threads; tile 128 rows (t) x 128 columns (64 (b, mi) pairs x re/im);
-// K (t') in chunks of 32, two shared-memory stages: while the tensor core works
-// on one chunk the threads fill the next.
+// K (t') in chunks of 32 over NS shared-memory stages: while the tensor core
+// works on one chunk the threads fill the next ones.
+// Accumulation: each K chunk accumulates into its own TMEM buffer (NS buffers of
+// 128 columns); once a chunk completes, every thread adds its 64 accumulator
+// values into FP32 registers.  Accumulating all of K in TMEM left a ~1.4e-5
+// relative error at N = 2048; per-chunk sums added with IEEE FP32 adds do not.
 constexpr int TQ_M = 128, TQ_N = 128, TQ_K = 32, TQ_THREADS = 256;
 constexpr int TQ_TILE = TQ_M * TQ_K * 4;          // bytes of one operand plane tile (16 KB)
-constexpr int TQ_STAGE = 6 * TQ_TILE;             // A1 A2 A3 B1 B2 B3
-constexpr int TQ_SMEM = 2 * TQ_STAGE + 64 + 1024; // + two mbarriers, the TMEM address, 1024-byte alignment
+template <int S, int NS> struct TqShape {
+    static constexpr int STAGE = 2 * S * TQ_TILE;
+    static constexpr int SMEM = NS * STAGE + 64 + 1024;   // + mbarriers, TMEM address, alignment
+    static constexpr int TMEM_COLS = NS * TQ_N <= 256 ? (NS * TQ_N <= 128 ? 128 : 256) : 512;
+};
 
 __device__ __forceinline__ void split3(float x, float &a, float &b, float &c)
 {
@@ -31,21 +38,18 @@ __device__ __forceinline__ void split3(float x, float &a, float &b, float &c)
     tc::split_tf32(r, b, c);
 }
 
-// Accumulation: the tensor core accumulates one K chunk (32 values, 24 MMAs) into
-// a fresh TMEM buffer (two buffers of 128 columns alternate); after the chunk
-// completes, every thread adds its 64 accumulator values of the chunk into FP32
-// registers.  Accumulating all of K in TMEM left a ~1.4e-5 relative error at
-// N = 2048; per-chunk partial sums added with IEEE FP32 adds do not.
+template <int S, int NS>
 static __global__ void __launch_bounds__(TQ_THREADS, 1) k_quad_tc(const float *__restrict__ Q3,
                                                                   const float2 *__restrict__ F,
                                                                   float2 *__restrict__ G, int N, int nmi, int mi0,
                                                                   int nj, int npairs, int *err)
 {
+    using Sh = TqShape<S, NS>;
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
     // operand tiles need 1024-byte alignment for the 128-byte swizzle
     unsigned char *smem = smem_dyn + ((1024 - (tc::smem_addr(smem_dyn) & 1023)) & 1023);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * TQ_STAGE);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + 2 * TQ_STAGE + 16);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + NS * Sh::STAGE);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + NS * Sh::STAGE + 32);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row0 = blockIdx.x * TQ_M;
     const int pair0 = blockIdx.y * (TQ_N / 2);
@@ -53,11 +57,11 @@ static __global__ void __launch_bounds__(TQ_THREADS, 1) k_quad_tc(const float *_
     constexpr uint32_t IDESC = tc::idesc_tf32(TQ_M, TQ_N);
 
     if (tid == 0) {
-        tc::mbar_init(&bar[0], 1);
-        tc::mbar_init(&bar[1], 1);
+#pragma unroll
+        for (int i = 0; i < NS; ++i) tc::mbar_init(&bar[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tc::tmem_alloc(tslot, 2 * TQ_N);
+    if (warp == 0) tc::tmem_alloc(tslot, Sh::TMEM_COLS);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
@@ -70,9 +74,9 @@ static __global__ void __launch_bounds__(TQ_THREADS, 1) k_quad_tc(const float *_
     for (int i = 0; i < 64; ++i) sum[i] = 0.f;
     bool ok = true;
     auto drain = [&](int q) {            // add chunk q's accumulator into sum
-        if (!tc::mbar_wait(&bar[q & 1], (q >> 1) & 1)) ok = false;
+        if (!tc::mbar_wait(&bar[q % NS], (q / NS) & 1)) ok = false;
         tc::fence_after();
-        const uint32_t acc = tmem + lane_addr + (uint32_t)((q & 1) * TQ_N + cbase);
+        const uint32_t acc = tmem + lane_addr + (uint32_t)((q % NS) * TQ_N + cbase);
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
             float v[16];
@@ -85,15 +89,15 @@ static __global__ void __launch_bounds__(TQ_THREADS, 1) k_quad_tc(const float *_
     const int nk = (N + TQ_K - 1) / TQ_K;
     const bool vec = (N & 3) == 0;
     for (int c = 0; c < nk; ++c) {
-        const int s = c & 1;
-        unsigned char *st = smem + s * TQ_STAGE;
-        if (c >= 2) drain(c - 2);        // frees shared stage s and TMEM buffer s
+        const int s = c % NS;
+        unsigned char *st = smem + s * Sh::STAGE;
+        if (c >= NS) drain(c - NS);      // frees shared stage s and TMEM buffer s
         const int k0 = c * TQ_K;
         // all global loads of this chunk first (8 consecutive threads read 128 or
         // 256 contiguous bytes), then the split and the swizzled stores, which
         // are conflict-free for the same 8 threads
-        constexpr int NA = 3 * TQ_M * (TQ_K / 4) / TQ_THREADS;       // 12 float4 of Q3 per thread
-        constexpr int NB = (TQ_N / 2) * (TQ_K / 4) / TQ_THREADS;     // 2 (pair, group of 4 K) per thread
+        constexpr int NA = S * TQ_M * (TQ_K / 4) / TQ_THREADS;       // float4 of Q planes per thread
+        constexpr int NB = (TQ_N / 2) * (TQ_K / 4) / TQ_THREADS;     // (pair, group of 4 K) per thread
         float4 av[NA];
         float2 bv[NB][4];
 #pragma unroll
@@ -140,22 +144,24 @@ static __global__ void __launch_bounds__(TQ_THREADS, 1) k_quad_tc(const float *_
         for (int i = 0; i < NB; ++i) {
             const int u = tid + i * TQ_THREADS;
             const int kg = u & 7, p = u >> 3;
-            float4 r1, r2, r3, i1, i2, i3;
-            split3(bv[i][0].x, r1.x, r2.x, r3.x);
-            split3(bv[i][1].x, r1.y, r2.y, r3.y);
-            split3(bv[i][2].x, r1.z, r2.z, r3.z);
-            split3(bv[i][3].x, r1.w, r2.w, r3.w);
-            split3(bv[i][0].y, i1.x, i2.x, i3.x);
-            split3(bv[i][1].y, i1.y, i2.y, i3.y);
-            split3(bv[i][2].y, i1.z, i2.z, i3.z);
-            split3(bv[i][3].y, i1.w, i2.w, i3.w);
+            float4 rp[3], ip[3];
+            float *rr = reinterpret_cast<float *>(rp), *ii = reinterpret_cast<float *>(ip);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (S == 3) {
+                    split3(bv[i][q].x, rr[q], rr[4 + q], rr[8 + q]);
+                    split3(bv[i][q].y, ii[q], ii[4 + q], ii[8 + q]);
+                } else {
+                    tc::split_tf32(bv[i][q].x, rr[q], rr[4 + q]);
+                    tc::split_tf32(bv[i][q].y, ii[q], ii[4 + q]);
+                }
+            }
             const uint32_t o0 = tc::sw128_off(2 * p, kg * 4), o1 = tc::sw128_off(2 * p + 1, kg * 4);
-            *reinterpret_cast<float4 *>(st + 3 * TQ_TILE + o0) = r1;
-            *reinterpret_cast<float4 *>(st + 4 * TQ_TILE + o0) = r2;
-            *reinterpret_cast<float4 *>(st + 5 * TQ_TILE + o0) = r3;
-            *reinterpret_cast<float4 *>(st + 3 * TQ_TILE + o1) = i1;
-            *reinterpret_cast<float4 *>(st + 4 * TQ_TILE + o1) = i2;
-            *reinterpret_cast<float4 *>(st + 5 * TQ_TILE + o1) = i3;
+#pragma unroll
+            for (int pl = 0; pl < S; ++pl) {
+                *reinterpret_cast<float4 *>(st + (S + pl) * TQ_TILE + o0) = rp[pl];
+                *reinterpret_cast<float4 *>(st + (S + pl) * TQ_TILE + o1) = ip[pl];
+            }
         }
         tc::fence_proxy_async();
         tc::fence_before();
@@ -167,25 +173,28 @@ static __global__ void __launch_bounds__(TQ_THREADS, 1) k_quad_tc(const float *_
 #pragma unroll
             for (int ks = 0; ks < TQ_K / 8; ++ks) {
                 const uint32_t ko = ks * 32;               // K = 8 FP32 per MMA = 32 bytes of the 128-byte row
-                uint64_t a[3], bb[3];
+                uint64_t a[S], bb[S];
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
+                for (int i = 0; i < S; ++i) {
                     a[i] = tc::smem_desc_sw128(base + i * TQ_TILE + ko);
-                    bb[i] = tc::smem_desc_sw128(base + (3 + i) * TQ_TILE + ko);
+                    bb[i] = tc::smem_desc_sw128(base + (S + i) * TQ_TILE + ko);
                 }
                 // smallest terms first
-                tc::mma_tf32(acc, a[0], bb[2], IDESC, ks > 0 ? 1u : 0u);
-                tc::mma_tf32(acc, a[1], bb[1], IDESC, 1u);
-                tc::mma_tf32(acc, a[2], bb[0], IDESC, 1u);
-                tc::mma_tf32(acc, a[0], bb[1], IDESC, 1u);
+                if (S == 3) {
+                    tc::mma_tf32(acc, a[0], bb[S - 1], IDESC, ks > 0 ? 1u : 0u);
+                    tc::mma_tf32(acc, a[1], bb[1], IDESC, 1u);
+                    tc::mma_tf32(acc, a[S - 1], bb[0], IDESC, 1u);
+                    tc::mma_tf32(acc, a[0], bb[1], IDESC, 1u);
+                } else {
+                    tc::mma_tf32(acc, a[0], bb[1], IDESC, ks > 0 ? 1u : 0u);
+                }
                 tc::mma_tf32(acc, a[1], bb[0], IDESC, 1u);
                 tc::mma_tf32(acc, a[0], bb[0], IDESC, 1u);
             }
             tc::mma_commit(&bar[s]);
         }
     }
-    if (nk >= 2) drain(nk - 2);
-    drain(nk - 1);
+    for (int q = nk > NS ? nk - NS : 0; q < nk; ++q) drain(q);
     // epilogue: rows t, columns (pair, re/im) from the register sums
     const int t_out = row0 + 32 * (warp & 3) + lane;
     if (ok && t_out < N) {
@@ -201,7 +210,7 @@ static __global__ void __launch_bounds__(TQ_THREADS, 1) k_quad_tc(const float *_
     if (!ok && lane == 0) atomicExch(err, 1);
     tc::fence_before();
     __syncthreads();
-    if (warp == 0) tc::tmem_free(tmem, 2 * TQ_N);
+    if (warp == 0) tc::tmem_free(tmem, Sh::TMEM_COLS);
 }
 
 // Q (FP32, N x N) -> three TF32 planes x1, x2, x3 with x = x1 + x2 + x3.

@@ -10,19 +10,19 @@ pytestmark = pytest.mark.gpu
 from oracle import kernels, sht, wavelet  # noqa: E402
 from paper_1211_1680_gb300 import inputs  # noqa: E402
 from paper_1211_1680_gb300.s2let import Plan  # noqa: E402
-from tests.gpu_util import TOL, flm_from_dev, flm_to_dev, from_dev_map, rel_err, to_dev_map  # noqa: E402
+from tests.gpu_util import TOL, flm_from_dev, flm_to_dev, from_dev_map, plan_kwargs, rel_err, to_dev_map  # noqa: E402
 
 
 def _maps(L, seeds, real, kind="white"):
     return np.stack([sht.inverse(inputs.random_flm(L, s, real, kind), L, real=real) for s in seeds])
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "tf32x3s3"])
 @pytest.mark.parametrize("real", [True, False])
 @pytest.mark.parametrize("L", [3, 4, 8, 17, 33, 64, 130])
 def test_sht_forward_inverse(L, real, prec):
     seeds = [11, 12, 13]
-    plan = Plan(L, 2, 0, batch=len(seeds), real=real, multires=True, precision=prec)
+    plan = Plan(L, 2, 0, batch=len(seeds), real=real, multires=True, **plan_kwargs(prec))
     flm = np.stack([inputs.random_flm(L, s, real) for s in seeds])
     f_ref = np.stack([sht.inverse(x, L, real=real) for x in flm])
     # inverse
@@ -56,6 +56,7 @@ CASES = [  # L, B, J0, multires, real, prec
     (96, 2, 2, True, True, "fp64"),
     (96, 2, 2, True, True, "tf32x3"),
     (40, 3, 1, True, False, "tf32x3"),
+    (96, 2, 2, True, True, "tf32x3s3"),
 ]
 
 
@@ -63,7 +64,7 @@ CASES = [  # L, B, J0, multires, real, prec
 def test_wavelet_analysis_synthesis(L, B, J0, multires, real, prec):
     seeds = [21, 22]
     f = _maps(L, seeds, real)
-    plan = Plan(L, B, J0, batch=len(seeds), real=real, multires=multires, precision=prec)
+    plan = Plan(L, B, J0, batch=len(seeds), real=real, multires=multires, **plan_kwargs(prec))
     fw_d, fs_d = plan.analysis(to_dev_map(f, plan.dtype, real))
     ref = [wavelet.analysis(x, L, B, J0, multires, real) for x in f]
     for i, view in enumerate(plan.wavelet_views(fw_d)):
