@@ -1,0 +1,545 @@
+// Legendre contractions of the TF32X3 plans on the tensor cores (tcgen05):
+//   k_leg_synth_tc  F_m(theta_t) = scale sum_l lambda_lm(theta_t) c_l f_lm     (Eq. harmonicssynthesis)
+//   k_leg_anal_tc   f_lm = scale c_l sum_t lambda_lm(theta_t) G_m(theta_t)    (last step of the MW quadrature)
+// for one order m and a tile of 128 columns (64 maps x re/im for real maps;
+// 32 maps x {m, -m} x re/im for complex maps, the layout of LegCols).
+//
+// The associated Legendre values come from the float-float recurrence of
+// legendre.cuh, are rounded to FP32 and split into TF32 hi + lo parts; so are
+// the FP32 operands of the other side.  Each 128 x 128 x 32 chunk is the sum of
+// the MMAs hi*lo + lo*hi + hi*hi accumulated in its own TMEM buffer, then added
+// into FP32 registers (the accumulation scheme of the tensor-core quadrature).
+//
+// Warp roles, synchronised by mbarriers over LT_NS shared-memory stages:
+//   warps 0-3   recurrence: write the lambda operand (A) of a stage
+//   warps 4-11  operand B (coefficients or G) of a stage, and drain the TMEM
+//               accumulator of each finished chunk into registers; epilogue
+//   warp 12     one thread issues the MMAs and commits them
+// Per stage: A hi, A lo, B hi, B lo, each a 128 x 32 FP32 tile in the K-major
+// 128-byte-swizzled layout (16 KB).  Barriers per stage s:
+//   full[s]   operands written: one arrival per writing warp (the recurrence
+//             warps that wrote A -- four in synthesis, one in analysis -- and
+//             the eight operand-B warps), after each lane's proxy fence and a
+//             warp barrier
+//   empty[s]  the chunk's MMAs have completed (tcgen05.commit): stage s free and
+//             TMEM buffer s holds the chunk's sum
+//   tempty[s] TMEM buffer s drained (one arrival per operand-B warp)
+// Every wait is bounded; a wait that runs out sets a shared abort flag, after
+// which all roles run to the end without waiting and the error word is set.
+#pragma once
+#include "common.cuh"
+#include "gemm_fp32.cuh"
+#include "legendre.cuh"
+#include "tc_kernels.cuh"
+#include "tc_sm100.cuh"
+
+namespace s2g {
+
+constexpr int LT_REC_WARPS = 4, LT_OPB_WARPS = 8, LT_MMA_WARP = LT_REC_WARPS + LT_OPB_WARPS;
+constexpr int LT_THREADS = 32 * (LT_MMA_WARP + 1);
+// analysis: recurrence warps 0-2 (one per stage), MMA warp 3, warps 4-11 as in
+// synthesis; twelve warps leave 168 registers per thread instead of 128
+constexpr int LT_ANAL_MMA_WARP = 3, LT_ANAL_THREADS = 32 * (LT_REC_WARPS + LT_OPB_WARPS);
+constexpr int LT_NS = 3;
+constexpr int LT_PLANE = TQ_TILE;                  // 128 x 32 FP32
+constexpr int LT_STAGE = 4 * LT_PLANE;
+constexpr int LT_TMEM_COLS = 512;                  // LT_NS accumulators of 128 columns
+constexpr int LT_ANAL_REC = LT_NS;                 // analysis: one recurrence warp per stage
+
+struct LtSync {
+    uint64_t full[LT_NS], empty[LT_NS], tempty[LT_NS], done;
+    uint32_t tslot;
+    int abort;
+    int lmin;
+    int nchunks;
+};
+constexpr int LT_SYNC_BYTES = 128;
+static_assert(sizeof(LtSync) <= LT_SYNC_BYTES, "sync block");
+
+// dynamic shared memory: stages, sync block, 1024-byte alignment slack, and
+// (analysis) recurrence states and per-ring-chunk minima of l_s for N rings
+__host__ __device__ constexpr size_t lt_synth_smem() { return (size_t)LT_NS * LT_STAGE + LT_SYNC_BYTES + 1024; }
+__host__ __device__ constexpr size_t lt_anal_smem(int N)
+{
+    return lt_synth_smem() + (size_t)N * sizeof(float4) + (size_t)((N + 31) / 32) * sizeof(int);
+}
+
+__device__ __forceinline__ bool lt_wait(uint64_t *bar, uint32_t parity, volatile int *abort)
+{
+    for (uint32_t i = 0; i < (1u << 22); ++i) {
+        if (tc::mbar_try_wait_hint(bar, parity, 1000)) return true;
+        if (*abort) return false;
+    }
+    *abort = 1;
+    return false;
+}
+
+// The calling warp's shared-memory writes are complete and visible to the
+// tensor core: every lane fences the async proxy, then one arrival for the warp.
+__device__ __forceinline__ void lt_warp_arrive(uint64_t *bar, int lane)
+{
+    tc::fence_proxy_async();
+    __syncwarp();
+    if (lane == 0) tc::mbar_arrive(bar);
+}
+
+__device__ __forceinline__ unsigned char *lt_align(unsigned char *p)
+{
+    return p + ((1024 - (tc::smem_addr(p) & 1023)) & 1023);
+}
+
+// Barrier set-up (thread 0) and TMEM allocation (MMA warp); ends with a CTA
+// barrier.  rec_warps: recurrence warps that arrive on full[] per chunk.
+__device__ __forceinline__ void lt_setup(LtSync &sy, int warp, int tid, int rec_warps, int mma_warp)
+{
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < LT_NS; ++i) {
+            tc::mbar_init(&sy.full[i], rec_warps + LT_OPB_WARPS);
+            tc::mbar_init(&sy.empty[i], 1);
+            tc::mbar_init(&sy.tempty[i], LT_OPB_WARPS);
+        }
+        tc::mbar_init(&sy.done, 1);
+        sy.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == mma_warp) tc::tmem_alloc(&sy.tslot, LT_TMEM_COLS);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+}
+
+// MMA issue loop (one thread): chunk c uses stage and TMEM buffer c % LT_NS.
+__device__ __forceinline__ void lt_issue(LtSync &sy, unsigned char *smem, uint32_t tmem, int nchunks)
+{
+    constexpr uint32_t IDESC = tc::idesc_tf32(128, 128);
+    volatile int *abort = &sy.abort;
+    for (int c = 0; c < nchunks; ++c) {
+        const int s = c % LT_NS;
+        bool ok = lt_wait(&sy.full[s], (c / LT_NS) & 1, abort);
+        if (c >= LT_NS) ok = lt_wait(&sy.tempty[s], ((c / LT_NS) - 1) & 1, abort) && ok;
+        tc::fence_after();
+        if (ok) {
+            const uint32_t base = tc::smem_addr(smem + s * LT_STAGE);
+            const uint32_t acc = tmem + (uint32_t)(s * 128);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                const uint32_t ko = ks * 32;
+                const uint64_t a0 = tc::smem_desc_sw128(base + ko), a1 = tc::smem_desc_sw128(base + LT_PLANE + ko);
+                const uint64_t b0 = tc::smem_desc_sw128(base + 2 * LT_PLANE + ko);
+                const uint64_t b1 = tc::smem_desc_sw128(base + 3 * LT_PLANE + ko);
+                tc::mma_tf32(acc, a0, b1, IDESC, ks > 0 ? 1u : 0u);
+                tc::mma_tf32(acc, a1, b0, IDESC, 1u);
+                tc::mma_tf32(acc, a0, b0, IDESC, 1u);
+            }
+        }
+        tc::mma_commit(&sy.empty[s]);
+    }
+    tc::mma_commit(&sy.done);
+    tc::mbar_wait(&sy.done, 0, 1u << 22);   // no MMA in flight when TMEM is released
+}
+
+// Operand-B / drain thread state: TMEM lane quadrant q = warp % 4, column half h.
+struct LtDrain {
+    float sum[64];
+    uint32_t lane_addr;
+    int h;
+    __device__ __forceinline__ void init(int warp)
+    {
+        lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+        h = (warp - LT_REC_WARPS) >> 2;
+#pragma unroll
+        for (int i = 0; i < 64; ++i) sum[i] = 0.f;
+    }
+    // add chunk c's accumulator (64 columns of this thread's lane) into sum
+    __device__ __forceinline__ void drain(LtSync &sy, uint32_t tmem, int c)
+    {
+        const int s = c % LT_NS;
+        lt_wait(&sy.empty[s], (c / LT_NS) & 1, &sy.abort);
+        tc::fence_after();
+        const uint32_t acc = tmem + lane_addr + (uint32_t)(s * 128 + 64 * h);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            float v[16];
+            tc::tmem_ld16(acc + 16 * g, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) sum[16 * g + i] += v[i];
+        }
+        tc::fence_before();
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) tc::mbar_arrive(&sy.tempty[s]);
+    }
+};
+
+// Operand B of a chunk: 64 column pairs (sign s, map b) x 32 K values read
+// from float2 rows (re, im), times an optional per-K factor, split into TF32
+// hi and lo planes.  Two halves, so that the global loads of a chunk can be in
+// flight while the thread waits for an accumulator to drain:
+//   load:  u = operand-B thread index (0..255); row(p) returns the source row
+//          of pair p shifted to the chunk's first K (nullptr: zero pair);
+//          kmax = number of valid K values; fac = per-K factors (or nullptr)
+//   store: split and write the swizzled planes of stage Bst
+struct LtB {
+    float2 v[2][4];
+    template <typename RowF> __device__ __forceinline__ void load(int u, RowF row, int kmax, const float *fac)
+    {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int unit = u + 256 * i;
+            const int kg = unit & 7, p = unit >> 3;
+            const float2 *r = row(p);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = 4 * kg + q;
+                v[i][q] = make_float2(0.f, 0.f);
+                if (r && k < kmax) {
+                    v[i][q] = r[k];
+                    if (fac) {
+                        const float f = fac[k];
+                        v[i][q].x *= f;
+                        v[i][q].y *= f;
+                    }
+                }
+            }
+        }
+    }
+    __device__ __forceinline__ void store(unsigned char *Bst, int u) const
+    {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int unit = u + 256 * i;
+            const int kg = unit & 7, p = unit >> 3;
+            float rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                tc::split_tf32(v[i][q].x, rh[q], rl[q]);
+                tc::split_tf32(v[i][q].y, ih[q], il[q]);
+            }
+            const uint32_t o0 = tc::sw128_off(2 * p, 4 * kg), o1 = tc::sw128_off(2 * p + 1, 4 * kg);
+            *reinterpret_cast<float4 *>(Bst + o0) = make_float4(rh[0], rh[1], rh[2], rh[3]);
+            *reinterpret_cast<float4 *>(Bst + o1) = make_float4(ih[0], ih[1], ih[2], ih[3]);
+            *reinterpret_cast<float4 *>(Bst + LT_PLANE + o0) = make_float4(rl[0], rl[1], rl[2], rl[3]);
+            *reinterpret_cast<float4 *>(Bst + LT_PLANE + o1) = make_float4(il[0], il[1], il[2], il[3]);
+        }
+    }
+};
+
+// Recurrence coefficient of degree l0 + j held by lane j of the warp (cf),
+// broadcast to every lane; all lanes must call it.
+__device__ __forceinline__ float4 lt_coef(const float4 &cf, int j)
+{
+    return make_float4(__shfl_sync(0xffffffffu, cf.x, j), __shfl_sync(0xffffffffu, cf.y, j),
+                       __shfl_sync(0xffffffffu, cf.z, j), __shfl_sync(0xffffffffu, cf.w, j));
+}
+
+// coefficient (a_lm, a_lm b_lm) of degree l as read by lane l - l0 (zero past the end)
+__device__ __forceinline__ float4 lt_coef_load(const float4 *cm, int l, int N)
+{
+    return l < N ? __ldg(cm + l) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ void lt_teardown(LtSync &sy, int warp, int tid, uint32_t tmem, int *err, int mma_warp)
+{
+    tc::fence_before();
+    __syncthreads();
+    if (warp == mma_warp) tc::tmem_free(tmem, LT_TMEM_COLS);
+    if (tid == 0 && sy.abort) atomicExch(err, 1);
+}
+
+// ---------------------------------------------------------------- synthesis
+// Block: (tile of 128 rings, order m, batch tile).  MMA rows = rings, K =
+// degrees in chunks of 32 from the tile's smallest l_s, columns = coefficient
+// columns.  Recurrence thread r owns ring t0 + r (row r of A).
+template <bool CPLX>
+static __global__ void __launch_bounds__(LT_THREADS, 1)
+    k_leg_synth_tc(const float2 *__restrict__ src, int Lsrc, const float *__restrict__ kfac, float scale,
+                   float2 *__restrict__ dst, int N, int B, LegTab<float> tab, int *err)
+{
+    using Cols = LegCols<CPLX>;
+    constexpr int BT = Cols::BT;
+    extern __shared__ __align__(1024) unsigned char smem_dyn[];
+    unsigned char *smem = lt_align(smem_dyn);
+    LtSync &sy = *reinterpret_cast<LtSync *>(smem + LT_NS * LT_STAGE);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int t0 = blockIdx.x * 128, m = blockIdx.y, b0 = blockIdx.z * BT;
+    const bool two = CPLX && m > 0;
+
+    int ls = N;
+    if (warp < LT_REC_WARPS && t0 + tid < N) ls = tab.ls[(size_t)m * N + t0 + tid];
+    if (tid == 0) sy.lmin = N;
+    lt_setup(sy, warp, tid, LT_REC_WARPS, LT_MMA_WARP);
+    if (warp < LT_REC_WARPS) {
+        int v = ls;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) atomicMin(&sy.lmin, v);
+    }
+    __syncthreads();
+    const int lstart = sy.lmin;
+    const int nk = lstart < N ? (N - lstart + 31) / 32 : 0;
+    const uint32_t tmem = sy.tslot;
+
+    if (warp < LT_REC_WARPS) {
+        // ------------------------------------------------ recurrence (A = lambda[ring][degree])
+        const int t = t0 + tid;
+        const bool own = t < N;
+        RecT<float> rec;
+        double2 seed = make_double2(0.0, 0.0);
+        if (own) {
+            rec.ring(tab.ring[t]);
+            seed = tab.seed[(size_t)m * N + t];
+        }
+        const float4 *cm = tab.coef + (size_t)m * tab.ldc;
+        // lane j holds the coefficient of degree l0 + j; the next chunk's is prefetched
+        float4 cf_next = lt_coef_load(cm, lstart + lane, N);
+        for (int c = 0; c < nk; ++c) {
+            const int s = c % LT_NS;
+            const float4 cf = cf_next;
+            cf_next = lt_coef_load(cm, lstart + 32 * (c + 1) + lane, N);
+            if (c >= LT_NS) lt_wait(&sy.empty[s], ((c / LT_NS) - 1) & 1, &sy.abort);
+            unsigned char *A = smem + s * LT_STAGE;
+            const int l0 = lstart + 32 * c;
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                float hi[4], lo[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int l = l0 + 4 * g + j;
+                    const float4 a = lt_coef(cf, 4 * g + j);
+                    float v = 0.f;
+                    if (own && l < N && l >= ls) {
+                        if (l == ls) {
+                            rec.seed(seed);
+                            v = rec.value();
+                        } else {
+                            v = rec.step(a);
+                        }
+                    }
+                    tc::split_tf32(v, hi[j], lo[j]);
+                }
+                const uint32_t o = tc::sw128_off(tid, 4 * g);
+                *reinterpret_cast<float4 *>(A + o) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+                *reinterpret_cast<float4 *>(A + LT_PLANE + o) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+            }
+            lt_warp_arrive(&sy.full[s], lane);
+        }
+    } else if (warp < LT_MMA_WARP) {
+        // ------------------------------------------------ operand B (c_l f_lm) and drains
+        const int u = tid - 32 * LT_REC_WARPS;
+        const int nmi_src = CPLX ? 2 * Lsrc - 1 : Lsrc;
+        LtDrain d;
+        d.init(warp);
+        int drained = 0;
+        for (int c = 0; c < nk; ++c) {
+            const int s = c % LT_NS;
+            const int l0 = lstart + 32 * c;
+            auto row = [&](int p) -> const float2 * {
+                const int sg = p / BT, b = p % BT;
+                if (b0 + b >= B || (sg == 1 && !two)) return nullptr;
+                const int mi = sg == 0 ? (CPLX ? m + Lsrc - 1 : m) : (-m + Lsrc - 1);
+                return src + ((size_t)(b0 + b) * nmi_src + mi) * Lsrc + l0;
+            };
+            LtB bv;
+            bv.load(u, row, N - l0, kfac ? kfac + l0 : nullptr);
+            while (drained <= c - LT_NS) d.drain(sy, tmem, drained++);
+            bv.store(smem + s * LT_STAGE + 2 * LT_PLANE, u);
+            lt_warp_arrive(&sy.full[s], lane);
+        }
+        while (drained < nk) d.drain(sy, tmem, drained++);
+        // epilogue: TMEM lane = ring
+        const int t = t0 + 32 * (warp & 3) + lane;
+        if (t < N && !sy.abort) {
+            const int nmi_dst = CPLX ? 2 * N - 1 : N;
+            const float sgn_m = (m & 1) ? -1.f : 1.f;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int p = 32 * d.h + j;
+                const int sg = p / BT, b = p % BT;
+                if (b0 + b >= B || (sg == 1 && !two)) continue;
+                const float f = sg == 1 ? scale * sgn_m : scale;
+                const int mi = sg == 0 ? (CPLX ? m + N - 1 : m) : (-m + N - 1);
+                dst[((size_t)(b0 + b) * nmi_dst + mi) * N + t] = make_float2(d.sum[2 * j] * f, d.sum[2 * j + 1] * f);
+            }
+        }
+    } else if (lane == 0) {
+        lt_issue(sy, smem, tmem, nk);
+    }
+    lt_teardown(sy, warp, tid, tmem, err, LT_MMA_WARP);
+}
+
+// ---------------------------------------------------------------- analysis
+// Block: (order m, batch tile).  Degree tiles of 128 from l = m (MMA rows),
+// K = rings in chunks of 32 (chunks whose rings all have l_s beyond the degree
+// tile are skipped), columns = G columns.  Recurrence warp w (< LT_ANAL_REC)
+// fills stage w: chunks c = w mod LT_NS of the sequence; lane i owns ring
+// 32 k + i and writes column i of A (one 4-byte store per degree, conflict-free
+// in the swizzled layout).  Recurrence states of all rings stay in shared memory
+// between degree tiles; the recurrence warps meet at a named barrier at the end
+// of each degree tile before the states are read again.
+template <bool CPLX>
+static __global__ void __launch_bounds__(LT_ANAL_THREADS, 1)
+    k_leg_anal_tc(const float2 *__restrict__ Gin, int N, const float *__restrict__ kfac, float scale, int accumulate,
+                  float2 *__restrict__ dst, int Ldst, int B, LegTab<float> tab, int *err)
+{
+    using Cols = LegCols<CPLX>;
+    constexpr int BT = Cols::BT;
+    extern __shared__ __align__(1024) unsigned char smem_dyn[];
+    unsigned char *smem = lt_align(smem_dyn);
+    LtSync &sy = *reinterpret_cast<LtSync *>(smem + LT_NS * LT_STAGE);
+    float4 *st = reinterpret_cast<float4 *>(smem + LT_NS * LT_STAGE + LT_SYNC_BYTES);
+    int *gmin = reinterpret_cast<int *>(st + N);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m = blockIdx.x, b0 = blockIdx.y * BT;
+    const bool two = CPLX && m > 0;
+    const int nkr = (N + 31) / 32;
+    const int ndt = (N - m + 127) / 128;
+
+    for (int k = warp; k < nkr; k += LT_ANAL_THREADS / 32) {
+        const int t = 32 * k + lane;
+        int v = t < N ? tab.ls[(size_t)m * N + t] : N;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) gmin[k] = v;
+    }
+    lt_setup(sy, warp, tid, 1, LT_ANAL_MMA_WARP);
+    if (warp == 0) {
+        // ring chunk k is processed in the degree tiles dt >= (gmin[k] - m) / 128
+        // (l_s >= m always), none when gmin[k] = N
+        int n = 0;
+        for (int k = lane; k < nkr; k += 32)
+            if (gmin[k] < N) n += ndt - (gmin[k] - m) / 128;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+        if (lane == 0) sy.nchunks = n;
+    }
+    __syncthreads();
+    const uint32_t tmem = sy.tslot;
+
+    if (warp < LT_ANAL_REC) {
+        // ------------------------------------------------ recurrence (A = lambda[degree][ring])
+        {
+            const float4 *cm = tab.coef + (size_t)m * tab.ldc;
+            int c = 0;
+            for (int dt = 0; dt < ndt; ++dt) {
+                const int l0 = m + 128 * dt;
+                const int lend = min(N, l0 + 128);
+                // lane j holds the coefficients of degrees l0 + 32 i + j, i = 0..3
+                const float4 cf0 = lt_coef_load(cm, l0 + lane, lend), cf1 = lt_coef_load(cm, l0 + 32 + lane, lend);
+                const float4 cf2 = lt_coef_load(cm, l0 + 64 + lane, lend), cf3 = lt_coef_load(cm, l0 + 96 + lane, lend);
+                for (int k = 0; k < nkr; ++k) {
+                    if (gmin[k] >= lend) continue;
+                    const int cc = c++;
+                    if (cc % LT_NS != warp) continue;
+                    const int s = warp;
+                    if (cc >= LT_NS) lt_wait(&sy.empty[s], ((cc / LT_NS) - 1) & 1, &sy.abort);
+                    unsigned char *A = smem + s * LT_STAGE;
+                    const int t = 32 * k + lane;
+                    const bool own = t < N;
+                    const int ls = own ? tab.ls[(size_t)m * N + t] : N;
+                    RecT<float> rec;
+                    double2 seed = make_double2(0.0, 0.0);
+                    if (own) {
+                        rec.ring(tab.ring[t]);
+                        if (l0 > ls) {
+                            const float4 q = st[t];
+                            rec.p0.h = q.x;
+                            rec.p0.l = q.y;
+                            rec.p1.h = q.z;
+                            rec.p1.l = q.w;
+                        } else if (ls < lend) {
+                            seed = tab.seed[(size_t)m * N + t];
+                        }
+                    }
+#pragma unroll 1
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 cf = i == 0 ? cf0 : i == 1 ? cf1 : i == 2 ? cf2 : cf3;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int r = 32 * i + j;
+                            const int l = l0 + r;
+                            const float4 a = lt_coef(cf, j);
+                            float v = 0.f;
+                            if (own && l < lend && l >= ls) {
+                                if (l == ls) {
+                                    rec.seed(seed);
+                                    v = rec.value();
+                                } else {
+                                    v = rec.step(a);
+                                }
+                            }
+                            float hi, lo;
+                            tc::split_tf32(v, hi, lo);
+                            const uint32_t o = tc::sw128_off(r, lane);
+                            *reinterpret_cast<float *>(A + o) = hi;
+                            *reinterpret_cast<float *>(A + LT_PLANE + o) = lo;
+                        }
+                    }
+                    if (own && lend - 1 >= ls) st[t] = make_float4(rec.p0.h, rec.p0.l, rec.p1.h, rec.p1.l);
+                    lt_warp_arrive(&sy.full[s], lane);
+                }
+                asm volatile("bar.sync 1, %0;" ::"n"(32 * LT_ANAL_REC) : "memory");
+            }
+        }
+    } else if (warp >= LT_REC_WARPS) {
+        // ------------------------------------------------ operand B (G) and drains
+        const int u = tid - 32 * LT_REC_WARPS;
+        const int nmi_src = CPLX ? 2 * N - 1 : N;
+        const int nmi_dst = CPLX ? 2 * Ldst - 1 : Ldst;
+        const float sgn_m = (m & 1) ? -1.f : 1.f;
+        LtDrain d;
+        d.init(warp);
+        int c = 0, drained = 0;
+        for (int dt = 0; dt < ndt; ++dt) {
+            const int l0 = m + 128 * dt;
+            const int lend = min(N, l0 + 128);
+            for (int k = 0; k < nkr; ++k) {
+                if (gmin[k] >= lend) continue;
+                const int cc = c++;
+                const int s = cc % LT_NS;
+                const int t0 = 32 * k;
+                auto row = [&](int p) -> const float2 * {
+                    const int sg = p / BT, b = p % BT;
+                    if (b0 + b >= B || (sg == 1 && !two)) return nullptr;
+                    const int mi = sg == 0 ? (CPLX ? m + N - 1 : m) : (-m + N - 1);
+                    return Gin + ((size_t)(b0 + b) * nmi_src + mi) * N + t0;
+                };
+                LtB bv;
+                bv.load(u, row, N - t0, nullptr);
+                while (drained <= cc - LT_NS) d.drain(sy, tmem, drained++);
+                bv.store(smem + s * LT_STAGE + 2 * LT_PLANE, u);
+                lt_warp_arrive(&sy.full[s], lane);
+            }
+            while (drained < c) d.drain(sy, tmem, drained++);
+            // epilogue of the degree tile: TMEM lane = degree
+            const int l = l0 + 32 * (warp & 3) + lane;
+            if (l < lend && !sy.abort) {
+                const float f = scale * (kfac ? kfac[l] : 1.f);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int p = 32 * d.h + j;
+                    const int sg = p / BT, b = p % BT;
+                    if (b0 + b < B && (sg == 0 || two)) {
+                        const float fs = sg == 1 ? f * sgn_m : f;
+                        const int mi = sg == 0 ? (CPLX ? m + Ldst - 1 : m) : (-m + Ldst - 1);
+                        float2 *o = dst + ((size_t)(b0 + b) * nmi_dst + mi) * Ldst + l;
+                        float2 v = make_float2(d.sum[2 * j] * fs, d.sum[2 * j + 1] * fs);
+                        if (accumulate) {
+                            const float2 w = *o;
+                            v.x += w.x;
+                            v.y += w.y;
+                        }
+                        *o = v;
+                    }
+                    if ((j & 7) == 7) asm volatile("" ::: "memory");   // keep the loads of later pairs below
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 64; ++i) d.sum[i] = 0.f;
+        }
+    } else if (warp == LT_ANAL_MMA_WARP) {
+        if (lane == 0) lt_issue(sy, smem, tmem, sy.nchunks);
+    }
+    lt_teardown(sy, warp, tid, tmem, err, LT_ANAL_MMA_WARP);
+}
+
+}  // namespace s2g

@@ -25,6 +25,7 @@
 #include "fft.cuh"
 #include "gemm_fp32.cuh"
 #include "tc_kernels.cuh"
+#include "legendre_tc.cuh"
 #include "host_tables.h"
 #include "legendre.cuh"
 
@@ -278,7 +279,15 @@ int run_synth(const s2let_plan *p, const BandDev &bd, const void *src, const voi
         const int bt = p->cplx ? LegCols<true>::BT : LegCols<false>::BT;
         dim3 grid((bd.N + LS_RT - 1) / LS_RT, bd.N, (p->batch + bt - 1) / bt);
         const LegTab<float> tab = leg_tab<float>(p, bd);
-        if (p->cplx)
+        if (p->tc && p->cplx)
+            k_leg_synth_tc<true><<<grid, LT_THREADS, lt_synth_smem(), st>>>(
+                (const float2 *)src, p->L, (const float *)kfac, (float)scale, (float2 *)dst, bd.N, p->batch, tab,
+                p->d_err);
+        else if (p->tc)
+            k_leg_synth_tc<false><<<grid, LT_THREADS, lt_synth_smem(), st>>>(
+                (const float2 *)src, p->L, (const float *)kfac, (float)scale, (float2 *)dst, bd.N, p->batch, tab,
+                p->d_err);
+        else if (p->cplx)
             k_leg_synth_gemm<true><<<grid, 256, 0, st>>>((const float2 *)src, p->L, (const float *)kfac, (float)scale,
                                                          (float2 *)dst, bd.N, p->batch, tab);
         else
@@ -332,7 +341,15 @@ int run_anal(const s2let_plan *p, const BandDev &bd, const void *G, const void *
         dim3 grid(bd.N, (p->batch + bt - 1) / bt);
         const size_t sm = anal_gemm_smem(bd.N);
         const LegTab<float> tab = leg_tab<float>(p, bd);
-        if (p->cplx)
+        if (p->tc && p->cplx)
+            k_leg_anal_tc<true><<<grid, LT_ANAL_THREADS, lt_anal_smem(bd.N), st>>>(
+                (const float2 *)G, bd.N, (const float *)kfac, (float)scale, acc, (float2 *)dst, p->L, p->batch, tab,
+                p->d_err);
+        else if (p->tc)
+            k_leg_anal_tc<false><<<grid, LT_ANAL_THREADS, lt_anal_smem(bd.N), st>>>(
+                (const float2 *)G, bd.N, (const float *)kfac, (float)scale, acc, (float2 *)dst, p->L, p->batch, tab,
+                p->d_err);
+        else if (p->cplx)
             k_leg_anal_gemm<true><<<grid, 256, sm, st>>>((const float2 *)G, bd.N, (const float *)kfac, (float)scale,
                                                          acc, (float2 *)dst, p->L, p->batch, tab);
         else
@@ -520,6 +537,10 @@ void set_smem_limits(int Mmax)
     allow_smem(k_ring_inv_cplx<float>, f);
     allow_smem(k_quad_tc<2, 3>, TqShape<2, 3>::SMEM);
     allow_smem(k_quad_tc<3, 2>, TqShape<3, 2>::SMEM);
+    allow_smem(k_leg_synth_tc<false>, lt_synth_smem());
+    allow_smem(k_leg_synth_tc<true>, lt_synth_smem());
+    allow_smem(k_leg_anal_tc<false>, lt_anal_smem(kMaxL));
+    allow_smem(k_leg_anal_tc<true>, lt_anal_smem(kMaxL));
     allow_smem(k_leg_anal_gemm<false>, anal_gemm_smem(kMaxL));
     allow_smem(k_leg_anal_gemm<true>, anal_gemm_smem(kMaxL));
     allow_smem(k_theta_quad<double, double, 16>, d);

@@ -1,5 +1,6 @@
 """Parity at the full L = 2048 x 64-map size, in the launch configuration that
-bench.py times (FP32 plan, B = 2, J_min = 2, multiresolution).  Inputs come from
+bench.py times (TF32X3 plan, B = 2, J_min = 2, multiresolution), and with the
+FP32 plan.  Inputs come from
 the oracle's inverse transform: slot b holds map (b mod 2) times a factor
 c_b = (-1)^b (1 + b/64) that differs from slot to slot, so a mix-up of slots
 shows.  Checked: wavelet maps
@@ -25,23 +26,32 @@ def _factor(b):
 
 
 @pytest.fixture(scope="module")
-def case():
+def oracle_case():
     flm = [inputs.random_flm(L, 3000 + i, True, "cl") for i in range(2)]
     maps = [sht.inverse(x, L, real=True) for x in flm]
     host = np.empty((NB, L, 2 * L - 1), dtype=np.float32)
     for b in range(NB):
         host[b] = _factor(b) * maps[b % 2]
-    plan = Plan(L, B, J0, batch=NB, real=True, multires=True, precision="fp32")
+    return flm, maps, host
+
+
+@pytest.fixture(scope="module", params=["tf32x3", "fp32"])
+def case(request, oracle_case):
+    flm, maps, host = oracle_case
+    plan = Plan(L, B, J0, batch=NB, real=True, multires=True, precision=request.param)
     x = torch.from_numpy(host).cuda()
     fw, fs = plan.analysis(x)
     rec = plan.synthesis(fw, fs)
     flm_gpu = plan.sht_forward(x)
     torch.cuda.synchronize()
-    return flm, maps, plan, x, fw, fs, rec, flm_gpu
+    assert plan.status() == 0
+    yield request.param, flm, maps, plan, x, fw, fs, rec, flm_gpu
+    del plan, x, fw, fs, rec, flm_gpu
+    torch.cuda.empty_cache()
 
 
 def test_wavelet_maps_on_sampled_rings(case):
-    flm, maps, plan, x, fw, fs, rec, _ = case
+    prec, flm, maps, plan, x, fw, fs, rec, _ = case
     phi, psi = wavelet.tables(L, B, J0)
     l_of = np.repeat(np.arange(L), 2 * np.arange(L) + 1)
     norm = np.sqrt(4 * np.pi / (2 * l_of + 1))
@@ -55,11 +65,11 @@ def test_wavelet_maps_on_sampled_rings(case):
             ref = sht.inverse_at(wlm, n, rings, np.arange(2 * n - 1)).real
             full = v[b].double().abs().max().item()
             got = v[b].double().cpu().numpy()[rings]
-            assert np.max(np.abs(got - ref)) / full < TOL["fp32"], (b, n)
+            assert np.max(np.abs(got - ref)) / full < TOL[prec], (b, n)
 
 
 def test_coefficients_of_sampled_orders(case):
-    flm, maps, plan, x, fw, fs, rec, flm_gpu = case
+    prec, flm, maps, plan, x, fw, fs, rec, flm_gpu = case
     g = flm_gpu[0].double().cpu().numpy()
     g = g[:, 0] + 1j * g[:, 1]
     for m in (0, 1, 2, 17, 640, 1500, 2046, 2047):
@@ -68,10 +78,10 @@ def test_coefficients_of_sampled_orders(case):
         got = g[l * l + l + m]
         # normwise over all coefficients of the map (small high-l coefficients
         # carry the same absolute error as large ones)
-        assert np.max(np.abs(got - ref)) / np.max(np.abs(flm[0])) < TOL["fp32"], m
+        assert np.max(np.abs(got - ref)) / np.max(np.abs(flm[0])) < TOL[prec], m
 
 
 def test_reconstruction_of_every_map(case):
-    _, _, plan, x, fw, fs, rec, _ = case
+    prec, _, _, plan, x, fw, fs, rec, _ = case
     err = ((rec - x).abs().amax(dim=(1, 2)) / x.abs().amax(dim=(1, 2))).max().item()
-    assert err < TOL["fp32"]
+    assert err < TOL[prec]

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle on the
 same seeded inputs.  Tolerances (max relative error, normwise per result):
-1e-10 for FP64 plans, 1e-5 for FP32 plans."""
+1e-10 for FP64 plans, 1e-5 for FP32 and TF32X3 plans."""
 import numpy as np
 import pytest
 
@@ -32,6 +32,27 @@ def test_sht_forward_inverse(L, real, prec):
     g = flm_from_dev(plan.sht_forward(to_dev_map(f_ref, plan.dtype, real)))
     ref = np.stack([sht.forward(x, L) for x in f_ref])
     assert rel_err(g, ref) < TOL[prec]
+    assert plan.status() == 0
+
+
+@pytest.mark.parametrize("real,nb", [(True, 70), (False, 35)])
+def test_sht_tensor_core_tiles(real, nb):
+    """TF32X3 plan at L = 300 with two batch tiles of the tensor-core Legendre
+    kernels: three ring tiles and three degree tiles (ragged), ten ring chunks.
+    Slot b holds c_b times one of two oracle transforms."""
+    L = 300
+    flm = [inputs.random_flm(L, 41 + i, real) for i in range(2)]
+    f_ref = [sht.inverse(x, L, real=real) for x in flm]
+    c = [(-1.0) ** b * (1.0 + b / nb) for b in range(nb)]
+    plan = Plan(L, 2, 0, batch=nb, real=real, precision="tf32x3")
+    f_gpu = from_dev_map(plan.sht_inverse(flm_to_dev(np.stack([c[b] * flm[b % 2] for b in range(nb)]), plan.dtype)),
+                         real)
+    assert rel_err(f_gpu, np.stack([c[b] * f_ref[b % 2] for b in range(nb)])) < TOL["tf32x3"]
+    fwd = [sht.forward(x, L) for x in f_ref]
+    x = to_dev_map(np.stack([c[b] * f_ref[b % 2] for b in range(nb)]), plan.dtype, real)
+    g = flm_from_dev(plan.sht_forward(x))
+    assert rel_err(g, np.stack([c[b] * fwd[b % 2] for b in range(nb)])) < TOL["tf32x3"]
+    assert plan.status() == 0
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
@@ -81,11 +102,13 @@ def test_wavelet_analysis_synthesis(L, B, J0, multires, real, prec):
     want = np.stack([wavelet.synthesis(r[0], r[1], L, B, J0, multires, real) for r in ref])
     assert rel_err(rec, want) < TOL[prec]
     assert rel_err(rec, f) < TOL[prec]
+    assert plan.status() == 0
 
 
 @pytest.mark.parametrize("L,B,J0,multires,real,prec", [
     (16, 2, 1, True, True, "fp64"), (16, 2, 0, False, False, "fp64"),
     (24, 3, 1, True, True, "fp32"), (33, 2, 2, True, False, "fp32"),
+    (24, 3, 1, True, True, "tf32x3"), (140, 2, 2, True, False, "tf32x3"),
 ])
 def test_adjoint_against_oracle(L, B, J0, multires, real, prec):
     plan = Plan(L, B, J0, batch=2, real=real, multires=multires, precision=prec)
@@ -98,6 +121,7 @@ def test_adjoint_against_oracle(L, B, J0, multires, real, prec):
     got = from_dev_map(plan.adjoint(fw, fs), real)
     want = np.stack([wavelet.analysis_adjoint(gws[b], gss[b], L, B, J0, multires, real) for b in range(2)])
     assert rel_err(got, want) < TOL[prec]
+    assert plan.status() == 0
 
 
 def test_plans_of_different_sizes_coexist():
