@@ -224,6 +224,53 @@ struct LtB {
     }
 };
 
+// Branch-free float-float recurrence of one ring (the step of RecT<float>):
+// the state is zero before l_s, so the recurrence yields zeros there; at
+// l = l_s the seed pair is selected in; coefficients past the band-limit are
+// zero, and so are the values.  A ring outside the map has x = 0, no seed.
+struct LtRec {
+    ff p0, p1, x, s0, s1;
+    int ls;
+    __device__ __forceinline__ void init(bool own, const RingF *ring, const double2 *seed, const int *lsp)
+    {
+        p0.h = p0.l = p1.h = p1.l = 0.f;
+        x.h = x.l = 0.f;
+        s0 = p0;
+        s1 = p0;
+        ls = 1 << 30;
+        if (own) {
+            const RingF r = *ring;
+            x.h = r.xh;
+            x.l = r.xl;
+            ls = *lsp;
+            const double2 sd = *seed;
+            s0.h = (float)sd.x;
+            s0.l = (float)(sd.x - (double)s0.h);
+            s1.h = (float)sd.y;
+            s1.l = (float)(sd.y - (double)s1.h);
+        }
+    }
+    // value of degree l given the coefficient (a hi, a lo, a b hi, a b lo) of l
+    __device__ __forceinline__ float step(const float4 c, int l)
+    {
+        ff a, ab;
+        a.h = c.x;
+        a.l = c.y;
+        ab.h = c.z;
+        ab.l = c.w;
+        const ff ax = ff_mul(a, x);
+        const ff pa = ff_mul(ax, p1);
+        const ff pb = ff_mul(ab, p0);
+        const ff p2 = ff_sub(pa, pb);
+        const bool at = l == ls;
+        p0.h = at ? s0.h : p1.h;
+        p0.l = at ? s0.l : p1.l;
+        p1.h = at ? s1.h : p2.h;
+        p1.l = at ? s1.l : p2.l;
+        return p1.h;
+    }
+};
+
 // Recurrence coefficient of degree l0 + j held by lane j of the warp (cf),
 // broadcast to every lane; all lanes must call it.
 __device__ __forceinline__ float4 lt_coef(const float4 &cf, int j)
@@ -283,12 +330,8 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
         // ------------------------------------------------ recurrence (A = lambda[ring][degree])
         const int t = t0 + tid;
         const bool own = t < N;
-        RecT<float> rec;
-        double2 seed = make_double2(0.0, 0.0);
-        if (own) {
-            rec.ring(tab.ring[t]);
-            seed = tab.seed[(size_t)m * N + t];
-        }
+        LtRec rec;
+        rec.init(own, tab.ring + t, tab.seed + (size_t)m * N + t, tab.ls + (size_t)m * N + t);
         const float4 *cm = tab.coef + (size_t)m * tab.ldc;
         // lane j holds the coefficient of degree l0 + j; the next chunk's is prefetched
         float4 cf_next = lt_coef_load(cm, lstart + lane, N);
@@ -304,17 +347,7 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
                 float hi[4], lo[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const int l = l0 + 4 * g + j;
-                    const float4 a = lt_coef(cf, 4 * g + j);
-                    float v = 0.f;
-                    if (own && l < N && l >= ls) {
-                        if (l == ls) {
-                            rec.seed(seed);
-                            v = rec.value();
-                        } else {
-                            v = rec.step(a);
-                        }
-                    }
+                    const float v = rec.step(lt_coef(cf, 4 * g + j), l0 + 4 * g + j);
                     tc::split_tf32(v, hi[j], lo[j]);
                 }
                 const uint32_t o = tc::sw128_off(tid, 4 * g);
@@ -435,20 +468,14 @@ static __global__ void __launch_bounds__(LT_ANAL_THREADS, 1)
                     unsigned char *A = smem + s * LT_STAGE;
                     const int t = 32 * k + lane;
                     const bool own = t < N;
-                    const int ls = own ? tab.ls[(size_t)m * N + t] : N;
-                    RecT<float> rec;
-                    double2 seed = make_double2(0.0, 0.0);
-                    if (own) {
-                        rec.ring(tab.ring[t]);
-                        if (l0 > ls) {
-                            const float4 q = st[t];
-                            rec.p0.h = q.x;
-                            rec.p0.l = q.y;
-                            rec.p1.h = q.z;
-                            rec.p1.l = q.w;
-                        } else if (ls < lend) {
-                            seed = tab.seed[(size_t)m * N + t];
-                        }
+                    LtRec rec;
+                    rec.init(own, tab.ring + t, tab.seed + (size_t)m * N + t, tab.ls + (size_t)m * N + t);
+                    if (own && l0 > rec.ls) {
+                        const float4 q = st[t];
+                        rec.p0.h = q.x;
+                        rec.p0.l = q.y;
+                        rec.p1.h = q.z;
+                        rec.p1.l = q.w;
                     }
 #pragma unroll 1
                     for (int i = 0; i < 4; ++i) {
@@ -456,17 +483,7 @@ static __global__ void __launch_bounds__(LT_ANAL_THREADS, 1)
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
                             const int r = 32 * i + j;
-                            const int l = l0 + r;
-                            const float4 a = lt_coef(cf, j);
-                            float v = 0.f;
-                            if (own && l < lend && l >= ls) {
-                                if (l == ls) {
-                                    rec.seed(seed);
-                                    v = rec.value();
-                                } else {
-                                    v = rec.step(a);
-                                }
-                            }
+                            const float v = rec.step(lt_coef(cf, j), l0 + r);
                             float hi, lo;
                             tc::split_tf32(v, hi, lo);
                             const uint32_t o = tc::sw128_off(r, lane);
@@ -474,7 +491,7 @@ static __global__ void __launch_bounds__(LT_ANAL_THREADS, 1)
                             *reinterpret_cast<float *>(A + LT_PLANE + o) = lo;
                         }
                     }
-                    if (own && lend - 1 >= ls) st[t] = make_float4(rec.p0.h, rec.p0.l, rec.p1.h, rec.p1.l);
+                    if (own && lend - 1 >= rec.ls) st[t] = make_float4(rec.p0.h, rec.p0.l, rec.p1.h, rec.p1.l);
                     lt_warp_arrive(&sy.full[s], lane);
                 }
                 asm volatile("bar.sync 1, %0;" ::"n"(32 * LT_ANAL_REC) : "memory");
