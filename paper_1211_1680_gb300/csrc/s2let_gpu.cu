@@ -26,6 +26,7 @@
 #include "gemm_fp32.cuh"
 #include "tc_kernels.cuh"
 #include "legendre_tc.cuh"
+#include "quad_tc.cuh"
 #include "host_tables.h"
 #include "legendre.cuh"
 
@@ -71,7 +72,9 @@ struct BandDev {
     RingD *ringd = nullptr;
     RingF *ringf = nullptr;
     float *Qe = nullptr, *Qo = nullptr;     // FP32 plans: quadrature matrices, even / odd m
-    float *Qe3 = nullptr, *Qo3 = nullptr;   // TF32X3 plans: the same, split into three TF32 planes
+    float *Qe3 = nullptr, *Qo3 = nullptr;   // TF32X3 plans with three-part split: three TF32 planes
+    float *Qe2 = nullptr, *Qo2 = nullptr;   // TF32X3 plans: two TF32 planes, row stride ldq
+    int ldq = 0;
 };
 
 }  // namespace
@@ -230,8 +233,9 @@ void *run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream
             const int npairs = nj * p->batch;
             dim3 grid((bd.N + QG_BM - 1) / QG_BM, (npairs + QG_BN / 2 - 1) / (QG_BN / 2));
             if (p->tc && p->tc_split == 2)
-                k_quad_tc<2, 3><<<grid, TQ_THREADS, TqShape<2, 3>::SMEM, st>>>(
-                    par ? bd.Qo3 : bd.Qe3, (const float2 *)F, (float2 *)p->G, bd.N, n, mi0, nj, npairs, p->d_err);
+                k_quad_tcp<<<grid, LT_THREADS, lt_synth_smem(), st>>>(par ? bd.Qo2 : bd.Qe2, bd.ldq,
+                                                                       (const float2 *)F, (float2 *)p->G, bd.N, n,
+                                                                       mi0, nj, npairs, p->d_err);
             else if (p->tc)
                 k_quad_tc<3, 2><<<grid, TQ_THREADS, TqShape<3, 2>::SMEM, st>>>(
                     par ? bd.Qo3 : bd.Qe3, (const float2 *)F, (float2 *)p->G, bd.N, n, mi0, nj, npairs, p->d_err);
@@ -535,7 +539,7 @@ void set_smem_limits(int Mmax)
     allow_smem(k_ring_fwd_cplx<float>, f);
     allow_smem(k_ring_inv_real<float>, f);
     allow_smem(k_ring_inv_cplx<float>, f);
-    allow_smem(k_quad_tc<2, 3>, TqShape<2, 3>::SMEM);
+    allow_smem(k_quad_tcp, lt_synth_smem());
     allow_smem(k_quad_tc<3, 2>, TqShape<3, 2>::SMEM);
     allow_smem(k_leg_synth_tc<false>, lt_synth_smem());
     allow_smem(k_leg_synth_tc<true>, lt_synth_smem());
@@ -585,7 +589,7 @@ int build_quad_matrices(s2let_plan *p, BandDev &bd)
         k_theta_quad<double, double, 16><<<dim3(N, 1), fft_threads(bd.M), padded_len(bd.M) * sizeof(double2)>>>(
             X, X, N, 0, 1.0, bd.fd, par);
         k_real_to_float<<<(unsigned)((nn + 255) / 256), 256>>>(X, Q, nn);
-        if (p->tc) {
+        if (p->tc && p->tc_split == 3) {
             float *Q3 = nullptr;
             if (cudaMalloc(&Q3, 3 * nn * sizeof(float)) != cudaSuccess) {
                 err = S2LET_ERR_ALLOC;
@@ -594,6 +598,17 @@ int build_quad_matrices(s2let_plan *p, BandDev &bd)
             p->owned.push_back(Q3);
             (par ? bd.Qo3 : bd.Qe3) = Q3;
             k_split3_planes<<<(unsigned)((nn + 255) / 256), 256>>>(Q, Q3, nn);
+        } else if (p->tc) {
+            bd.ldq = (N + 3) & ~3;
+            const size_t np = (size_t)N * bd.ldq;
+            float *Q2 = nullptr;
+            if (cudaMalloc(&Q2, 2 * np * sizeof(float)) != cudaSuccess) {
+                err = S2LET_ERR_ALLOC;
+                break;
+            }
+            p->owned.push_back(Q2);
+            (par ? bd.Qo2 : bd.Qe2) = Q2;
+            k_split2_padded<<<(unsigned)((np + 255) / 256), 256>>>(Q, Q2, N, bd.ldq);
         }
         if (cudaGetLastError() != cudaSuccess) err = S2LET_ERR_CUDA;
     }
