@@ -103,7 +103,7 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
     int ls = N;
     if (warp < LT_REC_WARPS && t0 + tid < N) ls = tab.ls[(size_t)m * N + t0 + tid];
     if (tid == 0) sy.lmin = N;
-    lt_setup(sy, warp, tid, LT_REC_WARPS, LT_MMA_WARP);
+    lt_setup(sy, warp, tid, LT_REC_WARPS + LT_OPB_WARPS, LT_MMA_WARP);
     if (warp < LT_REC_WARPS) {
         int v = ls;
 #pragma unroll
@@ -223,7 +223,7 @@ static __global__ void __launch_bounds__(LT_ANAL_THREADS, 1)
         for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
         if (lane == 0) gmin[k] = v;
     }
-    lt_setup(sy, warp, tid, 1, LT_ANAL_MMA_WARP);
+    lt_setup(sy, warp, tid, 1 + LT_OPB_WARPS, LT_ANAL_MMA_WARP);
     if (warp == 0) {
         // ring chunk k is processed in the degree tiles dt >= (gmin[k] - m) / 128
         // (l_s >= m always), none when gmin[k] = N

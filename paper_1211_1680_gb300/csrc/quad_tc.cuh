@@ -1,31 +1,23 @@
 // MW theta quadrature of the TF32X3 plans as a pipelined tensor-core product
 // (tc_pipe.cuh):  G[b][mi][t] = sum_t' Q_sigma[t][t'] F[b][mi][t']  for the
 // orders mi = mi0, mi0 + 2, ... of one parity sigma.
-//   operand A  rows t of Q_sigma, pre-split into two TF32 planes (hi, and the
-//              TF32 part of the remainder) with a zero-padded row stride ldq
-//              (a multiple of 4 floats, so every row starts on 16 bytes); warps
-//              0-3 copy them into the swizzled stage layout with cp.async,
-//              two chunks in flight
-//   operand B  64 (b, mi) pairs x re/im of F, split while stored (LtB)
+//   operand A  Q_sigma, split into two TF32 planes (hi, and the TF32 part of
+//              the remainder) and stored once per plan as the exact shared-
+//              memory image of each (row tile, K chunk): two 128 x 32 tiles in
+//              the swizzled layout, 32 KB contiguous, zeros outside N x N.  One
+//              thread moves a chunk with a single bulk copy (TMA engine) whose
+//              completion is counted on the stage's full barrier
+//   operand B  64 (b, mi) pairs x re/im of F, split while stored (LtB) by
+//              warps 4-11, which also drain the accumulators and write G
 // Block: (tile of 128 rows t, tile of 64 pairs).
 #pragma once
 #include "tc_pipe.cuh"
 
 namespace s2g {
 
-constexpr int QP_LOAD_WARPS = 4;
-
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, int src_bytes)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(tc::smem_addr(smem_dst)), "l"(gsrc),
-                 "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
+constexpr int QP_IMG_CHUNK = 2 * LT_PLANE;   // bytes of one (row tile, K chunk) image
 static __global__ void __launch_bounds__(LT_THREADS, 1)
-    k_quad_tcp(const float *__restrict__ Qp, int ldq, const float2 *__restrict__ F, float2 *__restrict__ G, int N,
+    k_quad_tcp(const unsigned char *__restrict__ Qimg, const float2 *__restrict__ F, float2 *__restrict__ G, int N,
                int nmi, int mi0, int nj, int npairs, int *err)
 {
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
@@ -34,35 +26,19 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row0 = blockIdx.x * 128, pair0 = blockIdx.y * 64;
     const int nk = (N + 31) / 32;
-    lt_setup(sy, warp, tid, QP_LOAD_WARPS, LT_MMA_WARP);
+    lt_setup(sy, warp, tid, 1 + LT_OPB_WARPS, LT_MMA_WARP);
     const uint32_t tmem = sy.tslot;
 
-    if (warp < QP_LOAD_WARPS) {
-        // ------------------------------------------------ operand A: Q planes by cp.async
-        const size_t plane = (size_t)N * ldq;
-        for (int c = 0; c < nk; ++c) {
-            const int s = c % LT_NS;
-            if (c >= LT_NS) lt_wait(&sy.empty[s], ((c / LT_NS) - 1) & 1, &sy.abort);
-            unsigned char *A = smem + s * LT_STAGE;
-            const int k0 = 32 * c;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {   // 2 planes x 128 rows x 8 pieces of 16 bytes
-                const int u = tid + 128 * i;
-                const int kg = u & 7, r = (u >> 3) & 127, pl = u >> 10;
-                const int rr = row0 + r, kk = k0 + 4 * kg;
-                const bool ok = rr < N && kk < ldq;
-                const float *src = Qp + pl * plane + (ok ? (size_t)rr * ldq + kk : 0);
-                cp_async16(A + pl * LT_PLANE + tc::sw128_off(r, 4 * kg), src, ok ? 16 : 0);
+    if (warp < LT_REC_WARPS) {
+        // ------------------------------------------------ operand A: one bulk copy per chunk
+        if (tid == 0) {
+            const unsigned char *img = Qimg + (size_t)blockIdx.x * nk * QP_IMG_CHUNK;
+            for (int c = 0; c < nk; ++c) {
+                const int s = c % LT_NS;
+                if (c >= LT_NS) lt_wait(&sy.empty[s], ((c / LT_NS) - 1) & 1, &sy.abort);
+                tc::mbar_arrive_expect_tx(&sy.full[s], QP_IMG_CHUNK);
+                tc::bulk_g2s(smem + s * LT_STAGE, img + (size_t)c * QP_IMG_CHUNK, QP_IMG_CHUNK, &sy.full[s]);
             }
-            cp_async_commit();
-            if (c > 0) {
-                cp_async_wait<1>();          // this thread's copies of chunk c - 1 have landed
-                lt_warp_arrive(&sy.full[(c - 1) % LT_NS], lane);
-            }
-        }
-        if (nk > 0) {
-            cp_async_wait<0>();
-            lt_warp_arrive(&sy.full[(nk - 1) % LT_NS], lane);
         }
     } else if (warp < LT_MMA_WARP) {
         // ------------------------------------------------ operand B (F) and drains
@@ -104,20 +80,37 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
     lt_teardown(sy, warp, tid, tmem, err, LT_MMA_WARP);
 }
 
-// Q (FP32, N x N) -> planes hi, lo with row stride ldq >= N (zero padding):
-// hi = the TF32 truncation of x, lo = the TF32 truncation of x - hi.
-static __global__ void k_split2_padded(const float *__restrict__ Q, float *__restrict__ Qp, int N, int ldq)
+// Q (FP32, N x N) -> shared-memory images of operand A: for row tile rt and K
+// chunk c, plane 0 holds the TF32 truncation hi of Q[128 rt + r][32 c + k] and
+// plane 1 the TF32 truncation of the remainder, at byte sw128_off(r, k) of the
+// plane; zeros outside N x N.  One thread per 16-byte piece (4 values of k).
+static __global__ void k_quad_images(const float *__restrict__ Q, unsigned char *__restrict__ img, int N)
 {
+    const int nk = (N + 31) / 32, nrt = (N + 127) / 128;
+    const size_t npieces = (size_t)nrt * nk * 128 * 8;
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t n = (size_t)N * ldq;
-    if (i >= n) return;
-    const int r = (int)(i / ldq), k = (int)(i % ldq);
-    const float x = k < N ? Q[(size_t)r * N + k] : 0.f;
-    float hi, rem, lo, drop;
-    tc::split_tf32(x, hi, rem);
-    tc::split_tf32(rem, lo, drop);
-    Qp[i] = hi;
-    Qp[n + i] = lo;
+    if (i >= npieces) return;
+    const int kg = (int)(i & 7), r = (int)((i >> 3) & 127);
+    const size_t tile = i >> 10;                      // rt * nk + c
+    const int c = (int)(tile % nk), rt = (int)(tile / nk);
+    const int row = 128 * rt + r;
+    float hi[4], lo[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int k = 32 * c + 4 * kg + q;
+        const float x = (row < N && k < N) ? Q[(size_t)row * N + k] : 0.f;
+        float rem, drop;
+        tc::split_tf32(x, hi[q], rem);
+        tc::split_tf32(rem, lo[q], drop);
+    }
+    unsigned char *base = img + tile * QP_IMG_CHUNK + tc::sw128_off(r, 4 * kg);
+    *reinterpret_cast<float4 *>(base) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<float4 *>(base + LT_PLANE) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+}
+
+__host__ __device__ inline size_t quad_image_bytes(int N)
+{
+    return (size_t)((N + 127) / 128) * ((N + 31) / 32) * QP_IMG_CHUNK;
 }
 
 }  // namespace s2g

@@ -73,8 +73,7 @@ struct BandDev {
     RingF *ringf = nullptr;
     float *Qe = nullptr, *Qo = nullptr;     // FP32 plans: quadrature matrices, even / odd m
     float *Qe3 = nullptr, *Qo3 = nullptr;   // TF32X3 plans with three-part split: three TF32 planes
-    float *Qe2 = nullptr, *Qo2 = nullptr;   // TF32X3 plans: two TF32 planes, row stride ldq
-    int ldq = 0;
+    unsigned char *Qei = nullptr, *Qoi = nullptr;   // TF32X3 plans: operand-A images of the two-part split
 };
 
 }  // namespace
@@ -233,9 +232,9 @@ void *run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream
             const int npairs = nj * p->batch;
             dim3 grid((bd.N + QG_BM - 1) / QG_BM, (npairs + QG_BN / 2 - 1) / (QG_BN / 2));
             if (p->tc && p->tc_split == 2)
-                k_quad_tcp<<<grid, LT_THREADS, lt_synth_smem(), st>>>(par ? bd.Qo2 : bd.Qe2, bd.ldq,
-                                                                       (const float2 *)F, (float2 *)p->G, bd.N, n,
-                                                                       mi0, nj, npairs, p->d_err);
+                k_quad_tcp<<<grid, LT_THREADS, lt_synth_smem(), st>>>(par ? bd.Qoi : bd.Qei, (const float2 *)F,
+                                                                       (float2 *)p->G, bd.N, n, mi0, nj, npairs,
+                                                                       p->d_err);
             else if (p->tc)
                 k_quad_tc<3, 2><<<grid, TQ_THREADS, TqShape<3, 2>::SMEM, st>>>(
                     par ? bd.Qo3 : bd.Qe3, (const float2 *)F, (float2 *)p->G, bd.N, n, mi0, nj, npairs, p->d_err);
@@ -599,16 +598,15 @@ int build_quad_matrices(s2let_plan *p, BandDev &bd)
             (par ? bd.Qo3 : bd.Qe3) = Q3;
             k_split3_planes<<<(unsigned)((nn + 255) / 256), 256>>>(Q, Q3, nn);
         } else if (p->tc) {
-            bd.ldq = (N + 3) & ~3;
-            const size_t np = (size_t)N * bd.ldq;
-            float *Q2 = nullptr;
-            if (cudaMalloc(&Q2, 2 * np * sizeof(float)) != cudaSuccess) {
+            unsigned char *img = nullptr;
+            if (cudaMalloc(&img, quad_image_bytes(N)) != cudaSuccess) {
                 err = S2LET_ERR_ALLOC;
                 break;
             }
-            p->owned.push_back(Q2);
-            (par ? bd.Qo2 : bd.Qe2) = Q2;
-            k_split2_padded<<<(unsigned)((np + 255) / 256), 256>>>(Q, Q2, N, bd.ldq);
+            p->owned.push_back(img);
+            (par ? bd.Qoi : bd.Qei) = img;
+            const size_t npieces = quad_image_bytes(N) / 16 / 2;
+            k_quad_images<<<(unsigned)((npieces + 255) / 256), 256>>>(Q, img, N);
         }
         if (cudaGetLastError() != cudaSuccess) err = S2LET_ERR_CUDA;
     }

@@ -76,13 +76,15 @@ __device__ __forceinline__ unsigned char *lt_align(unsigned char *p)
 }
 
 // Barrier set-up (thread 0) and TMEM allocation (MMA warp); ends with a CTA
-// barrier.  rec_warps: recurrence warps that arrive on full[] per chunk.
-__device__ __forceinline__ void lt_setup(LtSync &sy, int warp, int tid, int rec_warps, int mma_warp)
+// barrier.  full_arrivals: arrivals on full[] per chunk (one per warp that
+// writes an operand, one per bulk-copy issue); the eight drain warps arrive on
+// tempty[].
+__device__ __forceinline__ void lt_setup(LtSync &sy, int warp, int tid, int full_arrivals, int mma_warp)
 {
     if (tid == 0) {
 #pragma unroll
         for (int i = 0; i < LT_NS; ++i) {
-            tc::mbar_init(&sy.full[i], rec_warps + LT_OPB_WARPS);
+            tc::mbar_init(&sy.full[i], full_arrivals);
             tc::mbar_init(&sy.empty[i], 1);
             tc::mbar_init(&sy.tempty[i], LT_OPB_WARPS);
         }

@@ -101,6 +101,30 @@ __device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parit
     return ok != 0;
 }
 
+// One arrival on *bar that also raises the phase's expected transaction count
+// by tx bytes (completed by bulk copies with complete_tx).
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t tx)
+{
+    asm volatile(
+        "{\n"
+        ".reg .b64 st;\n"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n"
+        "}\n" ::"r"(smem_addr(bar)),
+        "r"(tx)
+        : "memory");
+}
+
+// Bulk copy (TMA engine) of bytes (multiple of 16, both addresses 16-byte
+// aligned) from global memory to this CTA's shared memory; completion is
+// signalled as transactions on *bar.
+__device__ __forceinline__ void bulk_g2s(void *smem_dst, const void *gsrc, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_addr(smem_dst)),
+                 "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
 // One arrival (release semantics, CTA scope) on *bar.
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
