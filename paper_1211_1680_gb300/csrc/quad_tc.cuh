@@ -45,21 +45,38 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
         const int u = tid - 32 * LT_REC_WARPS;
         LtDrain d;
         d.init(warp);
-        int drained = 0;
-        for (int c = 0; c < nk; ++c) {
-            const int s = c % LT_NS;
-            const int k0 = 32 * c;
-            auto row = [&](int p) -> const float2 * {
-                const int pp = pair0 + p;
-                if (pp >= npairs) return nullptr;
+        // F rows of this thread's two pairs, loaded one chunk ahead (two register
+        // sets, the loop unrolled by two so that they stay registers)
+        const float2 *frow[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int pp = pair0 + ((u + 256 * i) >> 3);
+            frow[i] = nullptr;
+            if (pp < npairs) {
                 const int b = pp / nj, j = pp % nj;
-                return F + ((size_t)b * nmi + mi0 + 2 * j) * N + k0;
-            };
-            LtB bv;
-            bv.load(u, row, N - k0, nullptr);
+                frow[i] = F + ((size_t)b * nmi + mi0 + 2 * j) * N;
+            }
+        }
+        auto load = [&](LtB &bv, int c) {
+            const int k0 = 32 * c;
+            bv.load(u, [&](int p) -> const float2 * {
+                const float2 *r = frow[p >= 32];
+                return r ? r + k0 : nullptr;
+            }, N - k0, nullptr);
+        };
+        int drained = 0;
+        auto body = [&](int c, LtB &cur, LtB &next) {
+            if (c >= nk) return;
+            if (c + 1 < nk) load(next, c + 1);
             while (drained <= c - LT_NS) d.drain(sy, tmem, drained++);
-            bv.store(smem + s * LT_STAGE + 2 * LT_PLANE, u);
-            lt_warp_arrive(&sy.full[s], lane);
+            cur.store(smem + (c % LT_NS) * LT_STAGE + 2 * LT_PLANE, u);
+            lt_warp_arrive(&sy.full[c % LT_NS], lane);
+        };
+        LtB b0, b1;
+        if (nk > 0) load(b0, 0);
+        for (int c = 0; c < nk; c += 2) {
+            body(c, b0, b1);
+            body(c + 1, b1, b0);
         }
         while (drained < nk) d.drain(sy, tmem, drained++);
         // epilogue: TMEM lane = row t
