@@ -179,8 +179,10 @@ int s2let_plan_profile(s2let_plan *plan, int enable);
  * launches, device time in ms of the timed launches (this call synchronizes
  * their events), and the algorithmic FP operations and DRAM bytes those timed
  * launches stand for (Legendre stages: 4 flops per (l, m, ring, map) product
- * plus 4 per recurrence value; FFT stages: bytes of their input and output
- * arrays).  Any output pointer may be NULL. */
+ * plus 4 per recurrence value; ring-DFT stages: the map, the ring-major
+ * spectrum read or written by the DFT kernel and the two passes of the
+ * transpose to or from the order-major spectrum; theta quadrature: its input
+ * and output spectra).  Any output pointer may be NULL. */
 int s2let_plan_stage_stats(s2let_plan *plan, int stage, int64_t *launches, int64_t *timed, double *ms,
                            double *flops, double *bytes);
 

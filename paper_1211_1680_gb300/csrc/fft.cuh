@@ -149,15 +149,191 @@ __device__ void conv_core(C *buf, const FftTab<C> &T, const C *__restrict__ khat
     ifft_dit<C>(buf, T.M, T.logM, T.tw);
 }
 
+// ---------------------------------------------------------------- fused convolution
+// The same convolution with fewer passes over shared memory (used by the ring
+// DFTs): the first DIF pass takes its elements from load(pos) (zero padding
+// included) instead of shared memory, the last RBF DIF stages, the pointwise
+// product with the kernel table and the first RBF DIT stages run in one pass
+// (both act on contiguous groups of 2^RBF in the bit-reversed order), and the
+// last DIT pass hands its results to store(pos, value) instead of shared
+// memory.  For M = 2^logM with logM >= RBF + 1.
+template <typename C, int RB, typename LoadF>
+__device__ __forceinline__ void dif_pass_load(C *a, int M, int logM, const C *__restrict__ tw, LoadF load)
+{
+    constexpr int R = 1 << RB;
+    const int h = M >> 1;
+    const int sub = h >> (RB - 1);
+    for (int j = threadIdx.x; j < M / R; j += blockDim.x) {
+        const int g = j / sub, k = j - g * sub;
+        const int base = g * 2 * h + k;
+        C x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = load(base + q * sub);
+#pragma unroll
+        for (int t = 0; t < RB; ++t) {
+            const int half = h >> t;
+            const int span = R >> (t + 1);
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                if (q & span) continue;
+                const int pos = base + q * sub;
+                const C u = x[q], v = x[q + span];
+                x[q] = cadd(u, v);
+                x[q + span] = cmul(csub(u, v), tw[M - 2 * half + (pos & (half - 1))]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) a[pad16(base + q * sub)] = x[q];
+    }
+    __syncthreads();
+}
+
+// last RB DIF stages, product with khat (bit-reversed positions), first RB DIT stages
+template <typename C, int RB, bool CONJ_K>
+__device__ __forceinline__ void mid_pass(C *a, int M, const C *__restrict__ tw, const C *__restrict__ khat)
+{
+    constexpr int R = 1 << RB;
+    for (int j = threadIdx.x; j < M / R; j += blockDim.x) {
+        const int base = j * R;
+        C x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = a[pad16(base + q)];
+#pragma unroll
+        for (int t = 0; t < RB; ++t) {            // DIF, half = R/2 ... 1
+            const int half = R >> (t + 1);
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                if (q & half) continue;
+                const C u = x[q], v = x[q + half];
+                x[q] = cadd(u, v);
+                x[q + half] = cmul(csub(u, v), tw[M - 2 * half + ((base + q) & (half - 1))]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const C k = khat[base + q];
+            x[q] = CONJ_K ? cmulc(x[q], k) : cmul(x[q], k);
+        }
+#pragma unroll
+        for (int t = 0; t < RB; ++t) {            // DIT, half = 1 ... R/2
+            const int half = 1 << t;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                if (q & half) continue;
+                const C u = x[q];
+                const C v = cmulc(x[q + half], tw[M - 2 * half + ((base + q) & (half - 1))]);
+                x[q] = cadd(u, v);
+                x[q + half] = csub(u, v);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) a[pad16(base + q)] = x[q];
+    }
+    __syncthreads();
+}
+
+// DIT pass over stages s .. logM (RB = logM - s + 1) handing results to store(pos, value)
+template <typename C, int RB, typename StoreF>
+__device__ __forceinline__ void dit_pass_store(const C *a, int M, int logM, const C *__restrict__ tw, StoreF store)
+{
+    constexpr int R = 1 << RB;
+    const int sub = M >> RB;
+    for (int j = threadIdx.x; j < sub; j += blockDim.x) {
+        const int base = j;
+        C x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = a[pad16(base + q * sub)];
+#pragma unroll
+        for (int t = 0; t < RB; ++t) {
+            const int half = sub << t;
+            const int span = 1 << t;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                if (q & span) continue;
+                const int pos = base + q * sub;
+                const C u = x[q];
+                const C v = cmulc(x[q + span], tw[M - 2 * half + (pos & (half - 1))]);
+                x[q] = cadd(u, v);
+                x[q + span] = csub(u, v);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) store(base + q * sub, x[q]);
+    }
+}
+
+template <typename C, int RB, typename LoadF>
+__device__ __forceinline__ void dif_first(C *a, int M, int logM, const C *tw, LoadF load, int rb)
+{
+    if (rb == 3) dif_pass_load<C, 3>(a, M, logM, tw, load);
+    else if (rb == 2) dif_pass_load<C, 2>(a, M, logM, tw, load);
+    else dif_pass_load<C, 1>(a, M, logM, tw, load);
+}
+
+// out(pos, v) receives IFFT_M( FFT_M(x) * K ) at every position pos < M, where
+// x_pos = load(pos); K = khat or conj(khat) (bit-reversed).  Unnormalised.
+// The middle pass runs FFT_RBF stages each way (radix 16) in single precision,
+// three (radix 8) in double precision, where registers are twice as wide.
+constexpr int FFT_RBF = 4;
+template <typename C> constexpr int fft_rbf() { return sizeof(C) == 16 ? 3 : FFT_RBF; }
+template <typename C, bool CONJ_K, typename LoadF, typename StoreF>
+__device__ void conv_fused(C *buf, const FftTab<C> &T, const C *__restrict__ khat, LoadF load, StoreF store)
+{
+    constexpr int RBF = fft_rbf<C>();
+    const int M = T.M, logM = T.logM;
+    const int D = logM - RBF;                     // DIF (and DIT) stages outside the middle pass, >= 1
+    const int rb1 = (D - 1) % 3 + 1;              // first DIF pass: 1..3 stages, then passes of 3
+    dif_first<C, 3>(buf, M, logM, T.tw, load, rb1);
+    for (int s = 1 + rb1; s <= D; s += 3) dif_pass<C, 3>(buf, M, logM, s, T.tw);
+    mid_pass<C, RBF, CONJ_K>(buf, M, T.tw, khat);
+    const int rbl = (D - 1) % 3 + 1;              // last DIT pass: 1..3 stages, before it passes of 3
+    for (int s = RBF + 1; s <= logM - rbl; s += 3) dit_pass<C, 3>(buf, M, logM, s, T.tw);
+    if (rbl == 3) dit_pass_store<C, 3>(buf, M, logM, T.tw, store);
+    else if (rbl == 2) dit_pass_store<C, 2>(buf, M, logM, T.tw, store);
+    else dit_pass_store<C, 1>(buf, M, logM, T.tw, store);
+}
+
 template <typename R> __device__ __forceinline__ R inv_m(int M) { return (R)1 / (R)M; }
+
+// Ring-DFT blocks have at most FFT_MAX_THREADS threads (M/16 for M <= 8192);
+// single-precision kernels are built for two resident blocks per SM.
+constexpr int FFT_MAX_THREADS = 512;
+
+// ---------------------------------------------------------------- spectrum transposes
+// The ring DFTs work on one ring (or two) per block, so they read and write
+// spectra ring-major, Ft[b][t][mi] (orders contiguous); the theta quadrature and
+// the Legendre stages use order-major spectra, F[b][mi][t] (rings contiguous).
+// out[b][c][r] = in[b][r][c] for rows x cols matrices, through 32 x 32 tiles
+// in shared memory (block 32 x 8 threads; grid (cols/32, rows/32, batch)).
+template <typename C>
+__global__ void __launch_bounds__(256) k_transpose(const C *__restrict__ in, C *__restrict__ out, int rows, int cols)
+{
+    __shared__ C tile[32][33];
+    const size_t mat = (size_t)rows * cols;
+    const C *src = in + blockIdx.z * mat;
+    C *dst = out + blockIdx.z * mat;
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int i = 0; i < 32; i += 8) {
+        const int r = r0 + ty + i, c = c0 + tx;
+        if (r < rows && c < cols) tile[ty + i][tx] = src[(size_t)r * cols + c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 32; i += 8) {
+        const int c = c0 + ty + i, r = r0 + tx;
+        if (r < rows && c < cols) dst[(size_t)c * rows + r] = tile[tx][ty + i];
+    }
+}
 
 // ---------------------------------------------------------------- S1: ring DFT
 // F_m(theta_t) = scale * sum_p f(theta_t, phi_p) e^{-i m phi_p}, phi_p = 2 pi p / P.
 // Real maps: two rings per block packed as one complex sequence, m = 0..N-1,
-// written to F[b][m][t].  Complex maps: one ring per block, m = -(N-1)..N-1,
-// written to F[b][m + N - 1][t].
+// written to Ft[b][t][m].  Complex maps: one ring per block, m = -(N-1)..N-1,
+// written to Ft[b][t][m + N - 1].
 template <typename R>
-__global__ void k_ring_fwd_real(const R *__restrict__ f, cplx_t<R> *__restrict__ F, R scale,
+__global__ void __launch_bounds__(FFT_MAX_THREADS, sizeof(R) == 4 ? 2 : 1) k_ring_fwd_real(const R *__restrict__ f, cplx_t<R> *__restrict__ F, R scale,
                                 FftTab<cplx_t<R>> T)
 {
     using C = cplx_t<R>;
@@ -169,31 +345,35 @@ __global__ void k_ring_fwd_real(const R *__restrict__ f, cplx_t<R> *__restrict__
     const bool has1 = t1 < N;
     const R *r0 = f + ((size_t)b * N + t0) * P;
     const R *r1 = f + ((size_t)b * N + (has1 ? t1 : t0)) * P;
-    for (int n = threadIdx.x; n < M; n += blockDim.x) {
-        C v = mk((R)0, (R)0);
-        if (n < P) v = cmulc(mk(r0[n], has1 ? r1[n] : (R)0), T.chirp[n]);
-        buf[pad16(n)] = v;
+    auto load = [&](int n) -> C {
+        return n < P ? cmulc(mk(r0[n], has1 ? r1[n] : (R)0), T.chirp[n]) : mk((R)0, (R)0);
+    };
+    if (T.logM > fft_rbf<C>()) {
+        // the transform is read back at positions < P only
+        conv_fused<C, false>(buf, T, T.bhat, load, [&](int pos, C v) {
+            if (pos < P) buf[pad16(pos)] = v;
+        });
+    } else {
+        for (int n = threadIdx.x; n < M; n += blockDim.x) buf[pad16(n)] = load(n);
+        __syncthreads();
+        conv_core<C, false>(buf, T, T.bhat);
     }
     __syncthreads();
-    conv_core<C, false>(buf, T, T.bhat);
     const R s = scale * inv_m<R>(M) * (R)0.5;
-    C *out = F + (size_t)b * N * N;
+    C *out0 = F + ((size_t)b * N + t0) * N;
+    C *out1 = F + ((size_t)b * N + t1) * N;
     for (int m = threadIdx.x; m < N; m += blockDim.x) {
         const int mp = (m == 0) ? 0 : P - m;
         C zk = cmulc(buf[pad16(m)], T.chirp[m]);    // conj(c_k) * buf[k]
         C zp = cmulc(buf[pad16(mp)], T.chirp[mp]);
         // X0 = (Zk + conj(Zp)) / 2, X1 = (Zk - conj(Zp)) / (2i)
-        C x0 = mk((zk.x + zp.x) * s, (zk.y - zp.y) * s);
-        out[(size_t)m * N + t0] = x0;
-        if (has1) {
-            C x1 = mk((zk.y + zp.y) * s, (zp.x - zk.x) * s);
-            out[(size_t)m * N + t1] = x1;
-        }
+        out0[m] = mk((zk.x + zp.x) * s, (zk.y - zp.y) * s);
+        if (has1) out1[m] = mk((zk.y + zp.y) * s, (zp.x - zk.x) * s);
     }
 }
 
 template <typename R>
-__global__ void k_ring_fwd_cplx(const cplx_t<R> *__restrict__ f, cplx_t<R> *__restrict__ F, R scale,
+__global__ void __launch_bounds__(FFT_MAX_THREADS, sizeof(R) == 4 ? 2 : 1) k_ring_fwd_cplx(const cplx_t<R> *__restrict__ f, cplx_t<R> *__restrict__ F, R scale,
                                 FftTab<cplx_t<R>> T)
 {
     using C = cplx_t<R>;
@@ -202,25 +382,32 @@ __global__ void k_ring_fwd_cplx(const cplx_t<R> *__restrict__ f, cplx_t<R> *__re
     const int N = T.N, P = T.P, M = T.M;
     const int b = blockIdx.y, t = blockIdx.x;
     const C *row = f + ((size_t)b * N + t) * P;
-    for (int n = threadIdx.x; n < M; n += blockDim.x)
-        buf[pad16(n)] = (n < P) ? cmulc(row[n], T.chirp[n]) : mk((R)0, (R)0);
-    __syncthreads();
-    conv_core<C, false>(buf, T, T.bhat);
     const R s = scale * inv_m<R>(M);
     const int nm = 2 * N - 1;
-    C *out = F + (size_t)b * nm * N;
-    for (int mi = threadIdx.x; mi < nm; mi += blockDim.x) {
-        const int m = mi - (N - 1);
-        const int k = m >= 0 ? m : m + P;
-        out[(size_t)mi * N + t] = cscale(cmulc(buf[pad16(k)], T.chirp[k]), s);
+    C *out = F + ((size_t)b * N + t) * nm;
+    auto load = [&](int n) -> C { return n < P ? cmulc(row[n], T.chirp[n]) : mk((R)0, (R)0); };
+    // position k < P holds order m = k (k < N) or m = k - P (k > P - N)
+    auto store = [&](int k, C v) {
+        if (k >= P || (k >= N && k <= P - N)) return;
+        const int mi = (k < N ? k : k - P) + N - 1;
+        out[mi] = cscale(cmulc(v, T.chirp[k]), s);
+    };
+    if (T.logM > fft_rbf<C>()) {
+        conv_fused<C, false>(buf, T, T.bhat, load, store);
+    } else {
+        for (int n = threadIdx.x; n < M; n += blockDim.x) buf[pad16(n)] = load(n);
+        __syncthreads();
+        conv_core<C, false>(buf, T, T.bhat);
+        for (int k = threadIdx.x; k < M; k += blockDim.x) store(k, buf[pad16(k)]);
     }
 }
 
 // ---------------------------------------------------------------- S6: inverse ring DFT
-// f(theta_t, phi_p) = scale * sum_m F_m(theta_t) e^{i m phi_p}.  Real maps use
-// F_{-m} = conj(F_m) and pack two rings per block.
+// f(theta_t, phi_p) = scale * sum_m F_m(theta_t) e^{i m phi_p} from ring-major
+// spectra Ft[b][t][mi].  Real maps use F_{-m} = conj(F_m) and pack two rings
+// per block.
 template <typename R>
-__global__ void k_ring_inv_real(const cplx_t<R> *__restrict__ F, R *__restrict__ f, R scale,
+__global__ void __launch_bounds__(FFT_MAX_THREADS, sizeof(R) == 4 ? 2 : 1) k_ring_inv_real(const cplx_t<R> *__restrict__ F, R *__restrict__ f, R scale,
                                 FftTab<cplx_t<R>> T)
 {
     using C = cplx_t<R>;
@@ -230,37 +417,41 @@ __global__ void k_ring_inv_real(const cplx_t<R> *__restrict__ F, R *__restrict__
     const int b = blockIdx.y;
     const int t0 = 2 * blockIdx.x, t1 = t0 + 1;
     const bool has1 = t1 < N;
-    const C *in = F + (size_t)b * N * N;
-    for (int k = threadIdx.x; k < M; k += blockDim.x) {
-        C v = mk((R)0, (R)0);
-        if (k < P) {
-            const bool neg = k >= N;
-            const int m = neg ? P - k : k;
-            C a = in[(size_t)m * N + t0];
-            C c = has1 ? in[(size_t)m * N + t1] : mk((R)0, (R)0);
-            if (neg) {
-                a = cconj(a);
-                c = cconj(c);
-            }
-            C z = mk(a.x - c.y, a.y + c.x);   // a + i c
-            v = cmul(z, T.chirp[k]);
+    const C *in0 = F + ((size_t)b * N + t0) * N;
+    const C *in1 = F + ((size_t)b * N + (has1 ? t1 : t0)) * N;
+    auto load = [&](int k) -> C {
+        if (k >= P) return mk((R)0, (R)0);
+        const bool neg = k >= N;
+        const int m = neg ? P - k : k;
+        C a = in0[m];
+        C c = has1 ? in1[m] : mk((R)0, (R)0);
+        if (neg) {
+            a = cconj(a);
+            c = cconj(c);
         }
-        buf[pad16(k)] = v;
-    }
-    __syncthreads();
-    conv_core<C, true>(buf, T, T.bhat);
+        return cmul(mk(a.x - c.y, a.y + c.x), T.chirp[k]);   // (a + i c) chirp_k
+    };
     const R s = scale * inv_m<R>(M);
     R *o0 = f + ((size_t)b * N + t0) * P;
     R *o1 = f + ((size_t)b * N + t1) * P;
-    for (int p = threadIdx.x; p < P; p += blockDim.x) {
-        C v = cmul(buf[pad16(p)], T.chirp[p]);
+    auto store = [&](int p, C v) {
+        if (p >= P) return;
+        v = cmul(v, T.chirp[p]);
         o0[p] = v.x * s;
         if (has1) o1[p] = v.y * s;
+    };
+    if (T.logM > fft_rbf<C>()) {
+        conv_fused<C, true>(buf, T, T.bhat, load, store);
+    } else {
+        for (int k = threadIdx.x; k < M; k += blockDim.x) buf[pad16(k)] = load(k);
+        __syncthreads();
+        conv_core<C, true>(buf, T, T.bhat);
+        for (int p = threadIdx.x; p < M; p += blockDim.x) store(p, buf[pad16(p)]);
     }
 }
 
 template <typename R>
-__global__ void k_ring_inv_cplx(const cplx_t<R> *__restrict__ F, cplx_t<R> *__restrict__ f, R scale,
+__global__ void __launch_bounds__(FFT_MAX_THREADS, sizeof(R) == 4 ? 2 : 1) k_ring_inv_cplx(const cplx_t<R> *__restrict__ F, cplx_t<R> *__restrict__ f, R scale,
                                 FftTab<cplx_t<R>> T)
 {
     using C = cplx_t<R>;
@@ -269,20 +460,25 @@ __global__ void k_ring_inv_cplx(const cplx_t<R> *__restrict__ F, cplx_t<R> *__re
     const int N = T.N, P = T.P, M = T.M;
     const int b = blockIdx.y, t = blockIdx.x;
     const int nm = 2 * N - 1;
-    const C *in = F + (size_t)b * nm * N;
-    for (int k = threadIdx.x; k < M; k += blockDim.x) {
-        C v = mk((R)0, (R)0);
-        if (k < P) {
-            const int m = k < N ? k : k - P;
-            v = cmul(in[(size_t)(m + N - 1) * N + t], T.chirp[k]);
-        }
-        buf[pad16(k)] = v;
-    }
-    __syncthreads();
-    conv_core<C, true>(buf, T, T.bhat);
+    const C *in = F + ((size_t)b * N + t) * nm;
+    auto load = [&](int k) -> C {
+        if (k >= P) return mk((R)0, (R)0);
+        const int m = k < N ? k : k - P;
+        return cmul(in[m + N - 1], T.chirp[k]);
+    };
     const R s = scale * inv_m<R>(M);
     C *o = f + ((size_t)b * N + t) * P;
-    for (int p = threadIdx.x; p < P; p += blockDim.x) o[p] = cscale(cmul(buf[pad16(p)], T.chirp[p]), s);
+    auto store = [&](int p, C v) {
+        if (p < P) o[p] = cscale(cmul(v, T.chirp[p]), s);
+    };
+    if (T.logM > fft_rbf<C>()) {
+        conv_fused<C, true>(buf, T, T.bhat, load, store);
+    } else {
+        for (int k = threadIdx.x; k < M; k += blockDim.x) buf[pad16(k)] = load(k);
+        __syncthreads();
+        conv_core<C, true>(buf, T, T.bhat);
+        for (int p = threadIdx.x; p < M; p += blockDim.x) store(p, buf[pad16(p)]);
+    }
 }
 
 // ---------------------------------------------------------------- S2: theta quadrature

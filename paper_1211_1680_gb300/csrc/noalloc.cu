@@ -29,7 +29,7 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 struct Layout {
-    size_t rect, F, chirp, bhat, tw, phase, ls, seed, ringf, coeff, ringd, coefd, sinth, mant, expo, total;
+    size_t rect, F, Ft, chirp, bhat, tw, phase, ls, seed, ringf, coeff, ringd, coefd, sinth, mant, expo, total;
 };
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -46,6 +46,7 @@ Layout layout(int N, int nm, int batch, int M)
     const size_t nn = (size_t)N * N;
     o.rect = take((size_t)batch * nm * N * sizeof(float2));
     o.F = take((size_t)batch * nm * N * sizeof(float2));
+    o.Ft = take((size_t)batch * nm * N * sizeof(float2));
     o.chirp = take((size_t)(2 * N - 1) * sizeof(float2));
     o.bhat = take((size_t)M * sizeof(float2));
     o.tw = take((size_t)M * sizeof(float2));
@@ -199,7 +200,9 @@ extern "C" int s2let_sht_inverse_noalloc(int L, int batch, int flags, const void
         k_leg_synth_gemm<true><<<grid, 256, 0, st>>>(rect, L, nullptr, 1.0f, F, L, batch, tab);
     else
         k_leg_synth_gemm<false><<<grid, 256, 0, st>>>(rect, L, nullptr, 1.0f, F, L, batch, tab);
-    // ring DFTs
+    // ring DFTs, on ring-major spectra
+    float2 *Ft = (float2 *)(b + o.Ft);
+    k_transpose<float2><<<dim3((L + 31) / 32, (nm + 31) / 32, batch), dim3(32, 8), 0, st>>>(F, Ft, nm, L);
     FftTab<float2> T;
     T.chirp = (const float2 *)(b + o.chirp);
     T.bhat = (const float2 *)(b + o.bhat);
@@ -210,11 +213,11 @@ extern "C" int s2let_sht_inverse_noalloc(int L, int batch, int flags, const void
     T.P = 2 * L - 1;
     T.M = d.M;
     T.logM = d.logM;
-    const int th = std::max(32, std::min(1024, d.M / 16));
+    const int th = std::max(32, std::min(FFT_MAX_THREADS, d.M / 16));
     const size_t sm = (size_t)padded_len(d.M) * sizeof(float2);
     if (cplx)
-        k_ring_inv_cplx<float><<<dim3(L, batch), th, sm, st>>>(F, (float2 *)f, 1.0f, T);
+        k_ring_inv_cplx<float><<<dim3(L, batch), th, sm, st>>>(Ft, (float2 *)f, 1.0f, T);
     else
-        k_ring_inv_real<float><<<dim3((L + 1) / 2, batch), th, sm, st>>>(F, (float *)f, 1.0f, T);
+        k_ring_inv_real<float><<<dim3((L + 1) / 2, batch), th, sm, st>>>(Ft, (float *)f, 1.0f, T);
     return cudaGetLastError() == cudaSuccess ? S2LET_OK : S2LET_ERR_CUDA;
 }

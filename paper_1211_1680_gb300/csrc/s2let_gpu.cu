@@ -37,7 +37,7 @@ namespace {
 constexpr int kMaxL = 2048;
 constexpr int kMaxM = 8192;   // FFT length for kMaxL (next power of two >= 4 kMaxL - 3)
 
-int fft_threads(int M) { return std::max(32, std::min(1024, M / 16)); }
+int fft_threads(int M) { return std::max(32, std::min(FFT_MAX_THREADS, M / 16)); }
 
 template <typename T> T *dev_upload(const std::vector<T> &h, std::vector<void *> &owned, int &err)
 {
@@ -90,6 +90,7 @@ struct s2let_plan {
     float4 *coeff = nullptr;                // [m][l] float-float
     std::vector<void *> kfac;               // per map: scaling first, then scales J0..J (R[L])
     void *F = nullptr, *flm = nullptr, *G = nullptr;   // workspace
+    void *Ft = nullptr;                                // ring-major spectra of the ring DFTs
     bool quad_gemm = false;                 // FP32 plans: theta quadrature as a dense FP32 product
     bool tc = false;                        // TF32X3 plans: dense products on the tensor cores
     int tc_split = 2;                       // TF32 parts per operand in the tensor-core products
@@ -124,14 +125,16 @@ int64_t map_elems(const s2let_plan *p, int N) { return (int64_t)N * (2 * N - 1) 
         if (cudaGetLastError() != cudaSuccess) return S2LET_ERR_CUDA; \
     } while (0)
 
-// Counts a launch of `stage` and, when profiling, brackets it with an event pair.
+// Counts the kernel launches of one run of `stage` (nk kernels) and, when
+// profiling, brackets the run with an event pair.
 struct StageScope {
     const s2let_plan *p;
     cudaStream_t st;
     long slot = -1;
-    StageScope(const s2let_plan *p_, int stage, cudaStream_t st_, double flops, double bytes) : p(p_), st(st_)
+    StageScope(const s2let_plan *p_, int stage, cudaStream_t st_, double flops, double bytes, int nk = 1)
+        : p(p_), st(st_)
     {
-        p->launches[stage]++;
+        p->launches[stage] += nk;
         if (p->prof && p->evnext + 2 <= p->evpool.size()) {
             s2let_plan::Rec r{stage, p->evpool[p->evnext], p->evpool[p->evnext + 1], flops, bytes};
             p->evnext += 2;
@@ -187,12 +190,18 @@ int run_ring_fwd(const s2let_plan *p, const BandDev &bd, const void *f, void *F,
     const auto &T = fft_tab<R>(bd);
     const size_t sm = (size_t)padded_len(bd.M) * sizeof(cplx_t<R>);
     const int th = fft_threads(bd.M);
-    StageScope sc(p, S2LET_STAGE_RING_FWD, st, 0.0, map_bytes(p, bd.N) + spectrum_bytes(p, bd.N));
+    StageScope sc(p, S2LET_STAGE_RING_FWD, st, 0.0, map_bytes(p, bd.N) + 3.0 * spectrum_bytes(p, bd.N), 2);
     if (p->cplx) {
-        k_ring_fwd_cplx<R><<<dim3(bd.N, p->batch), th, sm, st>>>((const cplx_t<R> *)f, (cplx_t<R> *)F, (R)scale, T);
+        k_ring_fwd_cplx<R><<<dim3(bd.N, p->batch), th, sm, st>>>((const cplx_t<R> *)f, (cplx_t<R> *)p->Ft, (R)scale,
+                                                                  T);
     } else {
-        k_ring_fwd_real<R><<<dim3((bd.N + 1) / 2, p->batch), th, sm, st>>>((const R *)f, (cplx_t<R> *)F, (R)scale, T);
+        k_ring_fwd_real<R><<<dim3((bd.N + 1) / 2, p->batch), th, sm, st>>>((const R *)f, (cplx_t<R> *)p->Ft,
+                                                                           (R)scale, T);
     }
+    // Ft[b][t][mi] -> F[b][mi][t]
+    const int n = nmi(p, bd.N);
+    k_transpose<cplx_t<R>><<<dim3((n + 31) / 32, (bd.N + 31) / 32, p->batch), dim3(32, 8), 0, st>>>(
+        (const cplx_t<R> *)p->Ft, (cplx_t<R> *)F, bd.N, n);
     S2_LAUNCH_CHECK();
     return S2LET_OK;
 }
@@ -203,11 +212,17 @@ int run_ring_inv(const s2let_plan *p, const BandDev &bd, const void *F, void *f,
     const auto &T = fft_tab<R>(bd);
     const size_t sm = (size_t)padded_len(bd.M) * sizeof(cplx_t<R>);
     const int th = fft_threads(bd.M);
-    StageScope sc(p, S2LET_STAGE_RING_INV, st, 0.0, map_bytes(p, bd.N) + spectrum_bytes(p, bd.N));
+    StageScope sc(p, S2LET_STAGE_RING_INV, st, 0.0, map_bytes(p, bd.N) + 3.0 * spectrum_bytes(p, bd.N), 2);
+    // F[b][mi][t] -> Ft[b][t][mi]
+    const int n = nmi(p, bd.N);
+    k_transpose<cplx_t<R>><<<dim3((bd.N + 31) / 32, (n + 31) / 32, p->batch), dim3(32, 8), 0, st>>>(
+        (const cplx_t<R> *)F, (cplx_t<R> *)p->Ft, n, bd.N);
     if (p->cplx) {
-        k_ring_inv_cplx<R><<<dim3(bd.N, p->batch), th, sm, st>>>((const cplx_t<R> *)F, (cplx_t<R> *)f, (R)scale, T);
+        k_ring_inv_cplx<R><<<dim3(bd.N, p->batch), th, sm, st>>>((const cplx_t<R> *)p->Ft, (cplx_t<R> *)f, (R)scale,
+                                                                  T);
     } else {
-        k_ring_inv_real<R><<<dim3((bd.N + 1) / 2, p->batch), th, sm, st>>>((const cplx_t<R> *)F, (R *)f, (R)scale, T);
+        k_ring_inv_real<R><<<dim3((bd.N + 1) / 2, p->batch), th, sm, st>>>((const cplx_t<R> *)p->Ft, (R *)f,
+                                                                           (R)scale, T);
     }
     S2_LAUNCH_CHECK();
     return S2LET_OK;
@@ -224,7 +239,7 @@ void *run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream
     if (std::is_same<R, float>::value && p->quad_gemm) {
         // two products, one per parity of m
         StageScope sc(p, S2LET_STAGE_THETA_QUAD, st, 2.0 * bd.N * (double)bd.N * n * 2 * p->batch,
-                      2.0 * spectrum_bytes(p, bd.N));
+                      2.0 * spectrum_bytes(p, bd.N), n > 1 ? 2 : 1);
         for (int par = 0; par < 2; ++par) {
             int mi0 = p->cplx ? (((bd.N - 1) & 1) ^ par) : par;
             if (mi0 >= n) continue;
@@ -791,6 +806,8 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
     p->owned.push_back(p->F);
     if (cudaMalloc(&p->flm, ws) != cudaSuccess) return S2LET_ERR_ALLOC;
     p->owned.push_back(p->flm);
+    if (cudaMalloc(&p->Ft, ws) != cudaSuccess) return S2LET_ERR_ALLOC;
+    p->owned.push_back(p->Ft);
     if (p->quad_gemm) {
         if (cudaMalloc(&p->G, ws) != cudaSuccess) return S2LET_ERR_ALLOC;
         p->owned.push_back(p->G);
