@@ -43,19 +43,66 @@ template <typename C> struct FftTab {
 // registers and stores them back, so shared memory is read and written once per
 // three stages.  The arithmetic and the output order are those of the plain
 // radix-2 algorithms.
-// DIF pass over stages s .. s+RB-1 (first half h = 2^(logM-s)).
+// Twiddles.  Stage half-size `half` multiplies by tw[M - 2 half + (pos mod
+// half)] = e^{-2 pi i (pos mod half) / (2 half)}.  Within a radix-8 group
+// (elements base + q sub, base = k mod sub) the twelve twiddles of its three
+// stages are three table entries times eighth roots of unity, so a group loads
+// three values and forms the rest with a multiplication by (1 - i)/sqrt(2) or
+// exact multiplications by -i.
+template <typename C> __device__ __forceinline__ C mul_mi(C w) { return mk(w.y, -w.x); }       // -i w
+template <typename C> __device__ __forceinline__ C mul_w8(C w)                                // e^{-i pi/4} w
+{
+    using R = decltype(w.x);
+    const R h = (R)0.70710678118654752440;
+    return mk((w.x + w.y) * h, (w.y - w.x) * h);
+}
+// e^{-2 pi i e / 16}, e = 0..7 (constants: cos and sin of multiples of pi/8)
+template <typename C> __device__ __forceinline__ C w16(int e)
+{
+    using R = decltype(C().x);
+    const R c1 = (R)0.92387953251128675613, s1 = (R)0.38268343236508977173, r2 = (R)0.70710678118654752440;
+    switch (e) {
+    case 0: return mk((R)1, (R)0);
+    case 1: return mk(c1, -s1);
+    case 2: return mk(r2, -r2);
+    case 3: return mk(s1, -c1);
+    case 4: return mk((R)0, (R)-1);
+    case 5: return mk(-s1, -c1);
+    case 6: return mk(-r2, -r2);
+    default: return mk(-c1, -s1);
+    }
+}
+
+// RB DIF stages on a group x[q] = a[base + q sub], first half-size h (sub = h / 2^(RB-1)).
 template <typename C, int RB>
-__device__ __forceinline__ void dif_pass(C *a, int M, int logM, int s, const C *__restrict__ tw)
+__device__ __forceinline__ void dif_group(C (&x)[1 << RB], int M, int h, int base, int sub, const C *__restrict__ tw)
 {
     constexpr int R = 1 << RB;
-    const int h = 1 << (logM - s);
-    const int sub = h >> (RB - 1);            // distance between the group's elements
-    for (int j = threadIdx.x; j < M / R; j += blockDim.x) {
-        const int g = j / sub, k = j - g * sub;
-        const int base = g * 2 * h + k;
-        C x[R];
+    if constexpr (RB == 3) {
+        const int k = base & (sub - 1);
+        const C W = tw[M - 2 * h + k], W2 = tw[M - h + k], W4 = tw[M - h / 2 + k];
+        const C w0[4] = {W, mul_w8(W), mul_mi(W), mul_mi(mul_w8(W))};
 #pragma unroll
-        for (int q = 0; q < R; ++q) x[q] = a[pad16(base + q * sub)];
+        for (int q = 0; q < 4; ++q) {
+            const C u = x[q], v = x[q + 4];
+            x[q] = cadd(u, v);
+            x[q + 4] = cmul(csub(u, v), w0[q]);
+        }
+        const C w1[2] = {W2, mul_mi(W2)};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (q & 2) continue;
+            const C u = x[q], v = x[q + 2];
+            x[q] = cadd(u, v);
+            x[q + 2] = cmul(csub(u, v), w1[q & 1]);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+            const C u = x[q], v = x[q + 1];
+            x[q] = cadd(u, v);
+            x[q + 1] = cmul(csub(u, v), W4);
+        }
+    } else {
 #pragma unroll
         for (int t = 0; t < RB; ++t) {
             const int half = h >> t;
@@ -69,6 +116,70 @@ __device__ __forceinline__ void dif_pass(C *a, int M, int logM, int s, const C *
                 x[q + span] = cmul(csub(u, v), tw[M - 2 * half + (pos & (half - 1))]);
             }
         }
+    }
+}
+
+// RB DIT stages on a group x[q] = a[base + q sub], first half-size sub.
+template <typename C, int RB>
+__device__ __forceinline__ void dit_group(C (&x)[1 << RB], int M, int base, int sub, const C *__restrict__ tw)
+{
+    constexpr int R = 1 << RB;
+    if constexpr (RB == 3) {
+        const int k = base & (sub - 1);
+        const C T1 = tw[M - 2 * sub + k], T2 = tw[M - 4 * sub + k], T4 = tw[M - 8 * sub + k];
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+            const C u = x[q], v = cmulc(x[q + 1], T1);
+            x[q] = cadd(u, v);
+            x[q + 1] = csub(u, v);
+        }
+        const C w1[2] = {T2, mul_mi(T2)};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (q & 2) continue;
+            const C u = x[q], v = cmulc(x[q + 2], w1[q & 1]);
+            x[q] = cadd(u, v);
+            x[q + 2] = csub(u, v);
+        }
+        const C w2[4] = {T4, mul_w8(T4), mul_mi(T4), mul_mi(mul_w8(T4))};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const C u = x[q], v = cmulc(x[q + 4], w2[q]);
+            x[q] = cadd(u, v);
+            x[q + 4] = csub(u, v);
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < RB; ++t) {
+            const int half = sub << t;
+            const int span = 1 << t;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                if (q & span) continue;
+                const int pos = base + q * sub;
+                const C u = x[q];
+                const C v = cmulc(x[q + span], tw[M - 2 * half + (pos & (half - 1))]);
+                x[q] = cadd(u, v);
+                x[q + span] = csub(u, v);
+            }
+        }
+    }
+}
+
+// DIF pass over stages s .. s+RB-1 (first half h = 2^(logM-s)).
+template <typename C, int RB>
+__device__ __forceinline__ void dif_pass(C *a, int M, int logM, int s, const C *__restrict__ tw)
+{
+    constexpr int R = 1 << RB;
+    const int h = 1 << (logM - s);
+    const int sub = h >> (RB - 1);            // distance between the group's elements
+    for (int j = threadIdx.x; j < M / R; j += blockDim.x) {
+        const int g = j / sub, k = j - g * sub;
+        const int base = g * 2 * h + k;
+        C x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = a[pad16(base + q * sub)];
+        dif_group<C, RB>(x, M, h, base, sub, tw);
 #pragma unroll
         for (int q = 0; q < R; ++q) a[pad16(base + q * sub)] = x[q];
     }
@@ -88,20 +199,7 @@ __device__ __forceinline__ void dit_pass(C *a, int M, int logM, int s, const C *
         C x[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) x[q] = a[pad16(base + q * sub)];
-#pragma unroll
-        for (int t = 0; t < RB; ++t) {
-            const int half = sub << t;
-            const int span = 1 << t;
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                if (q & span) continue;
-                const int pos = base + q * sub;
-                const C u = x[q];
-                const C v = cmulc(x[q + span], tw[M - 2 * half + (pos & (half - 1))]);
-                x[q] = cadd(u, v);
-                x[q + span] = csub(u, v);
-            }
-        }
+        dit_group<C, RB>(x, M, base, sub, tw);
 #pragma unroll
         for (int q = 0; q < R; ++q) a[pad16(base + q * sub)] = x[q];
     }
@@ -169,30 +267,21 @@ __device__ __forceinline__ void dif_pass_load(C *a, int M, int logM, const C *__
         C x[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) x[q] = load(base + q * sub);
-#pragma unroll
-        for (int t = 0; t < RB; ++t) {
-            const int half = h >> t;
-            const int span = R >> (t + 1);
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                if (q & span) continue;
-                const int pos = base + q * sub;
-                const C u = x[q], v = x[q + span];
-                x[q] = cadd(u, v);
-                x[q + span] = cmul(csub(u, v), tw[M - 2 * half + (pos & (half - 1))]);
-            }
-        }
+        dif_group<C, RB>(x, M, h, base, sub, tw);
 #pragma unroll
         for (int q = 0; q < R; ++q) a[pad16(base + q * sub)] = x[q];
     }
     __syncthreads();
 }
 
-// last RB DIF stages, product with khat (bit-reversed positions), first RB DIT stages
+// last RB DIF stages, product with khat (bit-reversed positions), first RB DIT
+// stages.  The group starts at a multiple of 2^RB, so its twiddles are the
+// 2^RB-th roots of unity e^{-2 pi i (q mod half)/(2 half)} = w16((q mod half) 8 / half).
 template <typename C, int RB, bool CONJ_K>
-__device__ __forceinline__ void mid_pass(C *a, int M, const C *__restrict__ tw, const C *__restrict__ khat)
+__device__ __forceinline__ void mid_pass(C *a, int M, const C *__restrict__ khat)
 {
     constexpr int R = 1 << RB;
+    static_assert(RB <= 4, "sixteenth roots of unity only");
     for (int j = threadIdx.x; j < M / R; j += blockDim.x) {
         const int base = j * R;
         C x[R];
@@ -206,7 +295,9 @@ __device__ __forceinline__ void mid_pass(C *a, int M, const C *__restrict__ tw, 
                 if (q & half) continue;
                 const C u = x[q], v = x[q + half];
                 x[q] = cadd(u, v);
-                x[q + half] = cmul(csub(u, v), tw[M - 2 * half + ((base + q) & (half - 1))]);
+                const C d = csub(u, v);
+                const int e = (q & (half - 1)) * (8 / half);
+                x[q + half] = e == 0 ? d : (e == 4 ? mul_mi(d) : cmul(d, w16<C>(e)));
             }
         }
 #pragma unroll
@@ -220,8 +311,9 @@ __device__ __forceinline__ void mid_pass(C *a, int M, const C *__restrict__ tw, 
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 if (q & half) continue;
+                const int e = (q & (half - 1)) * (8 / half);
                 const C u = x[q];
-                const C v = cmulc(x[q + half], tw[M - 2 * half + ((base + q) & (half - 1))]);
+                const C v = e == 0 ? x[q + half] : cmulc(x[q + half], w16<C>(e));
                 x[q] = cadd(u, v);
                 x[q + half] = csub(u, v);
             }
@@ -243,20 +335,7 @@ __device__ __forceinline__ void dit_pass_store(const C *a, int M, int logM, cons
         C x[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) x[q] = a[pad16(base + q * sub)];
-#pragma unroll
-        for (int t = 0; t < RB; ++t) {
-            const int half = sub << t;
-            const int span = 1 << t;
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                if (q & span) continue;
-                const int pos = base + q * sub;
-                const C u = x[q];
-                const C v = cmulc(x[q + span], tw[M - 2 * half + (pos & (half - 1))]);
-                x[q] = cadd(u, v);
-                x[q + span] = csub(u, v);
-            }
-        }
+        dit_group<C, RB>(x, M, base, sub, tw);
 #pragma unroll
         for (int q = 0; q < R; ++q) store(base + q * sub, x[q]);
     }
@@ -285,7 +364,7 @@ __device__ void conv_fused(C *buf, const FftTab<C> &T, const C *__restrict__ kha
     const int rb1 = (D - 1) % 3 + 1;              // first DIF pass: 1..3 stages, then passes of 3
     dif_first<C, 3>(buf, M, logM, T.tw, load, rb1);
     for (int s = 1 + rb1; s <= D; s += 3) dif_pass<C, 3>(buf, M, logM, s, T.tw);
-    mid_pass<C, RBF, CONJ_K>(buf, M, T.tw, khat);
+    mid_pass<C, RBF, CONJ_K>(buf, M, khat);
     const int rbl = (D - 1) % 3 + 1;              // last DIT pass: 1..3 stages, before it passes of 3
     for (int s = RBF + 1; s <= logM - rbl; s += 3) dit_pass<C, 3>(buf, M, logM, s, T.tw);
     if (rbl == 3) dit_pass_store<C, 3>(buf, M, logM, T.tw, store);
