@@ -85,7 +85,27 @@ __device__ __forceinline__ float4 lt_coef_load(const float4 *cm, int l, int N)
 // ---------------------------------------------------------------- synthesis
 // Block: (tile of 128 rings, order m, batch tile).  MMA rows = rings, K =
 // degrees in chunks of 32 from the tile's smallest l_s, columns = coefficient
-// columns.  Recurrence thread r owns ring t0 + r (row r of A).
+// columns.  Recurrence thread r owns ring t0 + r, which is row r of A and lane
+// r of tensor memory: it writes its split lambda values straight into TMEM
+// (tcgen05.st) and the MMAs read operand A from there, so the tensor core's
+// shared-memory traffic is operand B only and does not throttle the recurrence.
+// Operands of chunk c: stage q = c % LS_NA (A in TMEM columns 256 + 64 q (hi) and
+// + 32 (lo), B in shared memory); accumulator c % 2 in TMEM columns 128 (c % 2).
+// Barriers: full[q] (4 recurrence + 8 operand-B warps), empty[q] (the chunk's
+// MMAs completed: stage q free, accumulator ready), tempty[c % 2] (drained).
+// Each recurrence warp stages its chunk's 32 recurrence coefficients in shared
+// memory and every lane reads them with broadcast loads.
+constexpr int LS_NA = 4;
+constexpr int LS_STAGE = 2 * LT_PLANE;                 // operand B hi, lo
+struct LsSync {
+    uint64_t full[LS_NA], empty[LS_NA], tempty[2], done;
+    uint32_t tslot;
+    int abort, lmin;
+};
+constexpr int LS_COEF_OFF = LS_NA * LS_STAGE;          // 4 warps x 32 float4
+constexpr int LS_SYNC_OFF = LS_COEF_OFF + LT_REC_WARPS * 32 * 16;
+__host__ __device__ constexpr size_t ls_synth_smem() { return (size_t)LS_SYNC_OFF + 256 + 1024; }
+
 template <bool CPLX>
 static __global__ void __launch_bounds__(LT_THREADS, 1)
     k_leg_synth_tc(const float2 *__restrict__ src, int Lsrc, const float *__restrict__ kfac, float scale,
@@ -95,15 +115,32 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
     constexpr int BT = Cols::BT;
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
     unsigned char *smem = lt_align(smem_dyn);
-    LtSync &sy = *reinterpret_cast<LtSync *>(smem + LT_NS * LT_STAGE);
+    LsSync &sy = *reinterpret_cast<LsSync *>(smem + LS_SYNC_OFF);
+    float4 *coefs = reinterpret_cast<float4 *>(smem + LS_COEF_OFF);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int t0 = blockIdx.x * 128, m = blockIdx.y, b0 = blockIdx.z * BT;
     const bool two = CPLX && m > 0;
+    volatile int *abort = &sy.abort;
 
     int ls = N;
     if (warp < LT_REC_WARPS && t0 + tid < N) ls = tab.ls[(size_t)m * N + t0 + tid];
-    if (tid == 0) sy.lmin = N;
-    lt_setup(sy, warp, tid, LT_REC_WARPS + LT_OPB_WARPS, LT_MMA_WARP);
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < LS_NA; ++i) {
+            tc::mbar_init(&sy.full[i], LT_REC_WARPS + LT_OPB_WARPS);
+            tc::mbar_init(&sy.empty[i], 1);
+        }
+        tc::mbar_init(&sy.tempty[0], LT_OPB_WARPS);
+        tc::mbar_init(&sy.tempty[1], LT_OPB_WARPS);
+        tc::mbar_init(&sy.done, 1);
+        sy.abort = 0;
+        sy.lmin = N;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == LT_MMA_WARP) tc::tmem_alloc(&sy.tslot, LT_TMEM_COLS);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
     if (warp < LT_REC_WARPS) {
         int v = ls;
 #pragma unroll
@@ -116,44 +153,68 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
     const uint32_t tmem = sy.tslot;
 
     if (warp < LT_REC_WARPS) {
-        // ------------------------------------------------ recurrence (A = lambda[ring][degree])
+        // ------------------------------------------------ recurrence (A = lambda[ring][degree] in TMEM)
         const int t = t0 + tid;
         const bool own = t < N;
         LtRec rec;
         rec.init(own, tab.ring + t, tab.seed + (size_t)m * N + t, tab.ls + (size_t)m * N + t);
         const float4 *cm = tab.coef + (size_t)m * tab.ldc;
-        // lane j holds the coefficient of degree l0 + j; the next chunk's is prefetched
+        float4 *wc = coefs + 32 * warp;
+        const uint32_t lane_addr = (uint32_t)(32 * warp) << 16;
         float4 cf_next = lt_coef_load(cm, lstart + lane, N);
         for (int c = 0; c < nk; ++c) {
-            const int s = c % LT_NS;
-            const float4 cf = cf_next;
+            const int q = c % LS_NA;
+            __syncwarp();
+            wc[lane] = cf_next;                       // this chunk's coefficients, lane j: degree l0 + j
+            __syncwarp();
             cf_next = lt_coef_load(cm, lstart + 32 * (c + 1) + lane, N);
-            if (c >= LT_NS) lt_wait(&sy.empty[s], ((c / LT_NS) - 1) & 1, &sy.abort);
-            unsigned char *A = smem + s * LT_STAGE;
+            if (c >= LS_NA) lt_wait(&sy.empty[q], ((c / LS_NA) - 1) & 1, abort);
+            tc::fence_after();
+            const uint32_t ahi = tmem + lane_addr + (uint32_t)(256 + 64 * q), alo = ahi + 32;
             const int l0 = lstart + 32 * c;
 #pragma unroll
-            for (int g = 0; g < 8; ++g) {
-                float hi[4], lo[4];
+            for (int g = 0; g < 4; ++g) {
+                float hi[8], lo[8];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float v = rec.step(lt_coef(cf, 4 * g + j), l0 + 4 * g + j);
+                for (int j = 0; j < 8; ++j) {
+                    const float v = rec.step(wc[8 * g + j], l0 + 8 * g + j);
                     tc::split_tf32(v, hi[j], lo[j]);
                 }
-                const uint32_t o = tc::sw128_off(tid, 4 * g);
-                *reinterpret_cast<float4 *>(A + o) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-                *reinterpret_cast<float4 *>(A + LT_PLANE + o) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+                tc::tmem_st8(ahi + 8 * g, hi);
+                tc::tmem_st8(alo + 8 * g, lo);
             }
-            lt_warp_arrive(&sy.full[s], lane);
+            tc::tmem_wait_st();
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&sy.full[q]);
         }
     } else if (warp < LT_MMA_WARP) {
         // ------------------------------------------------ operand B (c_l f_lm) and drains
         const int u = tid - 32 * LT_REC_WARPS;
         const int nmi_src = CPLX ? 2 * Lsrc - 1 : Lsrc;
-        LtDrain d;
-        d.init(warp);
+        float sum[64];
+#pragma unroll
+        for (int i = 0; i < 64; ++i) sum[i] = 0.f;
+        const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+        const int h = (warp - LT_REC_WARPS) >> 2;
+        auto drain = [&](int c) {                     // accumulator c % 2 into sum
+            lt_wait(&sy.empty[c % LS_NA], (c / LS_NA) & 1, abort);
+            tc::fence_after();
+            const uint32_t acc = tmem + lane_addr + (uint32_t)(128 * (c & 1) + 64 * h);
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                float v[16];
+                tc::tmem_ld16(acc + 16 * g, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) sum[16 * g + i] += v[i];
+            }
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&sy.tempty[c & 1]);
+        };
         int drained = 0;
         for (int c = 0; c < nk; ++c) {
-            const int s = c % LT_NS;
+            const int q = c % LS_NA;
             const int l0 = lstart + 32 * c;
             auto row = [&](int p) -> const float2 * {
                 const int sg = p / BT, b = p % BT;
@@ -163,11 +224,12 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
             };
             LtB bv;
             bv.load(u, row, N - l0, kfac ? kfac + l0 : nullptr);
-            while (drained <= c - LT_NS) d.drain(sy, tmem, drained++);
-            bv.store(smem + s * LT_STAGE + 2 * LT_PLANE, u);
-            lt_warp_arrive(&sy.full[s], lane);
+            while (drained <= c - 2) drain(drained++);
+            if (c >= LS_NA) lt_wait(&sy.empty[q], ((c / LS_NA) - 1) & 1, abort);
+            bv.store(smem + q * LS_STAGE, u);
+            lt_warp_arrive(&sy.full[q], lane);
         }
-        while (drained < nk) d.drain(sy, tmem, drained++);
+        while (drained < nk) drain(drained++);
         // epilogue: TMEM lane = ring
         const int t = t0 + 32 * (warp & 3) + lane;
         if (t < N && !sy.abort) {
@@ -175,18 +237,44 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
             const float sgn_m = (m & 1) ? -1.f : 1.f;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-                const int p = 32 * d.h + j;
+                const int p = 32 * h + j;
                 const int sg = p / BT, b = p % BT;
                 if (b0 + b >= B || (sg == 1 && !two)) continue;
                 const float f = sg == 1 ? scale * sgn_m : scale;
                 const int mi = sg == 0 ? (CPLX ? m + N - 1 : m) : (-m + N - 1);
-                dst[((size_t)(b0 + b) * nmi_dst + mi) * N + t] = make_float2(d.sum[2 * j] * f, d.sum[2 * j + 1] * f);
+                dst[((size_t)(b0 + b) * nmi_dst + mi) * N + t] = make_float2(sum[2 * j] * f, sum[2 * j + 1] * f);
             }
         }
     } else if (lane == 0) {
-        lt_issue(sy, smem, tmem, nk);
+        // ------------------------------------------------ MMA issue: A from TMEM, B from shared memory
+        constexpr uint32_t IDESC = tc::idesc_tf32(128, 128);
+        for (int c = 0; c < nk; ++c) {
+            const int q = c % LS_NA;
+            bool ok = lt_wait(&sy.full[q], (c / LS_NA) & 1, abort);
+            if (c >= 2) ok = lt_wait(&sy.tempty[c & 1], ((c >> 1) - 1) & 1, abort) && ok;
+            tc::fence_after();
+            if (ok) {
+                const uint32_t bbase = tc::smem_addr(smem + q * LS_STAGE);
+                const uint32_t acc = tmem + (uint32_t)(128 * (c & 1));
+                const uint32_t ahi = tmem + (uint32_t)(256 + 64 * q), alo = ahi + 32;
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {
+                    const uint64_t b0d = tc::smem_desc_sw128(bbase + ks * 32);
+                    const uint64_t b1d = tc::smem_desc_sw128(bbase + LT_PLANE + ks * 32);
+                    tc::mma_tf32_ts(acc, ahi + 8 * ks, b1d, IDESC, ks > 0 ? 1u : 0u);
+                    tc::mma_tf32_ts(acc, alo + 8 * ks, b0d, IDESC, 1u);
+                    tc::mma_tf32_ts(acc, ahi + 8 * ks, b0d, IDESC, 1u);
+                }
+            }
+            tc::mma_commit(&sy.empty[q]);
+        }
+        tc::mma_commit(&sy.done);
+        tc::mbar_wait(&sy.done, 0, 1u << 22);   // no MMA in flight when TMEM is released
     }
-    lt_teardown(sy, warp, tid, tmem, err, LT_MMA_WARP);
+    tc::fence_before();
+    __syncthreads();
+    if (warp == LT_MMA_WARP) tc::tmem_free(tmem, LT_TMEM_COLS);
+    if (tid == 0 && sy.abort) atomicExch(err, 1);
 }
 
 // ---------------------------------------------------------------- analysis

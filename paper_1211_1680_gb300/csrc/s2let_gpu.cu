@@ -298,11 +298,11 @@ int run_synth(const s2let_plan *p, const BandDev &bd, const void *src, const voi
         dim3 grid((bd.N + LS_RT - 1) / LS_RT, bd.N, (p->batch + bt - 1) / bt);
         const LegTab<float> tab = leg_tab<float>(p, bd);
         if (p->tc && p->cplx)
-            k_leg_synth_tc<true><<<grid, LT_THREADS, lt_synth_smem(), st>>>(
+            k_leg_synth_tc<true><<<grid, LT_THREADS, ls_synth_smem(), st>>>(
                 (const float2 *)src, p->L, (const float *)kfac, (float)scale, (float2 *)dst, bd.N, p->batch, tab,
                 p->d_err);
         else if (p->tc)
-            k_leg_synth_tc<false><<<grid, LT_THREADS, lt_synth_smem(), st>>>(
+            k_leg_synth_tc<false><<<grid, LT_THREADS, ls_synth_smem(), st>>>(
                 (const float2 *)src, p->L, (const float *)kfac, (float)scale, (float2 *)dst, bd.N, p->batch, tab,
                 p->d_err);
         else if (p->cplx)
@@ -555,8 +555,8 @@ void set_smem_limits(int Mmax)
     allow_smem(k_ring_inv_cplx<float>, f);
     allow_smem(k_quad_tcp, lt_synth_smem());
     allow_smem(k_quad_tc<3, 2>, TqShape<3, 2>::SMEM);
-    allow_smem(k_leg_synth_tc<false>, lt_synth_smem());
-    allow_smem(k_leg_synth_tc<true>, lt_synth_smem());
+    allow_smem(k_leg_synth_tc<false>, ls_synth_smem());
+    allow_smem(k_leg_synth_tc<true>, ls_synth_smem());
     allow_smem(k_leg_anal_tc<false>, lt_anal_smem(kMaxL));
     allow_smem(k_leg_anal_tc<true>, lt_anal_smem(kMaxL));
     allow_smem(k_leg_anal_gemm<false>, anal_gemm_smem(kMaxL));

@@ -140,11 +140,12 @@ struct LtDrain {
 #pragma unroll
         for (int i = 0; i < 64; ++i) sum[i] = 0.f;
     }
-    // add chunk c's accumulator (64 columns of this thread's lane) into sum
-    __device__ __forceinline__ void drain(LtSync &sy, uint32_t tmem, int c)
+    // add chunk c's accumulator (64 columns of this thread's lane) into sum; NS
+    // stages (TMEM buffer c % NS at column 128 (c % NS))
+    template <int NS = LT_NS> __device__ __forceinline__ void drain(LtSync &sy, uint32_t tmem, int c)
     {
-        const int s = c % LT_NS;
-        lt_wait(&sy.empty[s], (c / LT_NS) & 1, &sy.abort);
+        const int s = c % NS;
+        lt_wait(&sy.empty[s], (c / NS) & 1, &sy.abort);
         tc::fence_after();
         const uint32_t acc = tmem + lane_addr + (uint32_t)(s * 128 + 64 * h);
 #pragma unroll
