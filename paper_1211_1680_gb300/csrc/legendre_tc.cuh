@@ -47,6 +47,22 @@ struct LtRec {
             s1.l = (float)(sd.y - (double)s1.h);
         }
     }
+    // step without the seed selection, for degrees l != l_s (after l_s, or before
+    // it where the state is zero)
+    __device__ __forceinline__ float step_plain(const float4 c)
+    {
+        ff a, ab;
+        a.h = c.x;
+        a.l = c.y;
+        ab.h = c.z;
+        ab.l = c.w;
+        const ff p2 = ff_sub(ff_mul(ff_mul(a, x), p1), ff_mul(ab, p0));
+        p0 = p1;
+        p1 = p2;
+        return p1.h;
+    }
+    // does the chain start in degrees [l0, l0 + n)?
+    __device__ __forceinline__ bool starts_in(int l0, int n) const { return ls >= l0 && ls < l0 + n; }
     // value of degree l given the coefficient (a hi, a lo, a b hi, a b lo) of l
     __device__ __forceinline__ float step(const float4 c, int l)
     {
@@ -176,10 +192,7 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
             for (int g = 0; g < 4; ++g) {
                 float hi[8], lo[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float v = rec.step(wc[8 * g + j], l0 + 8 * g + j);
-                    tc::split_tf32(v, hi[j], lo[j]);
-                }
+                for (int j = 0; j < 8; ++j) tc::split_tf32(rec.step(wc[8 * g + j], l0 + 8 * g + j), hi[j], lo[j]);
                 tc::tmem_st8(ahi + 8 * g, hi);
                 tc::tmem_st8(alo + 8 * g, lo);
             }
@@ -357,15 +370,25 @@ static __global__ void __launch_bounds__(LT_ANAL_THREADS, 1)
 #pragma unroll 1
                     for (int i = 0; i < 4; ++i) {
                         const float4 cf = i == 0 ? cf0 : i == 1 ? cf1 : i == 2 ? cf2 : cf3;
+                        const int lb = l0 + 32 * i;
+                        if (__any_sync(0xffffffffu, rec.starts_in(lb, 32))) {   // a chain of this warp starts here
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int r = 32 * i + j;
-                            const float v = rec.step(lt_coef(cf, j), l0 + r);
-                            float hi, lo;
-                            tc::split_tf32(v, hi, lo);
-                            const uint32_t o = tc::sw128_off(r, lane);
-                            *reinterpret_cast<float *>(A + o) = hi;
-                            *reinterpret_cast<float *>(A + LT_PLANE + o) = lo;
+                            for (int j = 0; j < 32; ++j) {
+                                float hi, lo;
+                                tc::split_tf32(rec.step(lt_coef(cf, j), lb + j), hi, lo);
+                                const uint32_t o = tc::sw128_off(32 * i + j, lane);
+                                *reinterpret_cast<float *>(A + o) = hi;
+                                *reinterpret_cast<float *>(A + LT_PLANE + o) = lo;
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                float hi, lo;
+                                tc::split_tf32(rec.step_plain(lt_coef(cf, j)), hi, lo);
+                                const uint32_t o = tc::sw128_off(32 * i + j, lane);
+                                *reinterpret_cast<float *>(A + o) = hi;
+                                *reinterpret_cast<float *>(A + LT_PLANE + o) = lo;
+                            }
                         }
                     }
                     if (own && lend - 1 >= rec.ls) st[t] = make_float4(rec.p0.h, rec.p0.l, rec.p1.h, rec.p1.l);
