@@ -32,6 +32,7 @@ METRIC = "wavelet round-trips/s, L=2048x64 maps, vs plain FP64 GPU path; max err
 UNIT = "map round-trips/s"
 SM_COUNT = 152
 FP32_LANES = 128
+TF32_PER_BF16 = 1.1 / 2.25      # nominal dense tensor rates (PFLOP/s per GPU)
 FLOPS_COUNTED = {
     "leg_anal": "4 per (l, m, ring, map) product + 4 per recurrence value (l, m, ring)",
     "leg_synth": "4 per (l, m, ring, map) product + 4 per recurrence value (l, m, ring)",
@@ -47,7 +48,7 @@ def parse():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--precision", choices=["fp32", "tf32x3", "fp64"], default="tf32x3")
     ap.add_argument("--quad-fft64", action="store_true", help="FP32 plans: theta quadrature by FP64 FFTs")
-    ap.add_argument("--tc-split3", action="store_true", help="tf32x3 plans: two-part TF32 split (3 MMAs)")
+    ap.add_argument("--tc-split3", action="store_true", help="tf32x3 plans: three-part TF32 split (6 MMAs)")
     ap.add_argument("--L", type=int, default=2048)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--B", type=int, default=2)
@@ -285,7 +286,29 @@ def run_gpu(a, rank, world, local_rank):
     dom = max(stats, key=lambda k: stats[k]["ms"])
     sd = stats[dom]
     peaks = measured_peaks()
-    if sd["flops"] > 0:
+    if sd["flops"] > 0 and a.precision == "tf32x3":
+        # a contraction stage on the tensor cores (split TF32: 3 MMAs per product).  Peak:
+        # TF32 dense from the measured sustained BF16 rate times the nominal TF32/BF16
+        # ratio (1.1 / 2.25 PFLOP/s), the stage being timed inside a long step
+        bf = peaks.get("bf16_tflops_sustained", 1700.0)
+        peak = bf * TF32_PER_BF16
+        achieved = sd["flops"] / (sd["ms"] / 1000.0) / 1e12 if sd["ms"] > 0 else 0.0
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "peak_source": "TF32 dense = MEASURED_PEAKS.json bf16_tflops_sustained %.1f (of measured) x 1.1/2.25"
+                               % bf,
+                "flops_counted": FLOPS_COUNTED.get(dom, "") + " (algorithmic)",
+                "executed_mma_frac": 3.0 * achieved / peak,
+                "executed_note": "the split-TF32 product runs 3 MMAs per algorithmic multiply-add",
+                "avg_launch_ms": sd["ms"] / max(sd["timed"], 1)}
+        if dom == "theta_quad":
+            # DRAM bytes of one quadrature stage (two parity launches of k_quad_tcp): ncu measured
+            # 276.9 + 235.5 MB per launch at L = 1024, 64 maps (the F read and G written, 0.954 of
+            # them); the traffic grows with orders x rings x maps, i.e. L^2 x maps
+            roof["traffic"] = 2 * 512.4e6 * (a.L / 1024.0) ** 2 * a.batch / 64.0
+            roof["traffic_note"] = ("dram read+write per quadrature stage (2 launches), from one ncu capture at "
+                                    "L=1024 x 64 maps scaled by L^2 x maps; avg_launch_ms is per stage as well")
+    elif sd["flops"] > 0:
         # a contraction stage: FP32 (or FP64) FMA pipe; peak derived from unit counts and clock
         mhz = peaks.get("sm_max_mhz", 2070.0)
         if a.precision in ("fp32", "tf32x3"):
@@ -307,7 +330,10 @@ def run_gpu(a, rank, world, local_rank):
                 "traffic": None, "kernel": dom, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                 "avg_launch_ms": sd["ms"] / max(sd["timed"], 1)}
     # every contraction stage against the same pipe peak, for context
-    pipe = roof["peak"] if roof["bound"] == "alu" else SM_COUNT * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) / 1e6
+    if a.precision == "tf32x3":
+        pipe = peaks.get("bf16_tflops_sustained", 1700.0) * TF32_PER_BF16
+    else:
+        pipe = roof["peak"] if roof["bound"] == "alu" else SM_COUNT * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) / 1e6
     roof["all_stages"] = {k: {"ms_per_step": v["ms"] / a.steps,
                               "tflops": (v["flops"] / (v["ms"] / 1000.0) / 1e12 if v["ms"] > 0 and v["flops"] else None),
                               "frac_of_pipe": (v["flops"] / (v["ms"] / 1000.0) / 1e12 / pipe
