@@ -105,22 +105,32 @@ __device__ __forceinline__ float4 lt_coef_load(const float4 *cm, int l, int N)
 // r of tensor memory: it writes its split lambda values straight into TMEM
 // (tcgen05.st) and the MMAs read operand A from there, so the tensor core's
 // shared-memory traffic is operand B only and does not throttle the recurrence.
-// Operands of chunk c: stage q = c % LS_NA (A in TMEM columns 256 + 64 q (hi) and
-// + 32 (lo), B in shared memory); accumulator c % 2 in TMEM columns 128 (c % 2).
-// Barriers: full[q] (4 recurrence + 8 operand-B warps), empty[q] (the chunk's
-// MMAs completed: stage q free, accumulator ready), tempty[c % 2] (drained).
+// Rings of different depth for chunk c:
+//   operand A in TMEM        stage c % LS_NA    columns 384 + 64 (c % LS_NA) (hi), + 32 (lo)
+//   accumulator in TMEM      buffer c % LS_NACC columns 128 (c % LS_NACC)
+//   operand B in shared mem  stage c % LS_NB
+// Barriers: full[c % LS_NR] (4 recurrence + 8 operand-B warps arrive), done[c %
+// LS_NR] (one commit: the chunk's MMAs completed, so its A and B stages are free
+// and its accumulator can be drained), tempty[c % LS_NACC] (drained).  LS_NR is
+// a common multiple of the ring depths, and no waiter runs LS_NR chunks behind,
+// so one commit per chunk serves every ring.  More accumulators than operand-A
+// stages: a chunk's MMAs wait for the drain three chunks back, which hides the
+// commit-to-drain round trip behind the recurrence.
 // Each recurrence warp stages its chunk's 32 recurrence coefficients in shared
-// memory and every lane reads them with broadcast loads.
-constexpr int LS_NA = 4;
+// memory and every lane reads them with broadcast loads.  Waits poll without
+// suspending (lt_spin): measured faster here than suspending waits.
+constexpr int LS_NA = 2, LS_NACC = 3, LS_NB = 4, LS_NR = 12;
 constexpr int LS_STAGE = 2 * LT_PLANE;                 // operand B hi, lo
 struct LsSync {
-    uint64_t full[LS_NA], empty[LS_NA], tempty[2], done;
+    uint64_t full[LS_NR], done[LS_NR], tempty[LS_NACC], fin;
     uint32_t tslot;
     int abort, lmin;
 };
-constexpr int LS_COEF_OFF = LS_NA * LS_STAGE;          // 4 warps x 32 float4
+constexpr int LS_COEF_OFF = LS_NB * LS_STAGE;          // 4 warps x 32 float4
 constexpr int LS_SYNC_OFF = LS_COEF_OFF + LT_REC_WARPS * 32 * 16;
 __host__ __device__ constexpr size_t ls_synth_smem() { return (size_t)LS_SYNC_OFF + 256 + 1024; }
+static_assert(sizeof(LsSync) <= 256, "sync block");
+static_assert(LS_NR % LS_NA == 0 && LS_NR % LS_NACC == 0 && LS_NR % LS_NB == 0, "barrier ring");
 
 template <bool CPLX>
 static __global__ void __launch_bounds__(LT_THREADS, 1)
@@ -137,18 +147,20 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
     const int t0 = blockIdx.x * 128, m = blockIdx.y, b0 = blockIdx.z * BT;
     const bool two = CPLX && m > 0;
     volatile int *abort = &sy.abort;
+    // phase parity of the completion / readiness of chunk c
+    auto par = [](int c) -> uint32_t { return (uint32_t)((c / LS_NR) & 1); };
 
     int ls = N;
     if (warp < LT_REC_WARPS && t0 + tid < N) ls = tab.ls[(size_t)m * N + t0 + tid];
     if (tid == 0) {
 #pragma unroll
-        for (int i = 0; i < LS_NA; ++i) {
+        for (int i = 0; i < LS_NR; ++i) {
             tc::mbar_init(&sy.full[i], LT_REC_WARPS + LT_OPB_WARPS);
-            tc::mbar_init(&sy.empty[i], 1);
+            tc::mbar_init(&sy.done[i], 1);
         }
-        tc::mbar_init(&sy.tempty[0], LT_OPB_WARPS);
-        tc::mbar_init(&sy.tempty[1], LT_OPB_WARPS);
-        tc::mbar_init(&sy.done, 1);
+#pragma unroll
+        for (int i = 0; i < LS_NACC; ++i) tc::mbar_init(&sy.tempty[i], LT_OPB_WARPS);
+        tc::mbar_init(&sy.fin, 1);
         sy.abort = 0;
         sy.lmin = N;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -184,9 +196,9 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
             wc[lane] = cf_next;                       // this chunk's coefficients, lane j: degree l0 + j
             __syncwarp();
             cf_next = lt_coef_load(cm, lstart + 32 * (c + 1) + lane, N);
-            if (c >= LS_NA) lt_wait(&sy.empty[q], ((c / LS_NA) - 1) & 1, abort);
+            if (c >= LS_NA) lt_spin(&sy.done[(c - LS_NA) % LS_NR], par(c - LS_NA), abort);
             tc::fence_after();
-            const uint32_t ahi = tmem + lane_addr + (uint32_t)(256 + 64 * q), alo = ahi + 32;
+            const uint32_t ahi = tmem + lane_addr + (uint32_t)(384 + 64 * q), alo = ahi + 32;
             const int l0 = lstart + 32 * c;
 #pragma unroll
             for (int g = 0; g < 4; ++g) {
@@ -199,7 +211,7 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
             tc::tmem_wait_st();
             tc::fence_before();
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&sy.full[q]);
+            if (lane == 0) tc::mbar_arrive(&sy.full[c % LS_NR]);
         }
     } else if (warp < LT_MMA_WARP) {
         // ------------------------------------------------ operand B (c_l f_lm) and drains
@@ -210,10 +222,10 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
         for (int i = 0; i < 64; ++i) sum[i] = 0.f;
         const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
         const int h = (warp - LT_REC_WARPS) >> 2;
-        auto drain = [&](int c) {                     // accumulator c % 2 into sum
-            lt_wait(&sy.empty[c % LS_NA], (c / LS_NA) & 1, abort);
+        auto drain = [&](int c) {                     // accumulator c % LS_NACC into sum
+            lt_spin(&sy.done[c % LS_NR], par(c), abort);
             tc::fence_after();
-            const uint32_t acc = tmem + lane_addr + (uint32_t)(128 * (c & 1) + 64 * h);
+            const uint32_t acc = tmem + lane_addr + (uint32_t)(128 * (c % LS_NACC) + 64 * h);
 #pragma unroll
             for (int g = 0; g < 4; ++g) {
                 float v[16];
@@ -223,11 +235,11 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
             }
             tc::fence_before();
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&sy.tempty[c & 1]);
+            if (lane == 0) tc::mbar_arrive(&sy.tempty[c % LS_NACC]);
         };
         int drained = 0;
         for (int c = 0; c < nk; ++c) {
-            const int q = c % LS_NA;
+            const int q = c % LS_NB;
             const int l0 = lstart + 32 * c;
             auto row = [&](int p) -> const float2 * {
                 const int sg = p / BT, b = p % BT;
@@ -237,10 +249,12 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
             };
             LtB bv;
             bv.load(u, row, N - l0, kfac ? kfac + l0 : nullptr);
-            while (drained <= c - 2) drain(drained++);
-            if (c >= LS_NA) lt_wait(&sy.empty[q], ((c / LS_NA) - 1) & 1, abort);
+            // the accumulator of chunk c - LS_NACC must be drained before chunk c's MMAs;
+            // draining no earlier keeps operand B LS_NACC chunks ahead of the MMAs
+            while (drained <= c - LS_NACC) drain(drained++);
+            if (c >= LS_NB) lt_spin(&sy.done[(c - LS_NB) % LS_NR], par(c - LS_NB), abort);
             bv.store(smem + q * LS_STAGE, u);
-            lt_warp_arrive(&sy.full[q], lane);
+            lt_warp_arrive(&sy.full[c % LS_NR], lane);
         }
         while (drained < nk) drain(drained++);
         // epilogue: TMEM lane = ring
@@ -262,14 +276,13 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
         // ------------------------------------------------ MMA issue: A from TMEM, B from shared memory
         constexpr uint32_t IDESC = tc::idesc_tf32(128, 128);
         for (int c = 0; c < nk; ++c) {
-            const int q = c % LS_NA;
-            bool ok = lt_wait(&sy.full[q], (c / LS_NA) & 1, abort);
-            if (c >= 2) ok = lt_wait(&sy.tempty[c & 1], ((c >> 1) - 1) & 1, abort) && ok;
+            bool ok = lt_spin(&sy.full[c % LS_NR], par(c), abort);
+            if (c >= LS_NACC) ok = lt_spin(&sy.tempty[c % LS_NACC], ((c / LS_NACC) - 1) & 1, abort) && ok;
             tc::fence_after();
             if (ok) {
-                const uint32_t bbase = tc::smem_addr(smem + q * LS_STAGE);
-                const uint32_t acc = tmem + (uint32_t)(128 * (c & 1));
-                const uint32_t ahi = tmem + (uint32_t)(256 + 64 * q), alo = ahi + 32;
+                const uint32_t bbase = tc::smem_addr(smem + (c % LS_NB) * LS_STAGE);
+                const uint32_t acc = tmem + (uint32_t)(128 * (c % LS_NACC));
+                const uint32_t ahi = tmem + (uint32_t)(384 + 64 * (c % LS_NA)), alo = ahi + 32;
 #pragma unroll
                 for (int ks = 0; ks < 4; ++ks) {
                     const uint64_t b0d = tc::smem_desc_sw128(bbase + ks * 32);
@@ -279,10 +292,10 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
                     tc::mma_tf32_ts(acc, ahi + 8 * ks, b0d, IDESC, 1u);
                 }
             }
-            tc::mma_commit(&sy.empty[q]);
+            tc::mma_commit(&sy.done[c % LS_NR]);
         }
-        tc::mma_commit(&sy.done);
-        tc::mbar_wait(&sy.done, 0, 1u << 22);   // no MMA in flight when TMEM is released
+        tc::mma_commit(&sy.fin);
+        tc::mbar_wait(&sy.fin, 0, 1u << 22);   // no MMA in flight when TMEM is released
     }
     tc::fence_before();
     __syncthreads();

@@ -61,6 +61,29 @@ __device__ __forceinline__ bool lt_wait(uint64_t *bar, uint32_t parity, volatile
     return false;
 }
 
+// As lt_wait, polling with the non-blocking test_wait instead of a suspending
+// try_wait (for waits on the critical path of a block whose other warps have
+// issue slots to spare).
+__device__ __forceinline__ bool lt_spin(uint64_t *bar, uint32_t parity, volatile int *abort)
+{
+    for (uint32_t i = 0; i < (1u << 26); ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n"
+            ".reg .pred p;\n"
+            "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n"
+            "}\n"
+            : "=r"(ok)
+            : "r"(tc::smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((i & 255) == 255 && *abort) return false;
+    }
+    *abort = 1;
+    return false;
+}
+
 // The calling warp's shared-memory writes are complete and visible to the
 // tensor core: every lane fences the async proxy, then one arrival for the warp.
 __device__ __forceinline__ void lt_warp_arrive(uint64_t *bar, int lane)
