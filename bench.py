@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--fp64-batch", type=int, default=8)
     ap.add_argument("--cpu-orders", type=int, default=128)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
+                    help="autotune the plan (kernel choice per stage and band-limit) before the warm-up")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
@@ -250,6 +252,7 @@ def run_gpu(a, rank, world, local_rank):
     fw, fs = plan.empty_wavelets()
     out = plan.empty_map()
     stream = torch.cuda.current_stream()
+    tuning = plan.autotune() if a.autotune else None
 
     def step(src=x):
         plan.analysis(src, fw, fs)
@@ -350,6 +353,8 @@ def run_gpu(a, rank, world, local_rank):
            "dtype": {"fp32": "f32", "tf32x3": "tf32x3+f32", "fp64": "f64"}[a.precision], "data": "synthetic",
            "config": config(a),
            "gpu_launches": launches, "roofline": roof, "stages": stage_share, "clocks": clk}
+    if tuning is not None:
+        res["tuning"] = {str(n): t for n, t in tuning.items()}
 
     # end to end: pinned host maps in, host maps out, copies inside the timed region
     if not a.skip_e2e:

@@ -151,6 +151,11 @@ int s2let_batch_map_layout(const s2let_batch *batch, int i, int64_t *f_off, int6
 int s2let_batch_group_plan(const s2let_batch *batch, int g, s2let_plan **plan, int64_t *f_off, int64_t *wav_off,
                            int64_t *scal_off);
 
+/* Autotunes every group's plan (s2let_plan_autotune) on `stream` and drops the
+ * graphs captured so far, so that the next round trip captures the chosen
+ * kernels.  Synchronises the stream. */
+int s2let_batch_autotune(s2let_batch *batch, void *stream);
+
 /* Analysis then synthesis of every map (f -> f_wav, f_scal -> f_out).  The
  * first call for a given set of pointers and stream captures the work of all
  * groups, each group on its own forked stream, into one CUDA graph; later
@@ -185,6 +190,21 @@ int s2let_plan_profile(s2let_plan *plan, int enable);
  * and output spectra).  Any output pointer may be NULL. */
 int s2let_plan_stage_stats(s2let_plan *plan, int stage, int64_t *launches, int64_t *timed, double *ms,
                            double *flops, double *bytes);
+
+/* Autotuner.  For every band-limit of the plan, times the candidate kernels of
+ * each stage on the plan's own workspace (contents ignored) with the plan's
+ * batch, and keeps the fastest: the ring-DFT block size (M/8, M/16, M/32 or
+ * M/64 threads, 32..512) for all plans, and for TF32X3 plans, per contraction stage
+ * (quadrature, Legendre analysis, Legendre synthesis), the tensor-core kernel
+ * or the CUDA-core FP32 kernel (same float-float recurrence; both meet the
+ * TF32X3 accuracy).  Runs on `stream` and synchronises it; overwrites the
+ * workspace; the choices persist for the plan.  Without this call the plan
+ * uses the tensor-core kernels and M/16 threads. */
+int s2let_plan_autotune(s2let_plan *plan, void *stream);
+
+/* The choices in force for band-limit N of the plan (1 = tensor-core kernel). */
+int s2let_plan_tuning(const s2let_plan *plan, int N, int *tc_quad, int *tc_anal, int *tc_synth,
+                      int *fft_threads);
 
 /* ---- allocation-free inverse transform (no counterpart in the paper) -----
  * For callers that cannot allocate device memory: code that runs while a

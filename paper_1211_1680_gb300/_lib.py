@@ -41,6 +41,10 @@ SIGNATURES = {
     "s2let_sht_forward": (_i, [_vp, _vp, _vp, _vp]),
     "s2let_sht_inverse": (_i, [_vp, _vp, _vp, _vp]),
     "s2let_plan_status": (_i, [_vp]),
+    "s2let_plan_autotune": (_i, [_vp, _vp]),
+    "s2let_batch_autotune": (_i, [_vp, _vp]),
+    "s2let_plan_tuning": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                               ctypes.POINTER(_i)]),
     "s2let_plan_profile": (_i, [_vp, _i]),
     "s2let_plan_stage_stats": (_i, [_vp, _i, _i64p, _i64p, ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),

@@ -152,6 +152,19 @@ int s2let_batch_group_plan(const s2let_batch *b, int g, s2let_plan **plan, int64
     return S2LET_OK;
 }
 
+int s2let_batch_autotune(s2let_batch *b, void *stream)
+{
+    if (!b) return S2LET_ERR_ARG;
+    for (auto &g : b->groups) {
+        const int e = s2let_plan_autotune(g.plan, stream);
+        if (e) return e;
+    }
+    // graphs captured before hold the earlier kernel choices
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+    b->graphs.clear();
+    return S2LET_OK;
+}
+
 int s2let_batch_round_trip(s2let_batch *b, const void *f, void *fw, void *fs, void *fo, void *stream)
 {
     if (!b || !f || !fw || !fs || !fo) return S2LET_ERR_ARG;

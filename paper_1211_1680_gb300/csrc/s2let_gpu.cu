@@ -74,6 +74,10 @@ struct BandDev {
     float *Qe = nullptr, *Qo = nullptr;     // FP32 plans: quadrature matrices, even / odd m
     float *Qe3 = nullptr, *Qo3 = nullptr;   // TF32X3 plans with three-part split: three TF32 planes
     unsigned char *Qei = nullptr, *Qoi = nullptr;   // TF32X3 plans: operand-A images of the two-part split
+    // kernel choices (s2let_plan_autotune): tensor-core or CUDA-core kernels per
+    // stage in TF32X3 plans, and the ring-DFT block size (0: M/16)
+    bool tc_quad = true, tc_anal = true, tc_synth = true;
+    int fft_th = 0;
 };
 
 }  // namespace
@@ -189,7 +193,7 @@ int run_ring_fwd(const s2let_plan *p, const BandDev &bd, const void *f, void *F,
 {
     const auto &T = fft_tab<R>(bd);
     const size_t sm = (size_t)padded_len(bd.M) * sizeof(cplx_t<R>);
-    const int th = fft_threads(bd.M);
+    const int th = bd.fft_th ? bd.fft_th : fft_threads(bd.M);
     StageScope sc(p, S2LET_STAGE_RING_FWD, st, 0.0, map_bytes(p, bd.N) + 3.0 * spectrum_bytes(p, bd.N), 2);
     if (p->cplx) {
         k_ring_fwd_cplx<R><<<dim3(bd.N, p->batch), th, sm, st>>>((const cplx_t<R> *)f, (cplx_t<R> *)p->Ft, (R)scale,
@@ -211,7 +215,7 @@ int run_ring_inv(const s2let_plan *p, const BandDev &bd, const void *F, void *f,
 {
     const auto &T = fft_tab<R>(bd);
     const size_t sm = (size_t)padded_len(bd.M) * sizeof(cplx_t<R>);
-    const int th = fft_threads(bd.M);
+    const int th = bd.fft_th ? bd.fft_th : fft_threads(bd.M);
     StageScope sc(p, S2LET_STAGE_RING_INV, st, 0.0, map_bytes(p, bd.N) + 3.0 * spectrum_bytes(p, bd.N), 2);
     // F[b][mi][t] -> Ft[b][t][mi]
     const int n = nmi(p, bd.N);
@@ -246,11 +250,11 @@ void *run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream
             const int nj = (n - 1 - mi0) / 2 + 1;
             const int npairs = nj * p->batch;
             dim3 grid((bd.N + QG_BM - 1) / QG_BM, (npairs + QG_BN / 2 - 1) / (QG_BN / 2));
-            if (p->tc && p->tc_split == 2)
+            if (p->tc && bd.tc_quad && p->tc_split == 2)
                 k_quad_tcp<<<grid, LT_THREADS, lt_synth_smem(), st>>>(par ? bd.Qoi : bd.Qei, (const float2 *)F,
                                                                        (float2 *)p->G, bd.N, n, mi0, nj, npairs,
                                                                        p->d_err);
-            else if (p->tc)
+            else if (p->tc && bd.tc_quad)
                 k_quad_tc<3, 2><<<grid, TQ_THREADS, TqShape<3, 2>::SMEM, st>>>(
                     par ? bd.Qo3 : bd.Qe3, (const float2 *)F, (float2 *)p->G, bd.N, n, mi0, nj, npairs, p->d_err);
             else
@@ -297,11 +301,11 @@ int run_synth(const s2let_plan *p, const BandDev &bd, const void *src, const voi
         const int bt = p->cplx ? LegCols<true>::BT : LegCols<false>::BT;
         dim3 grid((bd.N + LS_RT - 1) / LS_RT, bd.N, (p->batch + bt - 1) / bt);
         const LegTab<float> tab = leg_tab<float>(p, bd);
-        if (p->tc && p->cplx)
+        if (p->tc && bd.tc_synth && p->cplx)
             k_leg_synth_tc<true><<<grid, LT_THREADS, ls_synth_smem(), st>>>(
                 (const float2 *)src, p->L, (const float *)kfac, (float)scale, (float2 *)dst, bd.N, p->batch, tab,
                 p->d_err);
-        else if (p->tc)
+        else if (p->tc && bd.tc_synth)
             k_leg_synth_tc<false><<<grid, LT_THREADS, ls_synth_smem(), st>>>(
                 (const float2 *)src, p->L, (const float *)kfac, (float)scale, (float2 *)dst, bd.N, p->batch, tab,
                 p->d_err);
@@ -359,11 +363,11 @@ int run_anal(const s2let_plan *p, const BandDev &bd, const void *G, const void *
         dim3 grid(bd.N, (p->batch + bt - 1) / bt);
         const size_t sm = anal_gemm_smem(bd.N);
         const LegTab<float> tab = leg_tab<float>(p, bd);
-        if (p->tc && p->cplx)
+        if (p->tc && bd.tc_anal && p->cplx)
             k_leg_anal_tc<true><<<grid, LT_ANAL_THREADS, lt_anal_smem(bd.N), st>>>(
                 (const float2 *)G, bd.N, (const float *)kfac, (float)scale, acc, (float2 *)dst, p->L, p->batch, tab,
                 p->d_err);
-        else if (p->tc)
+        else if (p->tc && bd.tc_anal)
             k_leg_anal_tc<false><<<grid, LT_ANAL_THREADS, lt_anal_smem(bd.N), st>>>(
                 (const float2 *)G, bd.N, (const float *)kfac, (float)scale, acc, (float2 *)dst, p->L, p->batch, tab,
                 p->d_err);
@@ -820,6 +824,94 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
 }  // namespace
 
 // ------------------------------------------------------------ C ABI
+// ------------------------------------------------------------ autotuning
+namespace {
+
+// Median-free best-of timing of fn on the stream (ms); warm-up run first.
+template <typename Fn> float time_best(cudaStream_t st, Fn fn, int reps = 3)
+{
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    fn();
+    float best = 1e30f;
+    for (int i = 0; i < reps; ++i) {
+        cudaEventRecord(a, st);
+        fn();
+        cudaEventRecord(b, st);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        best = std::min(best, ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
+template <typename R> int autotune_t(s2let_plan *p, cudaStream_t st)
+{
+    // workspace as scratch operands: their contents do not change the timings
+    const size_t ws = (size_t)p->batch * nmi(p, p->L) * p->L * 2 * elem_size(p);
+    if (cudaMemsetAsync(p->F, 0, ws, st) != cudaSuccess || cudaMemsetAsync(p->flm, 0, ws, st) != cudaSuccess)
+        return S2LET_ERR_CUDA;
+    if (p->G && cudaMemsetAsync(p->G, 0, ws, st) != cudaSuccess) return S2LET_ERR_CUDA;
+    const bool prof = p->prof;
+    int64_t launches[S2LET_N_STAGES];
+    std::copy(p->launches, p->launches + S2LET_N_STAGES, launches);
+    p->prof = false;
+    int e = S2LET_OK;
+    for (auto &kv : p->bands) {
+        BandDev &bd = kv.second;
+        // ring DFTs: block of M/8, M/16, M/32 or M/64 threads (32 .. FFT_MAX_THREADS)
+        std::vector<int> ths;
+        for (int d : {8, 16, 32, 64}) {
+            const int th = std::max(32, std::min(FFT_MAX_THREADS, bd.M / d));
+            if (std::find(ths.begin(), ths.end(), th) == ths.end()) ths.push_back(th);
+        }
+        float best = 1e30f;
+        int best_th = 0;
+        for (int th : ths) {
+            bd.fft_th = th;
+            const float ms = time_best(st, [&] {
+                run_ring_fwd<R>(p, bd, p->flm, p->F, 1.0, st);
+                run_ring_inv<R>(p, bd, p->F, p->flm, 1.0, st);
+            });
+            if (ms < best) {
+                best = ms;
+                best_th = th;
+            }
+        }
+        bd.fft_th = best_th;
+        if (p->tc) {
+            // each contraction stage: tensor-core kernel or CUDA-core GEMM kernel
+            bd.tc_quad = true;
+            const float q1 = time_best(st, [&] { run_theta_quad<R>(p, bd, p->F, st, &e); });
+            bd.tc_quad = false;
+            const float q0 = time_best(st, [&] { run_theta_quad<R>(p, bd, p->F, st, &e); });
+            bd.tc_quad = q1 <= q0;
+            bd.tc_synth = true;
+            const float s1 = time_best(st, [&] { run_synth<R>(p, bd, p->flm, nullptr, 1.0, p->F, st); });
+            bd.tc_synth = false;
+            const float s0 = time_best(st, [&] { run_synth<R>(p, bd, p->flm, nullptr, 1.0, p->F, st); });
+            bd.tc_synth = s1 <= s0;
+            bd.tc_anal = true;
+            const float a1 = time_best(st, [&] { run_anal<R>(p, bd, p->F, nullptr, 1.0, 0, p->flm, st); });
+            bd.tc_anal = false;
+            const float a0 = time_best(st, [&] { run_anal<R>(p, bd, p->F, nullptr, 1.0, 0, p->flm, st); });
+            bd.tc_anal = a1 <= a0;
+        }
+        if (cudaGetLastError() != cudaSuccess) e = S2LET_ERR_CUDA;
+        if (e) break;
+    }
+    p->prof = prof;
+    std::copy(launches, launches + S2LET_N_STAGES, p->launches);
+    if (!e && cudaStreamSynchronize(st) != cudaSuccess) e = S2LET_ERR_CUDA;
+    return e;
+}
+
+}  // namespace
+
 extern "C" {
 
 int s2let_jmax(int L, int B)
@@ -898,6 +990,26 @@ int s2let_sht_inverse(s2let_plan *p, const void *flm, void *f, void *stream)
 {
     if (!p || !f || !flm) return S2LET_ERR_ARG;
     return S2_DISPATCH(sht_inverse_t, p, flm, f, (cudaStream_t)stream);
+}
+
+
+int s2let_plan_autotune(s2let_plan *p, void *stream)
+{
+    if (!p) return S2LET_ERR_ARG;
+    return S2_DISPATCH(autotune_t, p, (cudaStream_t)stream);
+}
+
+int s2let_plan_tuning(const s2let_plan *p, int N, int *tc_quad, int *tc_anal, int *tc_synth, int *fft_threads_out)
+{
+    if (!p) return S2LET_ERR_ARG;
+    auto it = p->bands.find(N);
+    if (it == p->bands.end()) return S2LET_ERR_ARG;
+    const BandDev &bd = it->second;
+    if (tc_quad) *tc_quad = p->tc && bd.tc_quad;
+    if (tc_anal) *tc_anal = p->tc && bd.tc_anal;
+    if (tc_synth) *tc_synth = p->tc && bd.tc_synth;
+    if (fft_threads_out) *fft_threads_out = bd.fft_th ? bd.fft_th : fft_threads(bd.M);
+    return S2LET_OK;
 }
 
 int s2let_plan_status(s2let_plan *p)

@@ -63,6 +63,22 @@ class Plan:
                                                            ctypes.byref(cnt)))
             self.scales.append((j, n.value, off.value, cnt.value))
 
+    def autotune(self, stream=None):
+        """Time the candidate kernels of every stage and band-limit and keep the
+        fastest (s2let_plan_autotune); returns the choices (see tuning())."""
+        check("s2let_plan_autotune", _lib.lib().s2let_plan_autotune(self._h, _stream_handle(stream)))
+        return self.tuning()
+
+    def tuning(self):
+        """{band-limit: {"tc_quad", "tc_anal", "tc_synth": bool, "fft_threads": int}}."""
+        out = {}
+        for n in sorted({self.L, self.N_scal} | {s[1] for s in self.scales}):
+            v = [ctypes.c_int() for _ in range(4)]
+            check("s2let_plan_tuning", _lib.lib().s2let_plan_tuning(self._h, n, *[ctypes.byref(x) for x in v]))
+            out[n] = {"tc_quad": bool(v[0].value), "tc_anal": bool(v[1].value), "tc_synth": bool(v[2].value),
+                      "fft_threads": v[3].value}
+        return out
+
     def status(self):
         """S2LET_OK, or S2LET_ERR_TIMEOUT if a bounded device wait gave up (synchronises)."""
         return _lib.lib().s2let_plan_status(self._h)
@@ -210,6 +226,11 @@ class BatchPlan:
             check("s2let_batch_group_plan", lib.s2let_batch_group_plan(self._h, g, ctypes.byref(ph), ctypes.byref(fo),
                                                                        ctypes.byref(wo), ctypes.byref(so)))
             self.groups.append((ph.value, fo.value, wo.value, so.value))
+
+    def autotune(self, stream=None):
+        """Autotune every group's plan (kernel choice per stage and band-limit,
+        ring-DFT block size); later round trips capture the chosen kernels."""
+        check("s2let_batch_autotune", _lib.lib().s2let_batch_autotune(self._h, _stream_handle(stream)))
 
     def close(self):
         if self._h:

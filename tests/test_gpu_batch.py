@@ -55,3 +55,29 @@ def test_uneven_batch_round_trip(real, prec):
             shape = (n.value, 2 * n.value - 1) if real else (n.value, 2 * n.value - 1, 2)
             got = from_dev_map(fw[start:start + per].view(shape), real)
             assert rel_err(got, ref) < TOL[prec], (i, j)
+
+
+def test_autotuned_batch_round_trip():
+    """s2let_batch_autotune before the first round trip and again between two
+    (the cached graph is dropped and captured with the new choices)."""
+    Ls = [16, 40, 9, 40]
+    Bs = [2, 2, 3, 2]
+    real, prec = True, "tf32x3"
+    bp = BatchPlan(Ls, Bs, 1, real=real, multires=True, precision=prec)
+    f, fw, fs, fo = bp.buffers()
+    maps = []
+    for i, (L, B) in enumerate(zip(Ls, Bs)):
+        x = sht.inverse(inputs.random_flm(L, 70 + i, real), L, real=real)
+        maps.append(x)
+        bp.map_view(f, i).copy_(torch.from_numpy(np.ascontiguousarray(x)))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        bp.autotune()
+        for rep in range(3):
+            if rep == 2:
+                bp.autotune()
+            fo.fill_(float("nan"))
+            bp.round_trip(f, fw, fs, fo)
+            stream.synchronize()
+            for i in range(len(Ls)):
+                assert rel_err(from_dev_map(bp.map_view(fo, i), real), maps[i]) < TOL[prec], (rep, i)

@@ -132,3 +132,28 @@ def test_plans_of_different_sizes_coexist():
         flm = inputs.random_flm(L, 3, True)
         f = from_dev_map(plan.sht_inverse(flm_to_dev(flm[None], plan.dtype)), True)
         assert rel_err(f[0], sht.inverse(flm, L, real=True)) < TOL["fp32"]
+
+
+@pytest.mark.parametrize("prec,real", [("tf32x3", True), ("tf32x3", False), ("fp32", True)])
+def test_autotuned_plan_keeps_parity(prec, real):
+    """After s2let_plan_autotune (kernel choice per stage and band-limit, ring-DFT
+    block size) the transforms still match the oracle."""
+    L = 160
+    flm = np.stack([inputs.random_flm(L, s, real) for s in (51, 52)])
+    plan = Plan(L, 2, 1, batch=2, real=real, multires=True, precision=prec)
+    tuning = plan.autotune()
+    assert set(tuning) >= {L, plan.N_scal}
+    for n, t in tuning.items():
+        assert 32 <= t["fft_threads"] <= 512
+        if prec != "tf32x3":
+            assert not (t["tc_quad"] or t["tc_anal"] or t["tc_synth"])
+    f_ref = np.stack([sht.inverse(x, L, real=real) for x in flm])
+    f_gpu = from_dev_map(plan.sht_inverse(flm_to_dev(flm, plan.dtype)), real)
+    assert rel_err(f_gpu, f_ref) < TOL[prec]
+    g = flm_from_dev(plan.sht_forward(to_dev_map(f_ref, plan.dtype, real)))
+    assert rel_err(g, np.stack([sht.forward(x, L) for x in f_ref])) < TOL[prec]
+    f = np.stack(f_ref)
+    fw_d, fs_d = plan.analysis(to_dev_map(f, plan.dtype, real))
+    rec = from_dev_map(plan.synthesis(fw_d, fs_d), real)
+    assert rel_err(rec, f) < TOL[prec]
+    assert plan.status() == 0
