@@ -434,7 +434,7 @@ static __global__ void __launch_bounds__(LT_ANAL_THREADS, 1)
                     return Gin + ((size_t)(b0 + b) * nmi_src + mi) * N + t0;
                 };
                 LtB bv;
-                bv.load(u, row, N - t0, nullptr);
+                bv.load<true>(u, row, N - t0, nullptr);
                 while (drained <= cc - LT_NS) d.drain(sy, tmem, drained++);
                 bv.store(smem + s * LT_STAGE + 2 * LT_PLANE, u);
                 lt_warp_arrive(&sy.full[s], lane);
