@@ -367,12 +367,14 @@ static __global__ void __launch_bounds__(LT_ANAL_THREADS, 1)
                     const int cc = c++;
                     if (cc % LT_NS != warp) continue;
                     const int s = warp;
-                    if (cc >= LT_NS) lt_wait(&sy.empty[s], ((cc / LT_NS) - 1) & 1, &sy.abort);
-                    unsigned char *A = smem + s * LT_STAGE;
+                    // the ring's tables are loaded before the wait for the stage, so that
+                    // their latency overlaps it
                     const int t = 32 * k + lane;
                     const bool own = t < N;
                     LtRec rec;
                     rec.init(own, tab.ring + t, tab.seed + (size_t)m * N + t, tab.ls + (size_t)m * N + t);
+                    if (cc >= LT_NS) lt_wait(&sy.empty[s], ((cc / LT_NS) - 1) & 1, &sy.abort);
+                    unsigned char *A = smem + s * LT_STAGE;
                     if (own && l0 > rec.ls) {
                         const float4 q = st[t];
                         rec.p0.h = q.x;
