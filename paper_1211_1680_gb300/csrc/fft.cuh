@@ -27,6 +27,7 @@ __host__ __device__ constexpr int padded_len(int M) { return M + (M >> 4); }
 template <typename C> struct FftTab {
     const C *chirp;
     const C *bhat;
+    const C *bhat_g;   // bhat in the order of the fused middle pass: bhat_g[q (M/R) + j] = bhat[R j + q]
     const C *what;
     const C *tw;
     const C *phase;
@@ -274,7 +275,8 @@ __device__ __forceinline__ void dif_pass_load(C *a, int M, int logM, const C *__
     __syncthreads();
 }
 
-// last RB DIF stages, product with khat (bit-reversed positions), first RB DIT
+// last RB DIF stages, product with the kernel table (bit-reversed positions,
+// stored group-major: entry q of group j at khat[q (M / 2^RB) + j]), first RB DIT
 // stages.  The group starts at a multiple of 2^RB, so its twiddles are the
 // 2^RB-th roots of unity e^{-2 pi i (q mod half)/(2 half)} = w16((q mod half) 8 / half).
 template <typename C, int RB, bool CONJ_K>
@@ -302,7 +304,7 @@ __device__ __forceinline__ void mid_pass(C *a, int M, const C *__restrict__ khat
         }
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-            const C k = khat[base + q];
+            const C k = khat[q * (M / R) + j];           // group-major table: coalesced over j
             x[q] = CONJ_K ? cmulc(x[q], k) : cmul(x[q], k);
         }
 #pragma unroll
@@ -429,7 +431,7 @@ __global__ void __launch_bounds__(FFT_MAX_THREADS, sizeof(R) == 4 ? 2 : 1) k_rin
     };
     if (T.logM > fft_rbf<C>()) {
         // the transform is read back at positions < P only
-        conv_fused<C, false>(buf, T, T.bhat, load, [&](int pos, C v) {
+        conv_fused<C, false>(buf, T, T.bhat_g, load, [&](int pos, C v) {
             if (pos < P) buf[pad16(pos)] = v;
         });
     } else {
@@ -472,7 +474,7 @@ __global__ void __launch_bounds__(FFT_MAX_THREADS, sizeof(R) == 4 ? 2 : 1) k_rin
         out[mi] = cscale(cmulc(v, T.chirp[k]), s);
     };
     if (T.logM > fft_rbf<C>()) {
-        conv_fused<C, false>(buf, T, T.bhat, load, store);
+        conv_fused<C, false>(buf, T, T.bhat_g, load, store);
     } else {
         for (int n = threadIdx.x; n < M; n += blockDim.x) buf[pad16(n)] = load(n);
         __syncthreads();
@@ -520,7 +522,7 @@ __global__ void __launch_bounds__(FFT_MAX_THREADS, sizeof(R) == 4 ? 2 : 1) k_rin
         if (has1) o1[p] = v.y * s;
     };
     if (T.logM > fft_rbf<C>()) {
-        conv_fused<C, true>(buf, T, T.bhat, load, store);
+        conv_fused<C, true>(buf, T, T.bhat_g, load, store);
     } else {
         for (int k = threadIdx.x; k < M; k += blockDim.x) buf[pad16(k)] = load(k);
         __syncthreads();
@@ -551,7 +553,7 @@ __global__ void __launch_bounds__(FFT_MAX_THREADS, sizeof(R) == 4 ? 2 : 1) k_rin
         if (p < P) o[p] = cscale(cmul(v, T.chirp[p]), s);
     };
     if (T.logM > fft_rbf<C>()) {
-        conv_fused<C, true>(buf, T, T.bhat, load, store);
+        conv_fused<C, true>(buf, T, T.bhat_g, load, store);
     } else {
         for (int k = threadIdx.x; k < M; k += blockDim.x) buf[pad16(k)] = load(k);
         __syncthreads();

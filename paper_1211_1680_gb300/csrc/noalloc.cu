@@ -29,7 +29,7 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 struct Layout {
-    size_t rect, F, Ft, chirp, bhat, tw, phase, ls, seed, ringf, coeff, ringd, coefd, sinth, mant, expo, total;
+    size_t rect, F, Ft, chirp, bhat, bhat_g, tw, phase, ls, seed, ringf, coeff, ringd, coefd, sinth, mant, expo, total;
 };
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -49,6 +49,7 @@ Layout layout(int N, int nm, int batch, int M)
     o.Ft = take((size_t)batch * nm * N * sizeof(float2));
     o.chirp = take((size_t)(2 * N - 1) * sizeof(float2));
     o.bhat = take((size_t)M * sizeof(float2));
+    o.bhat_g = take((size_t)M * sizeof(float2));
     o.tw = take((size_t)M * sizeof(float2));
     o.phase = take((size_t)(2 * N - 1) * sizeof(float2));
     o.ls = take(nn * sizeof(int));
@@ -111,6 +112,13 @@ int setup(DevState &d, int L, int batch, int cplx)
     std::vector<float2> c(h.chirp.size()), bh(h.bhat.size()), tw(h.tw.size()), ph(h.phase.size());
     for (size_t i = 0; i < c.size(); ++i) c[i] = make_float2((float)h.chirp[i].real(), (float)h.chirp[i].imag());
     for (size_t i = 0; i < bh.size(); ++i) bh[i] = make_float2((float)h.bhat[i].real(), (float)h.bhat[i].imag());
+    // group-major copy for the fused middle FFT pass (groups of R = 2^fft_rbf)
+    std::vector<float2> bg(bh.size());
+    {
+        const size_t R = (size_t)1 << fft_rbf<float2>(), ng = bh.size() / R;
+        for (size_t j = 0; j < ng; ++j)
+            for (size_t q = 0; q < R; ++q) bg[q * ng + j] = bh[R * j + q];
+    }
     for (size_t i = 0; i < tw.size(); ++i) tw[i] = make_float2((float)h.tw[i].real(), (float)h.tw[i].imag());
     for (size_t i = 0; i < ph.size(); ++i) ph[i] = make_float2((float)h.phase[i].real(), (float)h.phase[i].imag());
     std::vector<RingD> rd(L);
@@ -133,6 +141,7 @@ int setup(DevState &d, int L, int batch, int cplx)
     unsigned char *b = d.base;
     if (!e) e = put(b + o.chirp, c);
     if (!e) e = put(b + o.bhat, bh);
+    if (!e) e = put(b + o.bhat_g, bg);
     if (!e) e = put(b + o.tw, tw);
     if (!e) e = put(b + o.phase, ph);
     if (!e) e = put(b + o.ringd, rd);
@@ -206,6 +215,7 @@ extern "C" int s2let_sht_inverse_noalloc(int L, int batch, int flags, const void
     FftTab<float2> T;
     T.chirp = (const float2 *)(b + o.chirp);
     T.bhat = (const float2 *)(b + o.bhat);
+    T.bhat_g = (const float2 *)(b + o.bhat_g);
     T.what = nullptr;
     T.tw = (const float2 *)(b + o.tw);
     T.phase = (const float2 *)(b + o.phase);

@@ -634,6 +634,16 @@ int build_quad_matrices(s2let_plan *p, BandDev &bd)
     return err;
 }
 
+// v[R j + q] -> out[q (n / R) + j]: the order in which the fused middle FFT pass reads its table
+std::vector<s2h::cd> group_major(const std::vector<s2h::cd> &v, int R)
+{
+    const size_t n = v.size(), ng = n / R;
+    std::vector<s2h::cd> out(n);
+    for (size_t j = 0; j < ng; ++j)
+        for (int q = 0; q < R; ++q) out[(size_t)q * ng + j] = v[(size_t)R * j + q];
+    return out;
+}
+
 int build_band_dev(s2let_plan *p, int N, BandDev &bd)
 {
     s2h::Band h;
@@ -646,11 +656,13 @@ int build_band_dev(s2let_plan *p, int N, BandDev &bd)
     auto &o = p->owned;
     bd.fd.chirp = dev_upload(to_c<double2>(h.chirp), o, err);
     bd.fd.bhat = dev_upload(to_c<double2>(h.bhat), o, err);
+    bd.fd.bhat_g = dev_upload(to_c<double2>(group_major(h.bhat, 1 << fft_rbf<double2>())), o, err);
     bd.fd.what = dev_upload(to_c<double2>(h.what), o, err);
     bd.fd.tw = dev_upload(to_c<double2>(h.tw), o, err);
     bd.fd.phase = dev_upload(to_c<double2>(h.phase), o, err);
     bd.ff.chirp = dev_upload(to_c<float2>(h.chirp), o, err);
     bd.ff.bhat = dev_upload(to_c<float2>(h.bhat), o, err);
+    bd.ff.bhat_g = dev_upload(to_c<float2>(group_major(h.bhat, 1 << fft_rbf<float2>())), o, err);
     bd.ff.what = dev_upload(to_c<float2>(h.what), o, err);
     bd.ff.tw = dev_upload(to_c<float2>(h.tw), o, err);
     bd.ff.phase = dev_upload(to_c<float2>(h.phase), o, err);
