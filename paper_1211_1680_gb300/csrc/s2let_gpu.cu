@@ -251,7 +251,7 @@ void *run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream
             const int npairs = nj * p->batch;
             dim3 grid((bd.N + QG_BM - 1) / QG_BM, (npairs + QG_BN / 2 - 1) / (QG_BN / 2));
             if (p->tc && bd.tc_quad && p->tc_split == 2)
-                k_quad_tcp<<<grid, LT_THREADS, lt_synth_smem(), st>>>(par ? bd.Qoi : bd.Qei, (const float2 *)F,
+                k_quad_tcp<<<grid, LT_THREADS, quad_tc_smem(), st>>>(par ? bd.Qoi : bd.Qei, (const float2 *)F,
                                                                        (float2 *)p->G, bd.N, n, mi0, nj, npairs,
                                                                        p->d_err);
             else if (p->tc && bd.tc_quad)
@@ -557,7 +557,7 @@ void set_smem_limits(int Mmax)
     allow_smem(k_ring_fwd_cplx<float>, f);
     allow_smem(k_ring_inv_real<float>, f);
     allow_smem(k_ring_inv_cplx<float>, f);
-    allow_smem(k_quad_tcp, lt_synth_smem());
+    allow_smem(k_quad_tcp, quad_tc_smem());
     allow_smem(k_quad_tc<3, 2>, TqShape<3, 2>::SMEM);
     allow_smem(k_leg_synth_tc<false>, ls_synth_smem());
     allow_smem(k_leg_synth_tc<true>, ls_synth_smem());
@@ -624,7 +624,7 @@ int build_quad_matrices(s2let_plan *p, BandDev &bd)
             }
             p->owned.push_back(img);
             (par ? bd.Qoi : bd.Qei) = img;
-            const size_t npieces = quad_image_bytes(N) / 16 / 2;
+            const size_t npieces = quad_image_bytes(N) / 16;
             k_quad_images<<<(unsigned)((npieces + 255) / 256), 256>>>(Q, img, N);
         }
         if (cudaGetLastError() != cudaSuccess) err = S2LET_ERR_CUDA;
