@@ -14,6 +14,8 @@
 //              the MMAs, so their latency is off the MMA critical path.
 //   operand B  64 pairs x re/im of F, split while stored (LtB) by warps 4-11,
 //              which also drain the accumulators into FP32 registers and write G.
+//              The F values of a chunk arrive by asynchronous copies in a ring
+//              of QT_NF slots (see FRAW below).
 // The tensor core accumulates QT_D chunks (K = 32 QT_D) in one TMEM buffer;
 // the sums of these groups are added in FP32 registers.  Its accumulation error
 // grows with the number of products summed in TMEM, so this bounds it (measured
@@ -23,6 +25,7 @@
 //   accumulator in TMEM      g % QT_NACC  columns 128 (g % QT_NACC)
 //   operand B in shared mem  c % QT_NB
 //   raw A image in shared    c % QT_NRAW
+//   raw F rows in shared     c % QT_NF
 // Barriers: full[c % QT_NR] (4 producer + 8 operand-B warps arrive), done[c %
 // QT_NR] (one commit: the chunk's MMAs completed, so its A and B slots are free,
 // and after a group's last chunk its accumulator can be drained), tempty[g %
@@ -34,22 +37,32 @@
 
 namespace s2g {
 
-constexpr int QT_NA = 2, QT_NACC = 3, QT_NB = 4, QT_NR = 12, QT_NRAW = 6, QT_D = 4;
+constexpr int QT_NA = 2, QT_NACC = 3, QT_NB = 4, QT_NR = 12, QT_NRAW = 4, QT_NF = 2, QT_D = 4;
 constexpr int QT_RAW = LT_PLANE;                   // bytes of one (row tile, K chunk) image
 constexpr int QT_QUARTER = QT_RAW / LT_REC_WARPS;  // one producer warp's rows of an image
 constexpr int QT_BSTAGE = 2 * LT_PLANE;            // operand B hi, lo
+constexpr int QT_FROW = 32 * 8;                    // bytes of one F row of a chunk (32 float2)
+constexpr int QT_FSLOT = 64 * QT_FROW;             // F rows of the block's 64 pairs
 constexpr int QT_RAW_OFF = QT_NB * QT_BSTAGE;
-constexpr int QT_SYNC_OFF = QT_RAW_OFF + QT_NRAW * QT_RAW;
+constexpr int QT_FRAW_OFF = QT_RAW_OFF + QT_NRAW * QT_RAW;
+constexpr int QT_SYNC_OFF = QT_FRAW_OFF + QT_NF * QT_FSLOT;
 struct QtSync {
     uint64_t full[QT_NR], done[QT_NR], tempty[QT_NACC], raw[QT_NRAW][LT_REC_WARPS], fin;
     uint32_t tslot;
     int abort;
 };
-static_assert(sizeof(QtSync) <= 512, "sync block");
+constexpr int QT_SYNC_BYTES = 512;
+static_assert(sizeof(QtSync) <= QT_SYNC_BYTES, "sync block");
 static_assert(QT_NR % QT_NA == 0 && QT_NR % QT_NB == 0 && 2 * QT_D < QT_NR, "barrier ring");
-__host__ __device__ constexpr size_t quad_tc_smem() { return (size_t)QT_SYNC_OFF + 512 + 1024; }
+__host__ __device__ constexpr size_t quad_tc_smem() { return (size_t)QT_SYNC_OFF + QT_SYNC_BYTES + 1024; }
 static_assert(quad_tc_smem() <= 227 * 1024, "shared memory");
 
+// FRAW: F values reach shared memory by 16-byte asynchronous copies (a ring of
+// QT_NF chunks; each operand-B warp copies the rows it splits), so the split
+// reads shared memory and never waits on global loads.  Needs 16-byte
+// aligned rows (N even, F 16-byte aligned); otherwise (FRAW false) each thread
+// loads its units from global memory one chunk ahead into registers.
+template <bool FRAW>
 static __global__ void __launch_bounds__(LT_THREADS, 1)
     k_quad_tcp(const unsigned char *__restrict__ Qimg, const float2 *__restrict__ F, float2 *__restrict__ G, int N,
                int nmi, int mi0, int nj, int npairs, int *err)
@@ -150,50 +163,119 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
             tc::fence_after();
             const uint32_t acc = tmem + lane_addr + (uint32_t)(128 * (g % QT_NACC) + 64 * h);
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
+            for (int q = 0; q < 4; ++q) {
                 float v[16];
-                tc::tmem_ld16(acc + 16 * g, v);
+                tc::tmem_ld16(acc + 16 * q, v);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) sum[16 * g + i] += v[i];
+                for (int i = 0; i < 16; ++i) sum[16 * q + i] += v[i];
             }
             tc::fence_before();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&sy.tempty[g % QT_NACC]);
         };
-        // F rows of this thread's two pairs, loaded one chunk ahead (two register
-        // sets, the loop unrolled by two so that they stay registers)
-        const float2 *frow[2];
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int pp = pair0 + ((u + 256 * i) >> 3);
-            frow[i] = nullptr;
-            if (pp < npairs) {
-                const int b = pp / nj, j = pp % nj;
-                frow[i] = F + ((size_t)b * nmi + mi0 + 2 * j) * N;
-            }
-        }
-        auto load = [&](LtB &bv, int c) {
-            const int k0 = 32 * c;
-            bv.load(u, [&](int p) -> const float2 * {
-                const float2 *rr = frow[p >= 32];
-                return rr ? rr + k0 : nullptr;
-            }, N - k0, nullptr);
-        };
         int drained = 0;
-        auto body = [&](int c, LtB &cur, LtB &next) {
-            if (c >= nk) return;
-            if (c + 1 < nk) load(next, c + 1);
-            // the accumulator of group c / QT_D - QT_NACC must be drained before chunk c's MMAs
-            while (drained <= c / QT_D - QT_NACC) drain(drained++);
-            if (c >= QT_NB) lt_spin(&sy.done[(c - QT_NB) % QT_NR], par(c - QT_NB), abort);
-            cur.store(smem + (c % QT_NB) * QT_BSTAGE, u);
-            lt_warp_arrive(&sy.full[c % QT_NR], lane);
-        };
-        LtB b0, b1;
-        if (nk > 0) load(b0, 0);
-        for (int c = 0; c < nk; c += 2) {
-            body(c, b0, b1);
-            body(c + 1, b1, b0);
+        if constexpr (FRAW) {
+            // Operand-B warp wb splits the units of pairs 4 wb .. 4 wb + 3 and 32 + 4 wb ..
+            // 32 + 4 wb + 3: it stages exactly these 8 rows (256 bytes of a chunk each)
+            // with 16-byte asynchronous copies, QT_NF chunks ahead.  Lane l copies
+            // piece l & 15 of rows 2 r + (l >> 4), r = 0..3, so each copy instruction
+            // covers two whole rows; values past N and rows of absent pairs are zero-
+            // filled.  After its own copies land (wait_group), a warp barrier makes
+            // the warp's rows visible to all its lanes.
+            const int wb = warp - LT_REC_WARPS;
+            unsigned char *fraw = smem + QT_FRAW_OFF;
+            const int q = lane & 15;
+            const float2 *srow[4];
+            uint32_t drow[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int j = 2 * r + (lane >> 4);
+                const int p = j < 4 ? 4 * wb + j : 32 + 4 * wb + (j - 4), pp = pair0 + p;
+                srow[r] = nullptr;
+                if (pp < npairs) {
+                    const int b = pp / nj, jj = pp % nj;
+                    srow[r] = F + ((size_t)b * nmi + mi0 + 2 * jj) * N + 2 * q;
+                }
+                drow[r] = tc::smem_addr(fraw + p * QT_FROW + 16 * q);
+            }
+            auto issue = [&](int c) {                 // the warp's rows of chunk c, slot c % QT_NF
+                const int k0 = 32 * c, nv = max(0, min(2, N - k0 - 2 * q));
+                const uint32_t so = (uint32_t)((c % QT_NF) * QT_FSLOT);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const uint32_t n = srow[r] ? (uint32_t)nv : 0u;
+                    tc::cp_async16(drow[r] + so, n ? srow[r] + k0 : F, n * 8);
+                }
+            };
+#pragma unroll 1
+            for (int c = 0; c < QT_NF; ++c) {
+                if (c < nk) issue(c);
+                tc::cp_async_commit();
+            }
+            // this thread's unit i: pair (u + 256 i) >> 3, values k = 4 kg .. 4 kg + 3 as
+            // pieces 2 kg and 2 kg + 1 of the row; lanes with kg >= 4 read the second
+            // piece first, so that the eight lanes of a phase hit distinct banks
+            const int kg = u & 7, sw = (kg >> 2) & 1;
+            for (int c = 0; c < nk; ++c) {
+                tc::cp_async_wait<QT_NF - 1>();       // this thread's copies of chunk c landed
+                __syncwarp();                         // ... and those of the warp's other lanes
+                const float4 *slot = reinterpret_cast<const float4 *>(fraw + (c % QT_NF) * QT_FSLOT);
+                LtB bv;
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const float4 *pc = slot + ((u + 256 * i) >> 3) * (QT_FROW / 16) + 2 * kg;
+                    const float4 x = pc[sw], y = pc[sw ^ 1];
+                    const float4 a = sw ? y : x, b = sw ? x : y;
+                    bv.v[i][0] = make_float2(a.x, a.y);
+                    bv.v[i][1] = make_float2(a.z, a.w);
+                    bv.v[i][2] = make_float2(b.x, b.y);
+                    bv.v[i][3] = make_float2(b.z, b.w);
+                }
+                // the accumulator of group c / QT_D - QT_NACC must be drained before chunk c's MMAs
+                while (drained <= c / QT_D - QT_NACC) drain(drained++);
+                if (c >= QT_NB) lt_spin(&sy.done[(c - QT_NB) % QT_NR], par(c - QT_NB), abort);
+                bv.store(smem + (c % QT_NB) * QT_BSTAGE, u);
+                // (the warp barrier in the arrival also orders every lane's reads of
+                // the slot before its refill below)
+                lt_warp_arrive(&sy.full[c % QT_NR], lane);
+                if (c + QT_NF < nk) issue(c + QT_NF);
+                tc::cp_async_commit();
+            }
+            tc::cp_async_wait<0>();
+        } else {
+            // F rows of this thread's two pairs, loaded one chunk ahead (two register
+            // sets, the loop unrolled by two so that they stay registers)
+            const float2 *frow[2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int pp = pair0 + ((u + 256 * i) >> 3);
+                frow[i] = nullptr;
+                if (pp < npairs) {
+                    const int b = pp / nj, j = pp % nj;
+                    frow[i] = F + ((size_t)b * nmi + mi0 + 2 * j) * N;
+                }
+            }
+            auto load = [&](LtB &bv, int c) {
+                const int k0 = 32 * c;
+                bv.load(u, [&](int p) -> const float2 * {
+                    const float2 *rr = frow[p >= 32];
+                    return rr ? rr + k0 : nullptr;
+                }, N - k0, nullptr);
+            };
+            auto body = [&](int c, LtB &cur, LtB &next) {
+                if (c >= nk) return;
+                if (c + 1 < nk) load(next, c + 1);
+                while (drained <= c / QT_D - QT_NACC) drain(drained++);
+                if (c >= QT_NB) lt_spin(&sy.done[(c - QT_NB) % QT_NR], par(c - QT_NB), abort);
+                cur.store(smem + (c % QT_NB) * QT_BSTAGE, u);
+                lt_warp_arrive(&sy.full[c % QT_NR], lane);
+            };
+            LtB b0, b1;
+            if (nk > 0) load(b0, 0);
+            for (int c = 0; c < nk; c += 2) {
+                body(c, b0, b1);
+                body(c + 1, b1, b0);
+            }
         }
         while (drained < ng) drain(drained++);
         // epilogue: TMEM lane = row t

@@ -250,10 +250,12 @@ void *run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream
             const int nj = (n - 1 - mi0) / 2 + 1;
             const int npairs = nj * p->batch;
             dim3 grid((bd.N + QG_BM - 1) / QG_BM, (npairs + QG_BN / 2 - 1) / (QG_BN / 2));
-            if (p->tc && bd.tc_quad && p->tc_split == 2)
-                k_quad_tcp<<<grid, LT_THREADS, quad_tc_smem(), st>>>(par ? bd.Qoi : bd.Qei, (const float2 *)F,
-                                                                       (float2 *)p->G, bd.N, n, mi0, nj, npairs,
-                                                                       p->d_err);
+            if (p->tc && bd.tc_quad && p->tc_split == 2) {
+                // F rows by bulk copies where every row starts on a 16-byte boundary
+                const bool fraw = bd.N % 2 == 0 && (reinterpret_cast<uintptr_t>(F) & 15) == 0;
+                (fraw ? k_quad_tcp<true> : k_quad_tcp<false>)<<<grid, LT_THREADS, quad_tc_smem(), st>>>(
+                    par ? bd.Qoi : bd.Qei, (const float2 *)F, (float2 *)p->G, bd.N, n, mi0, nj, npairs, p->d_err);
+            }
             else if (p->tc && bd.tc_quad)
                 k_quad_tc<3, 2><<<grid, TQ_THREADS, TqShape<3, 2>::SMEM, st>>>(
                     par ? bd.Qo3 : bd.Qe3, (const float2 *)F, (float2 *)p->G, bd.N, n, mi0, nj, npairs, p->d_err);
@@ -557,7 +559,8 @@ void set_smem_limits(int Mmax)
     allow_smem(k_ring_fwd_cplx<float>, f);
     allow_smem(k_ring_inv_real<float>, f);
     allow_smem(k_ring_inv_cplx<float>, f);
-    allow_smem(k_quad_tcp, quad_tc_smem());
+    allow_smem(k_quad_tcp<true>, quad_tc_smem());
+    allow_smem(k_quad_tcp<false>, quad_tc_smem());
     allow_smem(k_quad_tc<3, 2>, TqShape<3, 2>::SMEM);
     allow_smem(k_leg_synth_tc<false>, ls_synth_smem());
     allow_smem(k_leg_synth_tc<true>, ls_synth_smem());

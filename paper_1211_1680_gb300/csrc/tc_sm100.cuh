@@ -126,6 +126,17 @@ __device__ __forceinline__ void bulk_g2s(void *smem_dst, const void *gsrc, uint3
 }
 
 // One arrival (release semantics, CTA scope) on *bar.
+// 16-byte asynchronous global -> shared copy; bytes (0..16) are read from src
+// and the rest of the 16 bytes is zero-filled.  Completion is tracked per
+// thread by commit groups.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
     asm volatile(
