@@ -306,11 +306,19 @@ def run_gpu(a, rank, world, local_rank):
                 "avg_launch_ms": sd["ms"] / max(sd["timed"], 1)}
         if dom == "theta_quad":
             # DRAM bytes of one quadrature stage (two parity launches of k_quad_tcp): ncu measured
-            # 276.9 + 235.5 MB per launch at L = 1024, 64 maps (the F read and G written, 0.954 of
-            # them); the traffic grows with orders x rings x maps, i.e. L^2 x maps
-            roof["traffic"] = 2 * 512.4e6 * (a.L / 1024.0) ** 2 * a.batch / 64.0
+            # 272.7 + 230.2 MB per launch at L = 1024, 64 maps (the F read and G written); the
+            # traffic grows with orders x rings x maps, i.e. L^2 x maps
+            roof["traffic"] = 2 * 502.9e6 * (a.L / 1024.0) ** 2 * a.batch / 64.0
             roof["traffic_note"] = ("dram read+write per quadrature stage (2 launches), from one ncu capture at "
                                     "L=1024 x 64 maps scaled by L^2 x maps; avg_launch_ms is per stage as well")
+        elif dom == "leg_anal":
+            # DRAM bytes of the full-band-limit analysis launch (k_leg_anal_tc): ncu measured
+            # 720.9 + 253.1 MB at L = 1024, 64 maps (G and the recurrence tables read, f_lm
+            # written); both grow with L^2 x maps.  The stage's launches at smaller band-limits
+            # (the wavelet synthesis) move less.
+            roof["traffic"] = 974.0e6 * (a.L / 1024.0) ** 2 * a.batch / 64.0
+            roof["traffic_note"] = ("dram read+write of the full-band-limit launch, from one ncu capture at "
+                                    "L=1024 x 64 maps scaled by L^2 x maps")
     elif sd["flops"] > 0:
         # a contraction stage: FP32 (or FP64) FMA pipe; peak derived from unit counts and clock
         mhz = peaks.get("sm_max_mhz", 2070.0)
