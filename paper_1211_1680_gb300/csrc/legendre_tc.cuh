@@ -437,6 +437,15 @@ static __global__ void __launch_bounds__(LT_ANAL_THREADS, 1)
                 };
                 LtB bv;
                 bv.load<true>(u, row, N - t0, nullptr);
+                // the next ring chunk's values of this thread into L2, so that its loads
+                // (issued only one drain ahead of their use) find them there (the
+                // chunk after k is usually k + 1; a skipped one costs a wasted prefetch)
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int unit = u + 256 * i, kk = t0 + 32 + 4 * (unit & 7);
+                    const float2 *r = row(unit >> 3);
+                    if (r && kk < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(r + 32 + 4 * (unit & 7)));
+                }
                 while (drained <= cc - LT_NS) d.drain(sy, tmem, drained++);
                 bv.store(smem + s * LT_STAGE + 2 * LT_PLANE, u);
                 lt_warp_arrive(&sy.full[s], lane);
