@@ -16,10 +16,11 @@
 
 namespace s2g {
 
-// analysis: recurrence warps 0-2 (one per stage), MMA warp 3, warps 4-11 as in
-// synthesis; twelve warps leave 168 registers per thread instead of 128
-constexpr int LT_ANAL_MMA_WARP = 3, LT_ANAL_THREADS = 32 * (LT_REC_WARPS + LT_OPB_WARPS);
-constexpr int LT_ANAL_REC = LT_NS;                 // analysis: one recurrence warp per stage
+// analysis: recurrence warps 0-3 (one per operand-A stage, each issuing its
+// chunks' MMAs), warps 4-11 as in synthesis; twelve warps leave 168 registers
+// per thread instead of 128
+constexpr int LT_ANAL_THREADS = 32 * (LT_REC_WARPS + LT_OPB_WARPS);
+constexpr int LT_ANAL_REC = LT_REC_WARPS;
 
 // Branch-free float-float recurrence of one ring (the step of RecT<float>):
 // the state is zero before l_s, so the recurrence yields zeros there; at
@@ -306,12 +307,44 @@ static __global__ void __launch_bounds__(LT_THREADS, 1)
 // ---------------------------------------------------------------- analysis
 // Block: (order m, batch tile).  Degree tiles of 128 from l = m (MMA rows),
 // K = rings in chunks of 32 (chunks whose rings all have l_s beyond the degree
-// tile are skipped), columns = G columns.  Recurrence warp w (< LT_ANAL_REC)
-// fills stage w: chunks c = w mod LT_NS of the sequence; lane i owns ring
-// 32 k + i and writes column i of A (one 4-byte store per degree, conflict-free
-// in the swizzled layout).  Recurrence states of all rings stay in shared memory
-// between degree tiles; the recurrence warps meet at a named barrier at the end
-// of each degree tile before the states are read again.
+// tile are skipped), columns = G columns.  Twelve warps:
+//   recurrence warps 0-3  warp w computes the chunks c = w mod 4 of the sequence
+//                         into its own operand-A stage (lane i owns ring 32 k + i
+//                         and writes column i of A: one 4-byte store per degree
+//                         and plane, conflict-free in the swizzled layout), then
+//                         one of its threads issues and commits the chunk's MMAs
+//                         once operand B is in place.  There is no MMA warp, so a
+//                         fourth recurrence warp fits in twelve warps (168
+//                         registers per thread; thirteen would leave 128)
+//   warps 4-11            operand B (G) in a ring of two stages, and the drains
+//                         of the accumulators (three TMEM buffers) into FP32
+//                         registers; epilogue per degree tile
+// Barriers per chunk c: full[c % LA_NR] (the eight operand-B warps), done[c %
+// LA_NR] (the MMAs completed: A stage c % 4 and B stage c % 2 are free, the
+// accumulator can be drained), tempty[c % 3] (drained).  MMAs of different
+// chunks may be issued out of order (by different warps); every wait names its
+// chunk, and no waiter can fall LA_NR chunks behind a barrier.
+// Recurrence states of all rings stay in shared memory between degree tiles;
+// the recurrence warps meet at a named barrier at the end of each degree tile
+// before the states are read again.
+constexpr int LA_NA = LT_ANAL_REC, LA_NB = 2, LA_NACC = 3, LA_NR = 12;
+constexpr int LA_STAGE = 2 * LT_PLANE;                // one operand: hi, lo
+constexpr int LA_B_OFF = LA_NA * LA_STAGE;
+constexpr int LA_SYNC_OFF = LA_B_OFF + LA_NB * LA_STAGE;
+struct LaSync {
+    uint64_t full[LA_NR], done[LA_NR], tempty[LA_NACC];
+    uint32_t tslot;
+    int abort;
+};
+constexpr int LA_SYNC_BYTES = 256;
+static_assert(sizeof(LaSync) <= LA_SYNC_BYTES, "sync block");
+static_assert(LA_NR % LA_NA == 0 && LA_NR % LA_NB == 0 && LA_NR % LA_NACC == 0, "barrier ring");
+__host__ __device__ constexpr size_t la_anal_smem(int N)
+{
+    return (size_t)LA_SYNC_OFF + LA_SYNC_BYTES + (size_t)N * sizeof(float4) + (size_t)((N + 31) / 32) * sizeof(int) +
+           1024;
+}
+
 template <bool CPLX>
 static __global__ void __launch_bounds__(LT_ANAL_THREADS, 1)
     k_leg_anal_tc(const float2 *__restrict__ Gin, int N, const float *__restrict__ kfac, float scale, int accumulate,
@@ -321,14 +354,16 @@ static __global__ void __launch_bounds__(LT_ANAL_THREADS, 1)
     constexpr int BT = Cols::BT;
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
     unsigned char *smem = lt_align(smem_dyn);
-    LtSync &sy = *reinterpret_cast<LtSync *>(smem + LT_NS * LT_STAGE);
-    float4 *st = reinterpret_cast<float4 *>(smem + LT_NS * LT_STAGE + LT_SYNC_BYTES);
+    LaSync &sy = *reinterpret_cast<LaSync *>(smem + LA_SYNC_OFF);
+    float4 *st = reinterpret_cast<float4 *>(smem + LA_SYNC_OFF + LA_SYNC_BYTES);
     int *gmin = reinterpret_cast<int *>(st + N);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m = blockIdx.x, b0 = blockIdx.y * BT;
     const bool two = CPLX && m > 0;
     const int nkr = (N + 31) / 32;
     const int ndt = (N - m + 127) / 128;
+    volatile int *abort = &sy.abort;
+    auto par = [](int c) -> uint32_t { return (uint32_t)((c / LA_NR) & 1); };
 
     for (int k = warp; k < nkr; k += LT_ANAL_THREADS / 32) {
         const int t = 32 * k + lane;
@@ -337,89 +372,139 @@ static __global__ void __launch_bounds__(LT_ANAL_THREADS, 1)
         for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
         if (lane == 0) gmin[k] = v;
     }
-    lt_setup(sy, warp, tid, 1 + LT_OPB_WARPS, LT_ANAL_MMA_WARP);
-    if (warp == 0) {
-        // ring chunk k is processed in the degree tiles dt >= (gmin[k] - m) / 128
-        // (l_s >= m always), none when gmin[k] = N
-        int n = 0;
-        for (int k = lane; k < nkr; k += 32)
-            if (gmin[k] < N) n += ndt - (gmin[k] - m) / 128;
+    if (tid == 0) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-        if (lane == 0) sy.nchunks = n;
+        for (int i = 0; i < LA_NR; ++i) {
+            tc::mbar_init(&sy.full[i], LT_OPB_WARPS);
+            tc::mbar_init(&sy.done[i], 1);
+        }
+#pragma unroll
+        for (int i = 0; i < LA_NACC; ++i) tc::mbar_init(&sy.tempty[i], LT_OPB_WARPS);
+        sy.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (warp == 0) tc::tmem_alloc(&sy.tslot, LT_TMEM_COLS);
+    tc::fence_before();
     __syncthreads();
+    tc::fence_after();
     const uint32_t tmem = sy.tslot;
 
-    if (warp < LT_ANAL_REC) {
-        // ------------------------------------------------ recurrence (A = lambda[degree][ring])
-        {
-            const float4 *cm = tab.coef + (size_t)m * tab.ldc;
-            int c = 0;
-            for (int dt = 0; dt < ndt; ++dt) {
-                const int l0 = m + 128 * dt;
-                const int lend = min(N, l0 + 128);
-                // lane j holds the coefficients of degrees l0 + 32 i + j, i = 0..3
-                const float4 cf0 = lt_coef_load(cm, l0 + lane, lend), cf1 = lt_coef_load(cm, l0 + 32 + lane, lend);
-                const float4 cf2 = lt_coef_load(cm, l0 + 64 + lane, lend), cf3 = lt_coef_load(cm, l0 + 96 + lane, lend);
-                for (int k = 0; k < nkr; ++k) {
-                    if (gmin[k] >= lend) continue;
-                    const int cc = c++;
-                    if (cc % LT_NS != warp) continue;
-                    const int s = warp;
-                    // the ring's tables are loaded before the wait for the stage, so that
-                    // their latency overlaps it
-                    const int t = 32 * k + lane;
-                    const bool own = t < N;
-                    LtRec rec;
-                    rec.init(own, tab.ring + t, tab.seed + (size_t)m * N + t, tab.ls + (size_t)m * N + t);
-                    if (cc >= LT_NS) lt_wait(&sy.empty[s], ((cc / LT_NS) - 1) & 1, &sy.abort);
-                    unsigned char *A = smem + s * LT_STAGE;
-                    if (own && l0 > rec.ls) {
-                        const float4 q = st[t];
-                        rec.p0.h = q.x;
-                        rec.p0.l = q.y;
-                        rec.p1.h = q.z;
-                        rec.p1.l = q.w;
-                    }
+    if (warp < LA_NA) {
+        // ------------------------------------------------ recurrence (A = lambda[degree][ring]) and MMA issue
+        constexpr uint32_t IDESC = tc::idesc_tf32(128, 128);
+        const float4 *cm = tab.coef + (size_t)m * tab.ldc;
+        unsigned char *A = smem + warp * LA_STAGE;
+        const uint32_t abase = tc::smem_addr(A);
+        int c = 0, last = -1;
+        for (int dt = 0; dt < ndt; ++dt) {
+            const int l0 = m + 128 * dt;
+            const int lend = min(N, l0 + 128);
+            // lane j holds the coefficients of degrees l0 + 32 i + j, i = 0..3
+            const float4 cf0 = lt_coef_load(cm, l0 + lane, lend), cf1 = lt_coef_load(cm, l0 + 32 + lane, lend);
+            const float4 cf2 = lt_coef_load(cm, l0 + 64 + lane, lend), cf3 = lt_coef_load(cm, l0 + 96 + lane, lend);
+            for (int k = 0; k < nkr; ++k) {
+                if (gmin[k] >= lend) continue;
+                const int cc = c++;
+                if (cc % LA_NA != warp) continue;
+                // the ring's tables are loaded before the wait for the stage, so that
+                // their latency overlaps it
+                const int t = 32 * k + lane;
+                const bool own = t < N;
+                LtRec rec;
+                rec.init(own, tab.ring + t, tab.seed + (size_t)m * N + t, tab.ls + (size_t)m * N + t);
+                if (cc >= LA_NA) lt_wait(&sy.done[(cc - LA_NA) % LA_NR], par(cc - LA_NA), abort);
+                if (own && l0 > rec.ls) {
+                    const float4 q = st[t];
+                    rec.p0.h = q.x;
+                    rec.p0.l = q.y;
+                    rec.p1.h = q.z;
+                    rec.p1.l = q.w;
+                }
 #pragma unroll 1
-                    for (int i = 0; i < 4; ++i) {
-                        const float4 cf = i == 0 ? cf0 : i == 1 ? cf1 : i == 2 ? cf2 : cf3;
-                        const int lb = l0 + 32 * i;
-                        if (__any_sync(0xffffffffu, rec.starts_in(lb, 32))) {   // a chain of this warp starts here
+                for (int i = 0; i < 4; ++i) {
+                    const float4 cf = i == 0 ? cf0 : i == 1 ? cf1 : i == 2 ? cf2 : cf3;
+                    const int lb = l0 + 32 * i;
+                    if (__any_sync(0xffffffffu, rec.starts_in(lb, 32))) {   // a chain of this warp starts here
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                float hi, lo;
-                                tc::split_tf32(rec.step(lt_coef(cf, j), lb + j), hi, lo);
-                                const uint32_t o = tc::sw128_off(32 * i + j, lane);
-                                *reinterpret_cast<float *>(A + o) = hi;
-                                *reinterpret_cast<float *>(A + LT_PLANE + o) = lo;
-                            }
-                        } else {
+                        for (int j = 0; j < 32; ++j) {
+                            float hi, lo;
+                            tc::split_tf32(rec.step(lt_coef(cf, j), lb + j), hi, lo);
+                            const uint32_t o = tc::sw128_off(32 * i + j, lane);
+                            *reinterpret_cast<float *>(A + o) = hi;
+                            *reinterpret_cast<float *>(A + LT_PLANE + o) = lo;
+                        }
+                    } else {
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                float hi, lo;
-                                tc::split_tf32(rec.step_plain(lt_coef(cf, j)), hi, lo);
-                                const uint32_t o = tc::sw128_off(32 * i + j, lane);
-                                *reinterpret_cast<float *>(A + o) = hi;
-                                *reinterpret_cast<float *>(A + LT_PLANE + o) = lo;
-                            }
+                        for (int j = 0; j < 32; ++j) {
+                            float hi, lo;
+                            tc::split_tf32(rec.step_plain(lt_coef(cf, j)), hi, lo);
+                            const uint32_t o = tc::sw128_off(32 * i + j, lane);
+                            *reinterpret_cast<float *>(A + o) = hi;
+                            *reinterpret_cast<float *>(A + LT_PLANE + o) = lo;
                         }
                     }
-                    if (own && lend - 1 >= rec.ls) st[t] = make_float4(rec.p0.h, rec.p0.l, rec.p1.h, rec.p1.l);
-                    lt_warp_arrive(&sy.full[s], lane);
                 }
-                asm volatile("bar.sync 1, %0;" ::"n"(32 * LT_ANAL_REC) : "memory");
+                if (own && lend - 1 >= rec.ls) st[t] = make_float4(rec.p0.h, rec.p0.l, rec.p1.h, rec.p1.l);
+                // operand A written and visible to the tensor core; one thread issues
+                // the chunk's MMAs once operand B is stored and the accumulator drained
+                tc::fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) {
+                    bool ok = lt_wait(&sy.full[cc % LA_NR], par(cc), abort);
+                    if (cc >= LA_NACC)
+                        ok = lt_wait(&sy.tempty[cc % LA_NACC], ((cc / LA_NACC) - 1) & 1, abort) && ok;
+                    tc::fence_after();
+                    if (ok) {
+                        const uint32_t bbase = tc::smem_addr(smem + LA_B_OFF + (cc % LA_NB) * LA_STAGE);
+                        const uint32_t acc = tmem + (uint32_t)(128 * (cc % LA_NACC));
+#pragma unroll
+                        for (int ks = 0; ks < 4; ++ks) {
+                            const uint32_t ko = ks * 32;
+                            const uint64_t a0 = tc::smem_desc_sw128(abase + ko);
+                            const uint64_t a1 = tc::smem_desc_sw128(abase + LT_PLANE + ko);
+                            const uint64_t b0d = tc::smem_desc_sw128(bbase + ko);
+                            const uint64_t b1d = tc::smem_desc_sw128(bbase + LT_PLANE + ko);
+                            tc::mma_tf32(acc, a0, b1d, IDESC, ks > 0 ? 1u : 0u);
+                            tc::mma_tf32(acc, a1, b0d, IDESC, 1u);
+                            tc::mma_tf32(acc, a0, b0d, IDESC, 1u);
+                        }
+                    }
+                    tc::mma_commit(&sy.done[cc % LA_NR]);
+                }
+                __syncwarp();
+                last = cc;
             }
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * LA_NA) : "memory");
         }
-    } else if (warp >= LT_REC_WARPS) {
+        // no MMA of this warp in flight when the block ends (its last commit
+        // covers all of them; bounded)
+        if (lane == 0 && last >= 0) tc::mbar_wait(&sy.done[last % LA_NR], par(last), 1u << 22);
+    } else {
         // ------------------------------------------------ operand B (G) and drains
         const int u = tid - 32 * LT_REC_WARPS;
         const int nmi_src = CPLX ? 2 * N - 1 : N;
         const int nmi_dst = CPLX ? 2 * Ldst - 1 : Ldst;
         const float sgn_m = (m & 1) ? -1.f : 1.f;
-        LtDrain d;
-        d.init(warp);
+        float sum[64];
+#pragma unroll
+        for (int i = 0; i < 64; ++i) sum[i] = 0.f;
+        const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+        const int h = (warp - LT_REC_WARPS) >> 2;
+        auto drain = [&](int c) {                     // accumulator c % LA_NACC into sum
+            lt_wait(&sy.done[c % LA_NR], par(c), abort);
+            tc::fence_after();
+            const uint32_t acc = tmem + lane_addr + (uint32_t)(128 * (c % LA_NACC) + 64 * h);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float v[16];
+                tc::tmem_ld16(acc + 16 * q, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) sum[16 * q + i] += v[i];
+            }
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&sy.tempty[c % LA_NACC]);
+        };
         int c = 0, drained = 0;
         for (int dt = 0; dt < ndt; ++dt) {
             const int l0 = m + 128 * dt;
@@ -427,7 +512,6 @@ static __global__ void __launch_bounds__(LT_ANAL_THREADS, 1)
             for (int k = 0; k < nkr; ++k) {
                 if (gmin[k] >= lend) continue;
                 const int cc = c++;
-                const int s = cc % LT_NS;
                 const int t0 = 32 * k;
                 auto row = [&](int p) -> const float2 * {
                     const int sg = p / BT, b = p % BT;
@@ -446,24 +530,25 @@ static __global__ void __launch_bounds__(LT_ANAL_THREADS, 1)
                     const float2 *r = row(unit >> 3);
                     if (r && kk < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(r + 32 + 4 * (unit & 7)));
                 }
-                while (drained <= cc - LT_NS) d.drain(sy, tmem, drained++);
-                bv.store(smem + s * LT_STAGE + 2 * LT_PLANE, u);
-                lt_warp_arrive(&sy.full[s], lane);
+                while (drained <= cc - LA_NACC) drain(drained++);
+                if (cc >= LA_NB) lt_wait(&sy.done[(cc - LA_NB) % LA_NR], par(cc - LA_NB), abort);
+                bv.store(smem + LA_B_OFF + (cc % LA_NB) * LA_STAGE, u);
+                lt_warp_arrive(&sy.full[cc % LA_NR], lane);
             }
-            while (drained < c) d.drain(sy, tmem, drained++);
+            while (drained < c) drain(drained++);
             // epilogue of the degree tile: TMEM lane = degree
             const int l = l0 + 32 * (warp & 3) + lane;
             if (l < lend && !sy.abort) {
                 const float f = scale * (kfac ? kfac[l] : 1.f);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const int p = 32 * d.h + j;
+                    const int p = 32 * h + j;
                     const int sg = p / BT, b = p % BT;
                     if (b0 + b < B && (sg == 0 || two)) {
                         const float fs = sg == 1 ? f * sgn_m : f;
                         const int mi = sg == 0 ? (CPLX ? m + Ldst - 1 : m) : (-m + Ldst - 1);
                         float2 *o = dst + ((size_t)(b0 + b) * nmi_dst + mi) * Ldst + l;
-                        float2 v = make_float2(d.sum[2 * j] * fs, d.sum[2 * j + 1] * fs);
+                        float2 v = make_float2(sum[2 * j] * fs, sum[2 * j + 1] * fs);
                         if (accumulate) {
                             const float2 w = *o;
                             v.x += w.x;
@@ -475,12 +560,13 @@ static __global__ void __launch_bounds__(LT_ANAL_THREADS, 1)
                 }
             }
 #pragma unroll
-            for (int i = 0; i < 64; ++i) d.sum[i] = 0.f;
+            for (int i = 0; i < 64; ++i) sum[i] = 0.f;
         }
-    } else if (warp == LT_ANAL_MMA_WARP) {
-        if (lane == 0) lt_issue(sy, smem, tmem, sy.nchunks);
     }
-    lt_teardown(sy, warp, tid, tmem, err, LT_ANAL_MMA_WARP);
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_free(tmem, LT_TMEM_COLS);
+    if (tid == 0 && sy.abort) atomicExch(err, 1);
 }
 
 }  // namespace s2g

@@ -366,11 +366,11 @@ int run_anal(const s2let_plan *p, const BandDev &bd, const void *G, const void *
         const size_t sm = anal_gemm_smem(bd.N);
         const LegTab<float> tab = leg_tab<float>(p, bd);
         if (p->tc && bd.tc_anal && p->cplx)
-            k_leg_anal_tc<true><<<grid, LT_ANAL_THREADS, lt_anal_smem(bd.N), st>>>(
+            k_leg_anal_tc<true><<<grid, LT_ANAL_THREADS, la_anal_smem(bd.N), st>>>(
                 (const float2 *)G, bd.N, (const float *)kfac, (float)scale, acc, (float2 *)dst, p->L, p->batch, tab,
                 p->d_err);
         else if (p->tc && bd.tc_anal)
-            k_leg_anal_tc<false><<<grid, LT_ANAL_THREADS, lt_anal_smem(bd.N), st>>>(
+            k_leg_anal_tc<false><<<grid, LT_ANAL_THREADS, la_anal_smem(bd.N), st>>>(
                 (const float2 *)G, bd.N, (const float *)kfac, (float)scale, acc, (float2 *)dst, p->L, p->batch, tab,
                 p->d_err);
         else if (p->cplx)
@@ -564,8 +564,8 @@ void set_smem_limits(int Mmax)
     allow_smem(k_quad_tc<3, 2>, TqShape<3, 2>::SMEM);
     allow_smem(k_leg_synth_tc<false>, ls_synth_smem());
     allow_smem(k_leg_synth_tc<true>, ls_synth_smem());
-    allow_smem(k_leg_anal_tc<false>, lt_anal_smem(kMaxL));
-    allow_smem(k_leg_anal_tc<true>, lt_anal_smem(kMaxL));
+    allow_smem(k_leg_anal_tc<false>, la_anal_smem(kMaxL));
+    allow_smem(k_leg_anal_tc<true>, la_anal_smem(kMaxL));
     allow_smem(k_leg_anal_gemm<false>, anal_gemm_smem(kMaxL));
     allow_smem(k_leg_anal_gemm<true>, anal_gemm_smem(kMaxL));
     allow_smem(k_theta_quad<double, double, 16>, d);

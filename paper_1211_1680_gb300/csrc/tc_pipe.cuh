@@ -1,22 +1,9 @@
-// Warp-specialised tcgen05 pipeline shared by the tensor-core contraction
-// kernels (split-TF32 products, see tc_kernels.cuh for the split scheme).
-// Each 128 x 128 x 32 chunk is the sum of the MMAs hi*lo + lo*hi + hi*hi
-// accumulated in its own TMEM buffer, then added into FP32 registers.
-//
-// Warp roles, synchronised by mbarriers over LT_NS shared-memory stages:
-//   producer warps  write operand A of a stage (recurrence values, or copies
-//                   of a pre-split matrix)
-//   warps 4-11      operand B (the data side) of a stage, and drain the TMEM
-//                   accumulator of each finished chunk into registers; epilogue
-//   MMA warp        one thread issues the MMAs and commits them
-// Per stage: A hi, A lo, B hi, B lo, each a 128 x 32 FP32 tile in the K-major
-// 128-byte-swizzled layout (16 KB).  Barriers per stage s:
-//   full[s]   operands written: one arrival per writing warp (the producer
-//             warps that wrote A and the eight operand-B warps), after each
-//             lane's proxy fence and a warp barrier
-//   empty[s]  the chunk's MMAs have completed (tcgen05.commit): stage s free and
-//             TMEM buffer s holds the chunk's sum
-//   tempty[s] TMEM buffer s drained (one arrival per operand-B warp)
+// Pieces shared by the warp-specialised tcgen05 kernels (split-TF32 products,
+// see tc_kernels.cuh for the split scheme): block shape constants, bounded
+// mbarrier waits, the warp arrival after operand stores, and the operand-B
+// loader/splitter.  Each 128 x 128 x 32 chunk of those kernels is the sum of
+// the MMAs hi*lo + lo*hi + hi*hi; operands are 128 x 32 FP32 tiles in the
+// K-major 128-byte-swizzled layout (16 KB per plane).
 // Every wait is bounded; a wait that runs out sets a shared abort flag, after
 // which all roles run to the end without waiting and the error word is set.
 #pragma once
@@ -26,30 +13,12 @@
 
 namespace s2g {
 
+// producer warps 0-3 (one per TMEM lane quadrant), operand-B / drain warps 4-11,
+// and (in the kernels that have one) an MMA warp 12
 constexpr int LT_REC_WARPS = 4, LT_OPB_WARPS = 8, LT_MMA_WARP = LT_REC_WARPS + LT_OPB_WARPS;
 constexpr int LT_THREADS = 32 * (LT_MMA_WARP + 1);
-constexpr int LT_NS = 3;
 constexpr int LT_PLANE = TQ_TILE;                  // 128 x 32 FP32
-constexpr int LT_STAGE = 4 * LT_PLANE;
-constexpr int LT_TMEM_COLS = 512;                  // LT_NS accumulators of 128 columns
-
-struct LtSync {
-    uint64_t full[LT_NS], empty[LT_NS], tempty[LT_NS], done;
-    uint32_t tslot;
-    int abort;
-    int lmin;
-    int nchunks;
-};
-constexpr int LT_SYNC_BYTES = 128;
-static_assert(sizeof(LtSync) <= LT_SYNC_BYTES, "sync block");
-
-// dynamic shared memory: stages, sync block, 1024-byte alignment slack, and
-// (analysis) recurrence states and per-ring-chunk minima of l_s for N rings
-__host__ __device__ constexpr size_t lt_synth_smem() { return (size_t)LT_NS * LT_STAGE + LT_SYNC_BYTES + 1024; }
-__host__ __device__ constexpr size_t lt_anal_smem(int N)
-{
-    return lt_synth_smem() + (size_t)N * sizeof(float4) + (size_t)((N + 31) / 32) * sizeof(int);
-}
+constexpr int LT_TMEM_COLS = 512;                  // TMEM columns per block
 
 __device__ __forceinline__ bool lt_wait(uint64_t *bar, uint32_t parity, volatile int *abort)
 {
@@ -97,92 +66,6 @@ __device__ __forceinline__ unsigned char *lt_align(unsigned char *p)
 {
     return p + ((1024 - (tc::smem_addr(p) & 1023)) & 1023);
 }
-
-// Barrier set-up (thread 0) and TMEM allocation (MMA warp); ends with a CTA
-// barrier.  full_arrivals: arrivals on full[] per chunk (one per warp that
-// writes an operand, one per bulk-copy issue); the eight drain warps arrive on
-// tempty[].
-__device__ __forceinline__ void lt_setup(LtSync &sy, int warp, int tid, int full_arrivals, int mma_warp)
-{
-    if (tid == 0) {
-#pragma unroll
-        for (int i = 0; i < LT_NS; ++i) {
-            tc::mbar_init(&sy.full[i], full_arrivals);
-            tc::mbar_init(&sy.empty[i], 1);
-            tc::mbar_init(&sy.tempty[i], LT_OPB_WARPS);
-        }
-        tc::mbar_init(&sy.done, 1);
-        sy.abort = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == mma_warp) tc::tmem_alloc(&sy.tslot, LT_TMEM_COLS);
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-}
-
-// MMA issue loop (one thread): chunk c uses stage and TMEM buffer c % LT_NS.
-__device__ __forceinline__ void lt_issue(LtSync &sy, unsigned char *smem, uint32_t tmem, int nchunks)
-{
-    constexpr uint32_t IDESC = tc::idesc_tf32(128, 128);
-    volatile int *abort = &sy.abort;
-    for (int c = 0; c < nchunks; ++c) {
-        const int s = c % LT_NS;
-        bool ok = lt_wait(&sy.full[s], (c / LT_NS) & 1, abort);
-        if (c >= LT_NS) ok = lt_wait(&sy.tempty[s], ((c / LT_NS) - 1) & 1, abort) && ok;
-        tc::fence_after();
-        if (ok) {
-            const uint32_t base = tc::smem_addr(smem + s * LT_STAGE);
-            const uint32_t acc = tmem + (uint32_t)(s * 128);
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-                const uint32_t ko = ks * 32;
-                const uint64_t a0 = tc::smem_desc_sw128(base + ko), a1 = tc::smem_desc_sw128(base + LT_PLANE + ko);
-                const uint64_t b0 = tc::smem_desc_sw128(base + 2 * LT_PLANE + ko);
-                const uint64_t b1 = tc::smem_desc_sw128(base + 3 * LT_PLANE + ko);
-                tc::mma_tf32(acc, a0, b1, IDESC, ks > 0 ? 1u : 0u);
-                tc::mma_tf32(acc, a1, b0, IDESC, 1u);
-                tc::mma_tf32(acc, a0, b0, IDESC, 1u);
-            }
-        }
-        tc::mma_commit(&sy.empty[s]);
-    }
-    tc::mma_commit(&sy.done);
-    tc::mbar_wait(&sy.done, 0, 1u << 22);   // no MMA in flight when TMEM is released
-}
-
-// Operand-B / drain thread state: TMEM lane quadrant q = warp % 4, column half h.
-struct LtDrain {
-    float sum[64];
-    uint32_t lane_addr;
-    int h;
-    __device__ __forceinline__ void init(int warp)
-    {
-        lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
-        h = (warp - LT_REC_WARPS) >> 2;
-#pragma unroll
-        for (int i = 0; i < 64; ++i) sum[i] = 0.f;
-    }
-    // add chunk c's accumulator (64 columns of this thread's lane) into sum; NS
-    // stages (TMEM buffer c % NS at column 128 (c % NS))
-    template <int NS = LT_NS> __device__ __forceinline__ void drain(LtSync &sy, uint32_t tmem, int c)
-    {
-        const int s = c % NS;
-        lt_wait(&sy.empty[s], (c / NS) & 1, &sy.abort);
-        tc::fence_after();
-        const uint32_t acc = tmem + lane_addr + (uint32_t)(s * 128 + 64 * h);
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            float v[16];
-            tc::tmem_ld16(acc + 16 * g, v);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) sum[16 * g + i] += v[i];
-        }
-        tc::fence_before();
-        __syncwarp();
-        if ((threadIdx.x & 31) == 0) tc::mbar_arrive(&sy.tempty[s]);
-    }
-};
 
 // Operand B of a chunk: 64 column pairs (sign s, map b) x 32 K values read
 // from float2 rows (re, im), times an optional per-K factor, split into TF32
@@ -247,13 +130,5 @@ struct LtB {
         }
     }
 };
-
-__device__ __forceinline__ void lt_teardown(LtSync &sy, int warp, int tid, uint32_t tmem, int *err, int mma_warp)
-{
-    tc::fence_before();
-    __syncthreads();
-    if (warp == mma_warp) tc::tmem_free(tmem, LT_TMEM_COLS);
-    if (tid == 0 && sy.abort) atomicExch(err, 1);
-}
 
 }  // namespace s2g
