@@ -313,10 +313,10 @@ def run_gpu(a, rank, world, local_rank):
                                     "L=1024 x 64 maps scaled by L^2 x maps; avg_launch_ms is per stage as well")
         elif dom == "leg_anal":
             # DRAM bytes of the full-band-limit analysis launch (k_leg_anal_tc): ncu measured
-            # 720.9 + 253.1 MB at L = 1024, 64 maps (G and the recurrence tables read, f_lm
+            # 772.0 + 255.5 MB at L = 1024, 64 maps (G and the recurrence tables read, f_lm
             # written); both grow with L^2 x maps.  The stage's launches at smaller band-limits
             # (the wavelet synthesis) move less.
-            roof["traffic"] = 974.0e6 * (a.L / 1024.0) ** 2 * a.batch / 64.0
+            roof["traffic"] = 1027.5e6 * (a.L / 1024.0) ** 2 * a.batch / 64.0
             roof["traffic_note"] = ("dram read+write of the full-band-limit launch, from one ncu capture at "
                                     "L=1024 x 64 maps scaled by L^2 x maps")
     elif sd["flops"] > 0:
