@@ -57,10 +57,11 @@ extern "C" {
                                     recurrence, FP64 seeds; theta quadrature as a
                                     dense FP32 product with its matrix built in
                                     FP64                                       */
-#define S2LET_PREC_TF32X3 0x20   /* as FP32, with the dense quadrature product on
-                                    the tensor cores (tcgen05): operands split in
-                                    TF32 hi + lo, 3 MMAs per product, per-chunk
-                                    TMEM sums added in FP32 registers          */
+#define S2LET_PREC_TF32X3 0x20   /* as FP32, with the dense quadrature product and
+                                    the Legendre contractions on the tensor cores
+                                    (tcgen05): operands split in TF32 hi + lo, 3
+                                    MMAs per product, TMEM partial sums over at
+                                    most 128 K values added in FP32 registers  */
 #define S2LET_PREC_MASK 0xf0
 #define S2LET_QUAD_FFT64 0x100   /* FP32 plans only: theta quadrature by FP64 FFTs
                                     instead of the dense FP32 product          */
