@@ -4,6 +4,7 @@ on MW-sampled spheres, one step = one round trip of a batch of real maps at
 L = 2048, B = 2, J_min = 2, multiresolution (64 maps per GPU).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+                  [--L L --B B --J-min J0 --full-res]   (other workloads)
 
 Prints one JSON line (rank 0).  Inputs are seeded synthetic maps: Gaussian
 f_lm with C_l = 1/(l(l+1)), turned into maps by the library's inverse
@@ -53,6 +54,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--B", type=int, default=2)
     ap.add_argument("--J-min", type=int, default=2)
+    ap.add_argument("--full-res", action="store_true",
+                    help="every wavelet and scaling map at L (the full-resolution transform) instead of the "
+                         "multiresolution band-limits min(L, B^(j+1))")
     ap.add_argument("--fp64-batch", type=int, default=8)
     ap.add_argument("--cpu-orders", type=int, default=128)
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -69,9 +73,10 @@ def parse():
 
 
 def config(a):
-    return {"workload": "real maps, L=%d, B=%d, J_min=%d, multiresolution, %d maps per GPU, f_lm ~ C_l=1/(l(l+1))"
-                        % (a.L, a.B, a.J_min, a.batch),
-            "L": a.L, "B": a.B, "J_min": a.J_min, "maps_per_gpu": a.batch, "multires": True, "signal": "real",
+    return {"workload": "real maps, L=%d, B=%d, J_min=%d, %s, %d maps per GPU, f_lm ~ C_l=1/(l(l+1))"
+                        % (a.L, a.B, a.J_min, "full resolution" if a.full_res else "multiresolution", a.batch),
+            "L": a.L, "B": a.B, "J_min": a.J_min, "maps_per_gpu": a.batch, "multires": not a.full_res,
+            "signal": "real",
             "precision": a.precision + ("+quad_fft64" if a.quad_fft64 else "") + ("+split3" if a.tc_split3 else ""),
             "l2": "inputs larger than L2 (map batch %.2f GB)" % (a.batch * a.L * (2 * a.L - 1)
                                                                    * (8 if a.precision == "fp64" else 4) / 1e9)}
@@ -139,8 +144,8 @@ def oracle_sample_step(f, a, orders):
     full workload size, restricted to the given orders m (both transforms act
     on each order separately)."""
     import oracle.wavelet as ow
-    fw, fs = ow.analysis(f, a.L, a.B, a.J_min, True, False, orders=orders)
-    ow.synthesis(fw, fs, a.L, a.B, a.J_min, True, False, orders=orders)
+    fw, fs = ow.analysis(f, a.L, a.B, a.J_min, not a.full_res, False, orders=orders)
+    ow.synthesis(fw, fs, a.L, a.B, a.J_min, not a.full_res, False, orders=orders)
 
 
 def oracle_input(a, seed):
@@ -220,17 +225,22 @@ def check_errors(plan, x, fw, fs, out, flm, a):
                                                zip(plan.scales, psi, views)]
     l_of = np.repeat(np.arange(a.L), 2 * np.arange(a.L) + 1)
     norm = np.sqrt(4 * np.pi / (2 * l_of + 1))
+    xmax = x[0].detach().double().abs().max().item()
     for name, n, kern, v in maps:
         wlm = (norm * flm * kern[l_of])[:n * n]
         rings = sorted({0, 1, n // 3, n // 2, n - 2, n - 1} & set(range(n)))
         ref = osht.inverse_at(wlm, n, rings, np.arange(2 * n - 1)).real
         got = v[0].detach().double().cpu().numpy()[rings]
-        full = v[0].detach().double().abs().max().item()
+        # a scale whose band holds no power of the input (C_0 = C_1 = 0 leaves the
+        # scaling map and scale 0 of J_min = 0 exactly zero) has no scale of its own:
+        # its rounding residue is measured against the input map instead
+        full = v[0].detach().double().abs().max().item() if np.any(wlm) else xmax
         res[name] = float(np.max(np.abs(got - ref)) / max(full, 1e-300))
     rec = float(((out[0] - x[0]).abs().max() / x[0].abs().max()).item())
     return {"max_rel_err_by_scale": res, "max_rel_err": max(res.values()), "round_trip_rel_err": rec,
             "check": "map 0; rings {0,1,N/3,N/2,N-2,N-1} of every scale against the oracle's direct sum; "
-                     "error normalised by the scale map's max"}
+                     "error normalised by the scale map's max (by the input map's max for a scale whose "
+                     "band holds no input power)"}
 
 
 def run_gpu(a, rank, world, local_rank):
@@ -244,7 +254,7 @@ def run_gpu(a, rank, world, local_rank):
         import torch.distributed as dist
     seeds = [3000 + rank * a.batch + i for i in range(a.batch)]
     flm = inputs.random_flm_batch(a.L, seeds, real=True, kind="cl")
-    plan = Plan(a.L, a.B, a.J_min, batch=a.batch, real=True, multires=True, precision=a.precision,
+    plan = Plan(a.L, a.B, a.J_min, batch=a.batch, real=True, multires=not a.full_res, precision=a.precision,
                 quad_fft64=a.quad_fft64, tc_split3=a.tc_split3)
     flm_d = torch.from_numpy(np.stack([flm.real, flm.imag], -1)).to(device="cuda", dtype=plan.dtype).contiguous()
     x = plan.sht_inverse(flm_d)
@@ -396,7 +406,7 @@ def run_gpu(a, rank, world, local_rank):
     if rank == 0 and not a.skip_fp64 and a.precision != "fp64":
         del fw, fs, out
         nb = a.fp64_batch
-        p64 = Plan(a.L, a.B, a.J_min, batch=nb, real=True, multires=True, precision="fp64")
+        p64 = Plan(a.L, a.B, a.J_min, batch=nb, real=True, multires=not a.full_res, precision="fp64")
         f64 = torch.from_numpy(np.stack([flm[:nb].real, flm[:nb].imag], -1)).cuda().contiguous()
         x64 = p64.sht_inverse(f64)
         w64, s64 = p64.empty_wavelets()
