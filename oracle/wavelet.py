@@ -32,36 +32,49 @@ def _norm(N):
     return np.sqrt(4.0 * math.pi / (2.0 * l + 1.0))
 
 
-def tables(L, B, J0):
-    """(Phi_l0, [Psi^j_l0 for j = J0..J]) for l < L."""
+def tables(L, B, J0, kernel="sd"):
+    """(Phi_l0, [Psi^j_l0 for j = J0..J]) for l < L, of the generating-function
+    family `kernel` ("sd" or "bspline")."""
     J = kernels.check_params(L, B, J0)
+    if kernel == "bspline":
+        return (kernels.phi_l0_bspline(L, B, J0, J),
+                [kernels.psi_l0_bspline(L, B, j, J) for j in range(J0, J + 1)])
+    if kernel != "sd":
+        raise ValueError("kernel must be 'sd' or 'bspline'")
     phi = kernels.phi_l0(L, B, J0)
     psi = [kernels.psi_l0(L, B, j) for j in range(J0, J + 1)]
     return phi, psi
+
+
+def bandlimits(L, B, J0, multires, kernel="sd"):
+    """Band-limits of the scaling map and of scales J0..J for the family."""
+    if kernel == "bspline":
+        return kernels.bandlimits_bspline(L, B, J0, multires)
+    return kernels.bandlimits(L, B, J0, multires)
 
 
 def _expand(per_l, N):
     return np.asarray(per_l)[_ell_index(N)]
 
 
-def analysis_lm(flm, L, B, J0, multires=True):
+def analysis_lm(flm, L, B, J0, multires=True, kernel="sd"):
     """Harmonic coefficients of the scaling map and wavelet maps, each truncated
     at its band-limit (Eqs. wav2, wav4)."""
-    phi, psi = tables(L, B, J0)
-    n_scal, n_wav = kernels.bandlimits(L, B, J0, multires)
+    phi, psi = tables(L, B, J0, kernel)
+    n_scal, n_wav = bandlimits(L, B, J0, multires, kernel)
     c = _norm(L) * flm[:L * L]
     scal = (c * np.conj(_expand(phi, L)))[:n_scal * n_scal]
     wav = [(c * np.conj(_expand(p, L)))[:n * n] for p, n in zip(psi, n_wav)]
     return scal, wav
 
 
-def analysis(f, L, B, J0, multires=True, real=True, orders=None):
+def analysis(f, L, B, J0, multires=True, real=True, orders=None, kernel="sd"):
     """With `orders`, only the parts of those orders m are computed: every step
     acts on each order separately, so the result is the order-m component of
     the full analysis (used to time a bounded sample of one map)."""
     flm = sht.forward(f, L, orders)
-    scal_lm, wav_lm = analysis_lm(flm, L, B, J0, multires)
-    n_scal, n_wav = kernels.bandlimits(L, B, J0, multires)
+    scal_lm, wav_lm = analysis_lm(flm, L, B, J0, multires, kernel)
+    n_scal, n_wav = bandlimits(L, B, J0, multires, kernel)
     f_scal = sht.inverse(scal_lm, n_scal, real=real, orders=orders)
     f_wav = [sht.inverse(w, n, real=real, orders=orders) for w, n in zip(wav_lm, n_wav)]
     return f_wav, f_scal
@@ -73,9 +86,9 @@ def _pad(xlm, L):
     return out
 
 
-def synthesis_lm(scal_lm, wav_lm, L, B, J0):
+def synthesis_lm(scal_lm, wav_lm, L, B, J0, kernel="sd"):
     """Eq. (waveletsynthesis) in harmonic space."""
-    phi, psi = tables(L, B, J0)
+    phi, psi = tables(L, B, J0, kernel)
     c = _norm(L)
     flm = c * _pad(scal_lm, L) * _expand(phi, L)
     for w, p in zip(wav_lm, psi):
@@ -83,20 +96,20 @@ def synthesis_lm(scal_lm, wav_lm, L, B, J0):
     return flm
 
 
-def synthesis(f_wav, f_scal, L, B, J0, multires=True, real=True, orders=None):
+def synthesis(f_wav, f_scal, L, B, J0, multires=True, real=True, orders=None, kernel="sd"):
     """With `orders`, only the parts of those orders m (see analysis())."""
-    n_scal, n_wav = kernels.bandlimits(L, B, J0, multires)
+    n_scal, n_wav = bandlimits(L, B, J0, multires, kernel)
     scal_lm = sht.forward(f_scal, n_scal, orders)
     wav_lm = [sht.forward(w, n, orders) for w, n in zip(f_wav, n_wav)]
-    flm = synthesis_lm(scal_lm, wav_lm, L, B, J0)
+    flm = synthesis_lm(scal_lm, wav_lm, L, B, J0, kernel)
     return sht.inverse(flm, L, real=real, orders=orders)
 
 
-def analysis_adjoint(g_wav, g_scal, L, B, J0, multires=True, real=True):
+def analysis_adjoint(g_wav, g_scal, L, B, J0, multires=True, real=True, kernel="sd"):
     """Conjugate transpose of analysis(): sum over maps of
     forward_L^H diag(conj(c)) inverse_N^H, with c the kernel factor of each map."""
-    phi, psi = tables(L, B, J0)
-    n_scal, n_wav = kernels.bandlimits(L, B, J0, multires)
+    phi, psi = tables(L, B, J0, kernel)
+    n_scal, n_wav = bandlimits(L, B, J0, multires, kernel)
     c = _norm(L)
     ylm = np.conj(c * np.conj(_expand(phi, L))) * _pad(sht.inverse_adjoint(g_scal, n_scal), L)
     for g, p, n in zip(g_wav, psi, n_wav):

@@ -119,3 +119,75 @@ def test_kappa_relative_accuracy_near_support_edges():
             assert got > 0.0
             # absolute accuracy at the FP64 level everywhere, relative where kappa > 1e-12
             assert abs(got - ref) < 2e-16 + (1e-11 * ref if ref > 1e-12 else 0.0)
+
+
+# ---------------------------------------------------------------- B-spline family (footnote of Sect. 2.2)
+def test_bspline3_values_and_partition_of_unity():
+    """The cubic B-spline: B_3(0) = 2/3, B_3(+-1) = 1/6, B_3(+-1/2) = 23/48, zero for
+    |x| >= 2, and its integer translates sum to one (the textbook properties, which
+    any dropped term or wrong coefficient of the five-term sum breaks)."""
+    B3 = kernels.bspline3
+    assert B3(0.0) == pytest.approx(2.0 / 3.0, abs=1e-15)
+    assert B3(1.0) == pytest.approx(1.0 / 6.0, abs=1e-15) and B3(-1.0) == pytest.approx(1.0 / 6.0, abs=1e-15)
+    assert B3(0.5) == pytest.approx(23.0 / 48.0, abs=1e-15) and B3(-0.5) == pytest.approx(23.0 / 48.0, abs=1e-15)
+    for x in (2.0, -2.0, 2.5, -3.7):
+        assert abs(B3(x)) < 1e-15
+    for x in np.linspace(-0.5, 0.5, 11):
+        assert sum(B3(x - k) for k in range(-3, 4)) == pytest.approx(1.0, abs=1e-14)
+    # piecewise form on [0, 1] and [1, 2]
+    for x in np.linspace(0.0, 1.0, 9):
+        assert B3(x) == pytest.approx(2.0 / 3.0 - x * x + x ** 3 / 2.0, abs=1e-14)
+    for x in np.linspace(1.0, 2.0, 9):
+        assert B3(x) == pytest.approx((2.0 - x) ** 3 / 6.0, abs=1e-14)
+
+
+@pytest.mark.parametrize("L,B,J0", [(32, 2, 0), (128, 3, 2), (256, 2, 1), (100, 3, 1)])
+def test_bspline_admissibility(L, B, J0):
+    """With the finest scale taking the remainder, the squared B-spline kernels of
+    all scales and the scaling function sum to one for every l < L (exact
+    reconstruction, Eq. identity)."""
+    phi, psi = wavelet.tables(L, B, J0, "bspline")
+    l = np.arange(L)
+    total = 4 * np.pi / (2 * l + 1) * (phi ** 2 + sum(p ** 2 for p in psi))
+    assert np.max(np.abs(total - 1.0)) < 1e-14
+
+
+@pytest.mark.parametrize("L,B,J0", [(128, 3, 2), (256, 2, 1), (2048, 2, 2), (500, 3, 0)])
+def test_bspline_support_and_bandlimits(L, B, J0):
+    """The j-th B-spline filter (j < J) has support [0, L / lambda^(J-j-2)) (footnote of
+    Sect. 2.2 and Sect. 3.1); the scaling function vanishes from L / lambda^(J-J0-1) on;
+    the multiresolution band-limits are the (capped) ends of these supports."""
+    J = kernels.jmax(L, B)
+    phi, psi = wavelet.tables(L, B, J0, "bspline")
+    l = np.arange(L)
+    for j, p in zip(range(J0, J + 1), psi):
+        end = L / B ** (J - j - 2)
+        if j < J:
+            assert np.all(p[l >= end] == 0.0)
+            assert np.all(p[(l > 0) & (l < end)] > 0.0)
+        assert p[0] == 0.0                          # no scale sees the monopole but the scaling function
+    assert np.all(phi[l >= L / B ** (J - J0 - 1)] == 0.0)
+    assert np.all(phi[l < L / B ** (J - J0 - 1)] > 0.0)
+    n_scal, n_wav = wavelet.bandlimits(L, B, J0, True, "bspline")
+    assert n_scal == min(L, math.ceil(L / B ** (J - J0 - 1)))
+    assert n_wav == [min(L, math.ceil(L / B ** (J - j - 2))) if J - j - 2 > 0 else L for j in range(J0, J + 1)]
+    # every kernel vanishes at and beyond its band-limit
+    assert np.all(phi[n_scal:] == 0.0)
+    for p, n in zip(psi, n_wav):
+        assert np.all(p[n:] == 0.0)
+    # B-spline scales are at least as wide as the scale-discretised ones (Sect. 3.1)
+    _, n_sd = kernels.bandlimits(L, B, J0, True)
+    assert all(a >= b for a, b in zip(n_wav, n_sd))
+
+
+def test_bspline_k_shape():
+    """k(t) = 3/2 B_3(2 t lambda^(J-1) / L): 1 at t = 0, 0 from t = L / lambda^(J-1) on,
+    strictly decreasing in between."""
+    L, lam = 256, 2
+    J = kernels.jmax(L, lam)
+    t_end = L / lam ** (J - 1)
+    assert kernels.k_bspline(0.0, lam, L, J) == pytest.approx(1.0, abs=1e-15)
+    assert kernels.k_bspline(t_end, lam, L, J) == 0.0
+    ts = np.linspace(0.0, t_end, 33)
+    ks = [kernels.k_bspline(t, lam, L, J) for t in ts]
+    assert all(a > b for a, b in zip(ks[:-1], ks[1:]))

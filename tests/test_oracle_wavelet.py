@@ -153,3 +153,32 @@ def test_round_trip_by_orders():
                                            - np.repeat(np.arange(n), 2 * np.arange(n) + 1), sub),
                                    sht.forward(w, n), 0), n)
         assert np.max(np.abs(w_s - ref)) < 1e-13
+
+
+@pytest.mark.parametrize("L,B,J0,multires,real", [(32, 2, 0, True, True), (40, 3, 1, True, False),
+                                                  (33, 2, 1, False, True)])
+def test_bspline_exact_reconstruction(L, B, J0, multires, real):
+    """B-spline generating functions (footnote of Sect. 2.2): synthesis after analysis
+    returns the map, with every scale at its (wider) multiresolution band-limit."""
+    f = sht.inverse(inputs.random_flm(L, 9, real=real), L, real=real)
+    fw, fs = wavelet.analysis(f, L, B, J0, multires, real, kernel="bspline")
+    n_scal, n_wav = wavelet.bandlimits(L, B, J0, multires, "bspline")
+    assert fs.shape == (n_scal, 2 * n_scal - 1)
+    assert [w.shape for w in fw] == [(n, 2 * n - 1) for n in n_wav]
+    fr = wavelet.synthesis(fw, fs, L, B, J0, multires, real, kernel="bspline")
+    assert np.max(np.abs(fr - f)) / np.max(np.abs(f)) < 1e-13
+
+
+def test_bspline_multires_matches_full_resolution():
+    """The B-spline multiresolution maps hold the full-resolution maps' harmonic
+    content: the band-limits are the kernels' supports (Sect. 3.1)."""
+    L, B, J0 = 48, 2, 1
+    f = sht.inverse(inputs.random_flm(L, 13, real=True), L, real=True)
+    fw_m, fs_m = wavelet.analysis(f, L, B, J0, True, True, kernel="bspline")
+    fw_f, fs_f = wavelet.analysis(f, L, B, J0, False, True, kernel="bspline")
+    n_scal, n_wav = wavelet.bandlimits(L, B, J0, True, "bspline")
+    for wm, wf, n in list(zip(fw_m, fw_f, n_wav)) + [(fs_m, fs_f, n_scal)]:
+        lm_m = sht.forward(wm, n)
+        lm_f = sht.forward(wf, L)
+        assert np.max(np.abs(lm_f[:n * n] - lm_m)) < 1e-13
+        assert np.max(np.abs(lm_f[n * n:])) < 1e-13 if n < L else True
