@@ -4,7 +4,7 @@ on MW-sampled spheres, one step = one round trip of a batch of real maps at
 L = 2048, B = 2, J_min = 2, multiresolution (64 maps per GPU).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
-                  [--L L --B B --J-min J0 --full-res]   (other workloads)
+                  [--L L --B B --J-min J0 --full-res --kernel sd|bspline]   (other workloads)
 
 Prints one JSON line (rank 0).  Inputs are seeded synthetic maps: Gaussian
 f_lm with C_l = 1/(l(l+1)), turned into maps by the library's inverse
@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--B", type=int, default=2)
     ap.add_argument("--J-min", type=int, default=2)
+    ap.add_argument("--kernel", choices=["sd", "bspline"], default="sd",
+                    help="generating functions: smooth scale-discretised (sd) or cubic B-spline")
     ap.add_argument("--full-res", action="store_true",
                     help="every wavelet and scaling map at L (the full-resolution transform) instead of the "
                          "multiresolution band-limits min(L, B^(j+1))")
@@ -73,8 +75,10 @@ def parse():
 
 
 def config(a):
-    return {"workload": "real maps, L=%d, B=%d, J_min=%d, %s, %d maps per GPU, f_lm ~ C_l=1/(l(l+1))"
-                        % (a.L, a.B, a.J_min, "full resolution" if a.full_res else "multiresolution", a.batch),
+    return {"workload": "real maps, L=%d, B=%d, J_min=%d, %s%s, %d maps per GPU, f_lm ~ C_l=1/(l(l+1))"
+                        % (a.L, a.B, a.J_min, "full resolution" if a.full_res else "multiresolution",
+                           ", B-spline kernels" if a.kernel == "bspline" else "", a.batch),
+            "kernel": a.kernel,
             "L": a.L, "B": a.B, "J_min": a.J_min, "maps_per_gpu": a.batch, "multires": not a.full_res,
             "signal": "real",
             "precision": a.precision + ("+quad_fft64" if a.quad_fft64 else "") + ("+split3" if a.tc_split3 else ""),
@@ -144,8 +148,8 @@ def oracle_sample_step(f, a, orders):
     full workload size, restricted to the given orders m (both transforms act
     on each order separately)."""
     import oracle.wavelet as ow
-    fw, fs = ow.analysis(f, a.L, a.B, a.J_min, not a.full_res, False, orders=orders)
-    ow.synthesis(fw, fs, a.L, a.B, a.J_min, not a.full_res, False, orders=orders)
+    fw, fs = ow.analysis(f, a.L, a.B, a.J_min, not a.full_res, False, orders=orders, kernel=a.kernel)
+    ow.synthesis(fw, fs, a.L, a.B, a.J_min, not a.full_res, False, orders=orders, kernel=a.kernel)
 
 
 def oracle_input(a, seed):
@@ -218,7 +222,7 @@ def check_errors(plan, x, fw, fs, out, flm, a):
     input coefficients; plus the round-trip reconstruction error."""
     import oracle.sht as osht
     import oracle.wavelet as ow
-    phi, psi = ow.tables(a.L, a.B, a.J_min)
+    phi, psi = ow.tables(a.L, a.B, a.J_min, a.kernel)
     res = {}
     views = plan.wavelet_views(fw)
     maps = [("scal", plan.N_scal, phi, fs)] + [("j%d" % j, n, p, v) for (j, n, _, _), p, v in
@@ -255,6 +259,7 @@ def run_gpu(a, rank, world, local_rank):
     seeds = [3000 + rank * a.batch + i for i in range(a.batch)]
     flm = inputs.random_flm_batch(a.L, seeds, real=True, kind="cl")
     plan = Plan(a.L, a.B, a.J_min, batch=a.batch, real=True, multires=not a.full_res, precision=a.precision,
+                kernel=a.kernel,
                 quad_fft64=a.quad_fft64, tc_split3=a.tc_split3)
     flm_d = torch.from_numpy(np.stack([flm.real, flm.imag], -1)).to(device="cuda", dtype=plan.dtype).contiguous()
     x = plan.sht_inverse(flm_d)
@@ -406,7 +411,8 @@ def run_gpu(a, rank, world, local_rank):
     if rank == 0 and not a.skip_fp64 and a.precision != "fp64":
         del fw, fs, out
         nb = a.fp64_batch
-        p64 = Plan(a.L, a.B, a.J_min, batch=nb, real=True, multires=not a.full_res, precision="fp64")
+        p64 = Plan(a.L, a.B, a.J_min, batch=nb, real=True, multires=not a.full_res, precision="fp64",
+                   kernel=a.kernel)
         f64 = torch.from_numpy(np.stack([flm[:nb].real, flm[:nb].imag], -1)).cuda().contiguous()
         x64 = p64.sht_inverse(f64)
         w64, s64 = p64.empty_wavelets()

@@ -68,6 +68,17 @@ extern "C" {
 #define S2LET_TC_SPLIT3 0x200    /* TF32X3 plans only: split operands in three
                                     TF32 parts (6 MMAs per product) instead of
                                     two (3 MMAs)                               */
+#define S2LET_KERNEL_BSPLINE 0x400 /* B-spline generating functions (footnote of
+                                    Sect. 2.2) instead of the smooth scale-
+                                    discretised ones: k(t) = 3/2 B_3(2 t B^(J-1)
+                                    / L), wavelet j the square root of
+                                    k(l/B^(j+1)) - k(l/B^j), the finest scale J
+                                    sqrt(1 - k(l/B^J)) (so that the tiling is
+                                    admissible), scaling sqrt(k(l/B^J_min)).
+                                    Multiresolution band-limits (Sect. 3.1):
+                                    min(L, ceil(L / B^(J-j-2))) for scale j and
+                                    min(L, ceil(L / B^(J-J_min-1))) for the
+                                    scaling map                                */
 
 typedef struct s2let_plan s2let_plan;
 

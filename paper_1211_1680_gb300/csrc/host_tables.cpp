@@ -133,6 +133,34 @@ double kappa_lambda(double t, double lam)
 
 double eta_lambda(double t, double lam) { return std::sqrt(k_lambda(t, lam)); }
 
+// cubic B-spline as its two polynomial pieces: 2/3 - x^2 + |x|^3 / 2 on |x| <= 1,
+// (2 - |x|)^3 / 6 on 1 < |x| < 2, zero beyond
+static double bspline3(double x)
+{
+    const double a = std::fabs(x);
+    if (a >= 2.0) return 0.0;
+    if (a <= 1.0) return 2.0 / 3.0 - a * a + 0.5 * a * a * a;
+    const double b = 2.0 - a;
+    return b * b * b / 6.0;
+}
+
+double bspline_k(double t, double lam, int L, int J)
+{
+    return 1.5 * bspline3(2.0 * t * std::pow(lam, J - 1) / L);
+}
+
+double bspline_eta(int l, int B, int J0, int L, int J)
+{
+    return std::sqrt(std::max(0.0, bspline_k(l / std::pow((double)B, J0), B, L, J)));
+}
+
+double bspline_kappa(int l, int B, int j, int L, int J)
+{
+    const double kj = bspline_k(l / std::pow((double)B, j), B, L, J);
+    const double d = j < J ? bspline_k(l / std::pow((double)B, j + 1), B, L, J) - kj : 1.0 - kj;
+    return std::sqrt(std::max(0.0, d));
+}
+
 int jmax(int L, int B)
 {
     int J = 0;

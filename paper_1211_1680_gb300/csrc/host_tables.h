@@ -19,6 +19,15 @@ void fft_pow2(std::vector<cd> &a, int sign);
 double k_lambda(double t, double lam);
 double kappa_lambda(double t, double lam);
 double eta_lambda(double t, double lam);
+// B-spline generating function of the footnote of Sect. 2.2:
+// k(t) = 3/2 B_3(2 t lambda^(J-1) / L), B_3 the cubic B-spline (support (-2, 2))
+double bspline_k(double t, double lam, int L, int J);
+// kernel factors of the B-spline family for degree l: scaling eta(l / lambda^J0) =
+// sqrt(k(l / lambda^J0)); wavelet j < J: sqrt(k(l / lambda^(j+1)) - k(l / lambda^j));
+// the finest scale j = J: sqrt(1 - k(l / lambda^J)), so that the squared factors of
+// all maps sum to one for every l (exact reconstruction)
+double bspline_eta(int l, int B, int J0, int L, int J);
+double bspline_kappa(int l, int B, int j, int L, int J);
 int jmax(int L, int B);
 
 // Per band-limit tables (see fft.cuh and legendre.cuh for their meaning);

@@ -733,7 +733,8 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
     if (J0 < 0 || J0 >= J) return S2LET_ERR_ARG;
     const int prec = flags & S2LET_PREC_MASK;
     if (prec != S2LET_PREC_FP64 && prec != S2LET_PREC_FP32 && prec != S2LET_PREC_TF32X3) return S2LET_ERR_ARG;
-    if (flags & ~(S2LET_COMPLEX | S2LET_MULTIRES | S2LET_PREC_MASK | S2LET_QUAD_FFT64 | S2LET_TC_SPLIT3))
+    if (flags & ~(S2LET_COMPLEX | S2LET_MULTIRES | S2LET_PREC_MASK | S2LET_QUAD_FFT64 | S2LET_TC_SPLIT3 |
+                  S2LET_KERNEL_BSPLINE))
         return S2LET_ERR_ARG;
     if ((flags & S2LET_TC_SPLIT3) && prec != S2LET_PREC_TF32X3) return S2LET_ERR_ARG;
     if ((flags & S2LET_QUAD_FFT64) && prec == S2LET_PREC_FP64) return S2LET_ERR_ARG;
@@ -759,10 +760,18 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
         for (int i = 0; i < e; ++i) r = std::min<long long>(r * b, 1LL << 40);
         return r;
     };
-    p->n_scal = p->multires ? (int)std::min<long long>(L, ipow(B, J0)) : L;
+    // B-spline family: scale j is band-limited by the end of its kernel's support,
+    // min(L, ceil(L / B^(J-j-2))), the scaling map by min(L, ceil(L / B^(J-J0-1)))
+    const bool bspline = (flags & S2LET_KERNEL_BSPLINE) != 0;
+    auto cap = [&](int e) -> int {
+        if (e <= 0) return L;
+        const long long d = ipow(B, e);
+        return (int)std::min<long long>(L, (L + d - 1) / d);
+    };
+    p->n_scal = !p->multires ? L : bspline ? cap(J - J0 - 1) : (int)std::min<long long>(L, ipow(B, J0));
     int64_t off = 0;
     for (int j = J0; j <= J; ++j) {
-        const int N = p->multires ? (int)std::min<long long>(L, ipow(B, j + 1)) : L;
+        const int N = !p->multires ? L : bspline ? cap(J - j - 2) : (int)std::min<long long>(L, ipow(B, j + 1));
         p->n_wav.push_back(N);
         p->wav_off.push_back(off);
         off += map_elems(p.get(), N) * batch;
@@ -791,8 +800,11 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
     for (int k = 0; k <= J - J0 + 1; ++k) {
         std::vector<double> fac(L);
         for (int l = 0; l < L; ++l) {
-            fac[l] = (k == 0) ? s2h::eta_lambda(l / std::pow((double)B, J0), B)
-                              : s2h::kappa_lambda(l / std::pow((double)B, J0 + k - 1), B);
+            if (bspline)
+                fac[l] = (k == 0) ? s2h::bspline_eta(l, B, J0, L, J) : s2h::bspline_kappa(l, B, J0 + k - 1, L, J);
+            else
+                fac[l] = (k == 0) ? s2h::eta_lambda(l / std::pow((double)B, J0), B)
+                                  : s2h::kappa_lambda(l / std::pow((double)B, J0 + k - 1), B);
         }
         if (p->fp64) {
             p->kfac.push_back(dev_upload(fac, p->owned, err));

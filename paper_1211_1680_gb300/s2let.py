@@ -8,7 +8,7 @@ import torch
 
 from . import _lib
 from ._lib import (S2LET_COMPLEX, S2LET_MULTIRES, S2LET_PREC_FP32, S2LET_PREC_FP64,  # noqa: F401
-                   S2LET_PREC_TF32X3, S2LET_QUAD_FFT64, S2LET_TC_SPLIT3, check)
+                   S2LET_KERNEL_BSPLINE, S2LET_PREC_TF32X3, S2LET_QUAD_FFT64, S2LET_TC_SPLIT3, check)
 
 PRECISIONS = {"fp64": S2LET_PREC_FP64, "fp32": S2LET_PREC_FP32, "tf32x3": S2LET_PREC_TF32X3}
 
@@ -25,20 +25,28 @@ def _stream_handle(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _kernel_flag(kernel):
+    if kernel not in ("sd", "bspline"):
+        raise ValueError("kernel must be 'sd' or 'bspline'")
+    return S2LET_KERNEL_BSPLINE if kernel == "bspline" else 0
+
+
 class Plan:
     """A batched transform plan: `batch` maps of band-limit L, dilation B,
     lowest scale J_min (Sect. 2.2), real or complex, multiresolution or not,
-    precision "fp64" or "fp32"."""
+    precision "fp64", "fp32" or "tf32x3", generating functions `kernel` "sd"
+    (smooth scale-discretised) or "bspline" (footnote of Sect. 2.2)."""
 
     def __init__(self, L, B, J_min, batch=1, real=True, multires=True, precision="fp64",
-                 quad_fft64=False, tc_split3=False, device=None):
+                 quad_fft64=False, tc_split3=False, device=None, kernel="sd"):
         flags = (0 if real else S2LET_COMPLEX) | (S2LET_MULTIRES if multires else 0) | PRECISIONS[precision]
+        flags |= _kernel_flag(kernel)
         if quad_fft64:
             flags |= S2LET_QUAD_FFT64
         if tc_split3:
             flags |= S2LET_TC_SPLIT3
         self.L, self.B, self.J_min, self.batch = L, B, J_min, batch
-        self.real, self.multires, self.precision = real, multires, precision
+        self.real, self.multires, self.precision, self.kernel = real, multires, precision, kernel
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         self._h = ctypes.c_void_p()
@@ -194,12 +202,13 @@ class BatchPlan:
     graph (captured on the first call for a set of buffers) replays the round
     trip of every group with a single launch."""
 
-    def __init__(self, Ls, Bs, J_min, real=True, multires=True, precision="fp32", device=None):
+    def __init__(self, Ls, Bs, J_min, real=True, multires=True, precision="fp32", device=None, kernel="sd"):
         Ls = [int(x) for x in Ls]
         Bs = [int(x) for x in Bs]
         if len(Ls) != len(Bs) or not Ls:
             raise ValueError("need equally long, non-empty L and B lists")
         flags = (0 if real else S2LET_COMPLEX) | (S2LET_MULTIRES if multires else 0) | PRECISIONS[precision]
+        flags |= _kernel_flag(kernel)
         self.Ls, self.Bs, self.J_min, self.real = Ls, Bs, J_min, real
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.dtype = torch.float64 if precision == "fp64" else torch.float32

@@ -52,3 +52,16 @@ def test_plan_argument_errors_need_no_gpu():
     assert L.s2let_plan_create(ctypes.byref(h), 4096, 2, 0, 0, 1) == _lib.S2LET_ERR_ARG
     assert L.s2let_plan_create(ctypes.byref(h), 32, 2, 0, 0, 0) == _lib.S2LET_ERR_ARG
     assert not h.value
+
+
+def test_flag_constants_match_header():
+    """Every S2LET_* constant the header defines has the same value in the binding."""
+    txt = open(os.path.join(ROOT, "include", "s2let_gpu.h")).read()
+    defs = {k: int(v, 0) for k, v in re.findall(r"#define\s+(S2LET_\w+)\s+\(?(-?(?:0x)?[0-9a-fA-F]+)\)?", txt)}
+    assert "S2LET_KERNEL_BSPLINE" in defs and "S2LET_PREC_TF32X3" in defs
+    for k, v in defs.items():
+        if hasattr(_lib, k):
+            assert getattr(_lib, k) == v, k
+    for k in ("S2LET_COMPLEX", "S2LET_MULTIRES", "S2LET_PREC_FP32", "S2LET_PREC_TF32X3", "S2LET_QUAD_FFT64",
+              "S2LET_TC_SPLIT3", "S2LET_KERNEL_BSPLINE", "S2LET_ERR_ARG"):
+        assert getattr(_lib, k) == defs[k], k

@@ -124,6 +124,48 @@ def test_adjoint_against_oracle(L, B, J0, multires, real, prec):
     assert plan.status() == 0
 
 
+BSPLINE_CASES = [  # L, B, J0, multires, real, prec
+    (64, 2, 1, True, True, "fp64"),
+    (40, 3, 1, True, False, "fp64"),
+    (33, 2, 0, False, True, "fp32"),       # full resolution, odd band-limit
+    (96, 2, 2, True, True, "tf32x3"),
+    (130, 3, 1, True, False, "tf32x3"),    # band-limits ceil(L / 3^e), not powers of B
+]
+
+
+@pytest.mark.parametrize("L,B,J0,multires,real,prec", BSPLINE_CASES)
+def test_bspline_wavelets(L, B, J0, multires, real, prec):
+    """B-spline generating functions (footnote of Sect. 2.2): the plan's band-limits,
+    the analysis maps, the synthesis of the oracle's maps and the adjoint against
+    the oracle's B-spline transform."""
+    seeds = [31, 32]
+    f = _maps(L, seeds, real)
+    plan = Plan(L, B, J0, batch=len(seeds), real=real, multires=multires, kernel="bspline", **plan_kwargs(prec))
+    n_scal, n_wav = wavelet.bandlimits(L, B, J0, multires, "bspline")
+    assert plan.N_scal == n_scal and [n for (_, n, _, _) in plan.scales] == n_wav
+    fw_d, fs_d = plan.analysis(to_dev_map(f, plan.dtype, real))
+    ref = [wavelet.analysis(x, L, B, J0, multires, real, kernel="bspline") for x in f]
+    for i, view in enumerate(plan.wavelet_views(fw_d)):
+        want = np.stack([r[0][i] for r in ref])
+        assert rel_err(from_dev_map(view, real), want) < TOL[prec], "scale %d" % (J0 + i)
+    assert rel_err(from_dev_map(fs_d, real), np.stack([r[1] for r in ref])) < TOL[prec]
+    fw_in = torch.cat([to_dev_map(np.stack([r[0][i] for r in ref]), plan.dtype, real).reshape(-1)
+                       for i in range(len(ref[0][0]))])
+    fs_in = to_dev_map(np.stack([r[1] for r in ref]), plan.dtype, real)
+    rec = from_dev_map(plan.synthesis(fw_in, fs_in), real)
+    assert rel_err(rec, f) < TOL[prec]
+    # adjoint of the analysis on random wavelet-space inputs
+    gws = [[inputs.random_map((n, 2 * n - 1), 300 * b + i, real) for i, n in enumerate(n_wav)] for b in range(2)]
+    gss = [inputs.random_map((n_scal, 2 * n_scal - 1), 97 + b, real) for b in range(2)]
+    gw = torch.cat([to_dev_map(np.stack([g[i] for g in gws]), plan.dtype, real).reshape(-1)
+                    for i in range(len(n_wav))])
+    got = from_dev_map(plan.adjoint(gw, to_dev_map(np.stack(gss), plan.dtype, real)), real)
+    want = np.stack([wavelet.analysis_adjoint(gws[b], gss[b], L, B, J0, multires, real, kernel="bspline")
+                     for b in range(2)])
+    assert rel_err(got, want) < TOL[prec]
+    assert plan.status() == 0
+
+
 def test_plans_of_different_sizes_coexist():
     """A smaller plan created after a larger one must not break the larger one."""
     big = Plan(200, 2, 1, batch=1, real=True, precision="fp32")
