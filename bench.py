@@ -41,6 +41,12 @@ FLOPS_COUNTED = {
 }
 
 
+# noise level of the --denoise steps: white noise of this harmonic standard
+# deviation would be thresholded at 3 sigma^j; against the C_l = 1/(l(l+1)) maps
+# it zeroes a large part of the fine-scale samples
+DENOISE_SIGMA = 1e-3
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -56,6 +62,9 @@ def parse():
     ap.add_argument("--J-min", type=int, default=2)
     ap.add_argument("--kernel", choices=["sd", "bspline"], default="sd",
                     help="generating functions: smooth scale-discretised (sd) or cubic B-spline")
+    ap.add_argument("--denoise", action="store_true",
+                    help="each step denoises (Sect. 4.2): analysis, hard thresholding of the wavelet maps at "
+                         "3 sigma^j, synthesis")
     ap.add_argument("--full-res", action="store_true",
                     help="every wavelet and scaling map at L (the full-resolution transform) instead of the "
                          "multiresolution band-limits min(L, B^(j+1))")
@@ -78,7 +87,7 @@ def config(a):
     return {"workload": "real maps, L=%d, B=%d, J_min=%d, %s%s, %d maps per GPU, f_lm ~ C_l=1/(l(l+1))"
                         % (a.L, a.B, a.J_min, "full resolution" if a.full_res else "multiresolution",
                            ", B-spline kernels" if a.kernel == "bspline" else "", a.batch),
-            "kernel": a.kernel,
+            "kernel": a.kernel, "denoise": a.denoise,
             "L": a.L, "B": a.B, "J_min": a.J_min, "maps_per_gpu": a.batch, "multires": not a.full_res,
             "signal": "real",
             "precision": a.precision + ("+quad_fft64" if a.quad_fft64 else "") + ("+split3" if a.tc_split3 else ""),
@@ -271,6 +280,8 @@ def run_gpu(a, rank, world, local_rank):
 
     def step(src=x):
         plan.analysis(src, fw, fs)
+        if a.denoise:
+            plan.threshold(fw, DENOISE_SIGMA)
         plan.synthesis(fw, fs, out)
 
     for _ in range(a.warmup):
@@ -405,6 +416,11 @@ def run_gpu(a, rank, world, local_rank):
                       "d2h_bytes_per_step": oh.numel() * oh.element_size()}
 
     if rank == 0 and not a.skip_check:
+        if a.denoise:
+            # the check compares the transform itself: one round trip without thresholding
+            plan.analysis(x, fw, fs)
+            plan.synthesis(fw, fs, out)
+            torch.cuda.synchronize()
         res.update(check_errors(plan, x, fw, fs, out, flm[0], a))
 
     # the plain FP64 GPU path on the same workload (fewer maps per launch)

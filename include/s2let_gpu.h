@@ -247,6 +247,27 @@ int s2let_plan_tuning(const s2let_plan *plan, int N, int *tc_quad, int *tc_anal,
 #define S2LET_NOALLOC_SCRATCH_BYTES (8u << 20)
 int s2let_sht_inverse_noalloc(int L, int batch, int flags, const void *flm, void *f, void *stream);
 
+/* Wavelet denoising by hard thresholding (Sect. 4.2).
+ *
+ * s2let_wav_noise_std: *ratio = sigma^j / sigma = sqrt(sum_l |Psi^j_l0|^2), the
+ *   standard deviation in scale j (j = -1: the scaling function Phi) of zero-mean
+ *   white noise whose harmonic coefficients have variance sigma^2 (Eqs. noisevar,
+ *   noisemodel), from the plan's kernel tables.  Host only.  S2LET_ERR_ARG for a
+ *   j outside {-1, J_min..J}.
+ * s2let_wav_threshold: Eq. (threshold) in place on the wavelet maps `f_wav` (the
+ *   plan's wavelet layout, device pointer, caller-owned): every sample of scale
+ *   j whose modulus (absolute value of a real sample, |re + i im| of a complex
+ *   one) is below T^j = nsigma * sigma^j is set to zero, the others are kept; the
+ *   scaling maps are not thresholded (the paper keeps the scaling coefficients).
+ *   The paper's T^j = 3 sigma^j is nsigma = 3.  The test is made in the plan's
+ *   precision on T^j rounded to it (complex: re*re + im*im < T*T, each operation
+ *   rounded to nearest).  One kernel launch on `stream`; S2LET_ERR_ARG for a
+ *   negative or non-finite sigma or nsigma or a NULL pointer.
+ * Denoising (Sect. 4.2) is s2let_analysis, s2let_wav_threshold on f_wav, then
+ * s2let_synthesis with the unchanged f_scal. */
+int s2let_wav_noise_std(const s2let_plan *plan, int j, double *ratio);
+int s2let_wav_threshold(s2let_plan *plan, void *f_wav, double sigma, double nsigma, void *stream);
+
 /* Device-side status of a plan: S2LET_ERR_TIMEOUT if a bounded wait inside a
  * tensor-core kernel gave up since the plan was created (its results are then
  * not valid), else S2LET_OK.  Synchronises the device. */

@@ -93,6 +93,8 @@ struct s2let_plan {
     double2 *coefd = nullptr;               // [m][l] (a, a b), FP64
     float4 *coeff = nullptr;                // [m][l] float-float
     std::vector<void *> kfac;               // per map: scaling first, then scales J0..J (R[L])
+    std::vector<double> noise_ratio;        // per map (same order): sqrt(sum_l |Psi_l0|^2), Eq. noisemodel
+    int nsm = 0;                            // SMs of the plan's device
     void *F = nullptr, *flm = nullptr, *G = nullptr;   // workspace
     void *Ft = nullptr;                                // ring-major spectra of the ring DFTs
     bool quad_gemm = false;                 // FP32 plans: theta quadrature as a dense FP32 product
@@ -780,6 +782,12 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
     p->scal_elems = map_elems(p.get(), p->n_scal) * batch;
 
     int err = S2LET_OK;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return S2LET_ERR_CUDA;
+    }
     if (cudaMalloc(&p->d_err, sizeof(int)) != cudaSuccess) return S2LET_ERR_ALLOC;
     p->owned.push_back(p->d_err);
     if (cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess) return S2LET_ERR_CUDA;
@@ -806,6 +814,11 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
                 fac[l] = (k == 0) ? s2h::eta_lambda(l / std::pow((double)B, J0), B)
                                   : s2h::kappa_lambda(l / std::pow((double)B, J0 + k - 1), B);
         }
+        // white noise of unit harmonic variance has, in this map, the per-sample
+        // variance sum_l |Psi_l0|^2 = sum_l (2l+1)/(4 pi) fac_l^2 (Eq. noisemodel)
+        double v = 0.0;
+        for (int l = 0; l < L; ++l) v += (2.0 * l + 1.0) / (4.0 * M_PI) * fac[l] * fac[l];
+        p->noise_ratio.push_back(std::sqrt(v));
         if (p->fp64) {
             p->kfac.push_back(dev_upload(fac, p->owned, err));
         } else {
@@ -939,6 +952,85 @@ template <typename R> int autotune_t(s2let_plan *p, cudaStream_t st)
 
 }  // namespace
 
+namespace {
+
+// ---------------------------------------------------------------- hard thresholding (Sect. 4.2)
+// The samples of scale s (R values of a real map, (re, im) pairs of a complex
+// map) are [begin[s], begin[s+1]) of the wavelet buffer; each is set to zero
+// where its modulus is below thr[s] (Eq. threshold).  Complex samples compare
+// the squared modulus with thr^2, every product and the sum rounded on its own,
+// so that the decision is the one the same-precision host arithmetic takes.
+// Every thread walks all scales, a grid-stride pass per scale with U samples in
+// flight, so no sample searches for its scale.
+constexpr int kThrMaxScales = 32;
+template <typename R> struct ThrTab {
+    int n;
+    int64_t begin[kThrMaxScales + 1];
+    R thr[kThrMaxScales];
+};
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
+template <typename R, bool CPLX>
+__global__ void __launch_bounds__(256) k_wav_threshold(R *__restrict__ w, ThrTab<R> tab)
+{
+    using C = cplx_t<R>;
+    constexpr int U = 4;                          // samples in flight per thread
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int s = 0; s < tab.n; ++s) {
+        const int64_t end = tab.begin[s + 1];
+        const R t = tab.thr[s];
+        const R t2 = mul_rn(t, t);
+        for (int64_t i0 = tab.begin[s] + t0; i0 < end; i0 += U * stride) {
+            C v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t i = i0 + u * stride;
+                if (i < end) v[u] = CPLX ? reinterpret_cast<const C *>(w)[i] : C{w[i], R(0)};
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t i = i0 + u * stride;
+                if (i >= end) continue;
+                if (CPLX) {
+                    if (add_rn(mul_rn(v[u].x, v[u].x), mul_rn(v[u].y, v[u].y)) < t2)
+                        reinterpret_cast<C *>(w)[i] = C{R(0), R(0)};
+                } else if (fabs(v[u].x) < t) {
+                    w[i] = R(0);
+                }
+            }
+        }
+    }
+}
+
+template <typename R>
+int run_threshold(const s2let_plan *p, void *f_wav, double sigma, double nsigma, cudaStream_t st)
+{
+    const int per = p->cplx ? 2 : 1;                 // R values per sample
+    ThrTab<R> tab;
+    tab.n = (int)p->n_wav.size();
+    for (int s = 0; s < tab.n; ++s) {
+        tab.begin[s] = p->wav_off[s] / per;
+        tab.thr[s] = (R)(nsigma * sigma * p->noise_ratio[s + 1]);
+    }
+    tab.begin[tab.n] = p->wav_elems / per;
+    const int64_t n = p->wav_elems / per;
+    if (n == 0) return S2LET_OK;
+    const int64_t want = (n + 256 * 4 - 1) / (256 * 4);
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)p->nsm * 8));
+    if (p->cplx)
+        k_wav_threshold<R, true><<<blocks, 256, 0, st>>>((R *)f_wav, tab);
+    else
+        k_wav_threshold<R, false><<<blocks, 256, 0, st>>>((R *)f_wav, tab);
+    S2_LAUNCH_CHECK();
+    return S2LET_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int s2let_jmax(int L, int B)
@@ -1037,6 +1129,27 @@ int s2let_plan_tuning(const s2let_plan *p, int N, int *tc_quad, int *tc_anal, in
     if (tc_synth) *tc_synth = p->tc && bd.tc_synth;
     if (fft_threads_out) *fft_threads_out = bd.fft_th ? bd.fft_th : fft_threads(bd.M);
     return S2LET_OK;
+}
+
+int s2let_wav_noise_std(const s2let_plan *p, int j, double *ratio)
+{
+    if (!p || !ratio) return S2LET_ERR_ARG;
+    if (j == -1) {
+        *ratio = p->noise_ratio[0];
+        return S2LET_OK;
+    }
+    if (j < p->J0 || j > p->J) return S2LET_ERR_ARG;
+    *ratio = p->noise_ratio[j - p->J0 + 1];
+    return S2LET_OK;
+}
+
+int s2let_wav_threshold(s2let_plan *p, void *f_wav, double sigma, double nsigma, void *stream)
+{
+    if (!p || !f_wav || !(sigma >= 0.0) || !(nsigma >= 0.0) || !std::isfinite(sigma * nsigma))
+        return S2LET_ERR_ARG;
+    if ((int)p->n_wav.size() > kThrMaxScales) return S2LET_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    return S2_DISPATCH(run_threshold, p, f_wav, sigma, nsigma, st);
 }
 
 int s2let_plan_status(s2let_plan *p)

@@ -195,6 +195,27 @@ class Plan:
         check("s2let_sht_inverse", _lib.lib().s2let_sht_inverse(self._h, a, o, _stream_handle(stream)))
         return f
 
+    # ---------------------------------------------------------------- denoising (Sect. 4.2)
+    def noise_std(self, j):
+        """sigma^j / sigma for scale j (j = -1: the scaling function)."""
+        r = ctypes.c_double()
+        check("s2let_wav_noise_std", _lib.lib().s2let_wav_noise_std(self._h, j, ctypes.byref(r)))
+        return r.value
+
+    def threshold(self, f_wav, sigma, nsigma=3.0, stream=None):
+        """Hard thresholding of the wavelet maps in place: |W^j| < nsigma sigma^j -> 0."""
+        w = self._chk(f_wav, self.wav_elems, "f_wav")
+        check("s2let_wav_threshold", _lib.lib().s2let_wav_threshold(self._h, w, float(sigma), float(nsigma),
+                                                                     _stream_handle(stream)))
+        return f_wav
+
+    def denoise(self, y, sigma, nsigma=3.0, out=None, stream=None):
+        """Analysis, hard thresholding of the wavelet maps (the scaling maps are
+        kept), synthesis: the denoising of Sect. 4.2."""
+        f_wav, f_scal = self.analysis(y, stream=stream)
+        self.threshold(f_wav, sigma, nsigma, stream=stream)
+        return self.synthesis(f_wav, f_scal, out, stream=stream)
+
 
 class BatchPlan:
     """Maps of uneven band-limit L_i and dilation B_i (same J_min, real/complex and
