@@ -191,3 +191,18 @@ def test_bspline_k_shape():
     ts = np.linspace(0.0, t_end, 33)
     ks = [kernels.k_bspline(t, lam, L, J) for t in ts]
     assert all(a > b for a, b in zip(ks[:-1], ks[1:]))
+
+
+@pytest.mark.parametrize("L,B,J0", [(128, 3, 2), (256, 2, 1), (1024, 2, 2)])
+def test_bspline_peaks_match_scale_discretised(L, B, J0):
+    """The footnote of Sect. 2.2 chooses k so that the j-th B-spline filter peaks at
+    about the scale of the j-th scale-discretised filter: the peak degrees agree
+    within 30% at every scale (a wrong power of lambda in k would move them by a
+    factor lambda)."""
+    l = np.arange(L)
+    norm = np.sqrt((2 * l + 1) / (4 * np.pi))
+    _, psi_sd = wavelet.tables(L, B, J0, "sd")
+    _, psi_bs = wavelet.tables(L, B, J0, "bspline")
+    for a, b in zip(psi_sd, psi_bs):
+        pa, pb = int(np.argmax(a / norm)), int(np.argmax(b / norm))
+        assert 0.8 <= pb / max(pa, 1) <= 1.3
