@@ -258,3 +258,16 @@ def test_denoising_raises_snr():
     assert 4.0 < snr_y < 6.0
     d = wavelet.denoise(y, sigma, L, B, J0, multires=True, real=True)
     assert wavelet.snr_db(s, d, L) > snr_y + 5.0
+
+
+@pytest.mark.parametrize("L,B,J0,multires,real", [(24, 2, 1, True, True), (20, 3, 0, True, False),
+                                                  (16, 2, 0, False, True)])
+def test_bspline_adjoint_dot_product(L, B, J0, multires, real):
+    """<A x, y> = <x, A^T y> for the B-spline transform, with its own band-limits."""
+    x = inputs.random_map((L, 2 * L - 1), 51, real=real)
+    fw, fs = wavelet.analysis(x, L, B, J0, multires, real, kernel="bspline")
+    gw = [inputs.random_map(w.shape, 60 + i, real=real) for i, w in enumerate(fw)]
+    gs = inputs.random_map(fs.shape, 59, real=real)
+    lhs = sum(np.vdot(g, w) for g, w in zip(gw, fw)) + np.vdot(gs, fs)
+    rhs = np.vdot(wavelet.analysis_adjoint(gw, gs, L, B, J0, multires, real, kernel="bspline"), x)
+    assert lhs == pytest.approx(rhs, rel=1e-12)
