@@ -247,6 +247,20 @@ int s2let_plan_tuning(const s2let_plan *plan, int N, int *tc_quad, int *tc_anal,
 #define S2LET_NOALLOC_SCRATCH_BYTES (8u << 20)
 int s2let_sht_inverse_noalloc(int L, int batch, int flags, const void *flm, void *f, void *stream);
 
+/* Host-only queries (no plan, no GPU), the tables a plan with these arguments uses:
+ * s2let_wav_bandlimits: *N_scal and N_wav[0 .. J-J_min] (N_wav may be NULL,
+ *   else it must hold n_wav_cap >= J - J_min + 1 entries) are the band-limits of
+ *   the scaling map and of scales J_min..J under `flags` (S2LET_MULTIRES,
+ *   S2LET_KERNEL_BSPLINE; Sect. 3.1).  Returns the number of scales J - J_min + 1,
+ *   or S2LET_ERR_ARG (L < 2, B < 2, J_min outside [0, J), unknown flag bits, a
+ *   too short N_wav).
+ * s2let_wav_kernel: fac[l], l < L, the kernel factor sqrt(4 pi/(2l+1)) Psi^j_l0
+ *   of scale j (J_min <= j <= J) or sqrt(4 pi/(2l+1)) Phi_l0 (j = -1) of the
+ *   family `flags` selects (Sect. 2.2); fac holds L doubles (caller-owned).
+ *   S2LET_ERR_ARG as above, for L > 65536, or for j outside {-1, J_min..J}. */
+int s2let_wav_bandlimits(int L, int B, int J_min, int flags, int *N_scal, int *N_wav, int n_wav_cap);
+int s2let_wav_kernel(int L, int B, int J_min, int flags, int j, double *fac);
+
 /* Wavelet denoising by hard thresholding (Sect. 4.2).
  *
  * s2let_wav_noise_std: *ratio = sigma^j / sigma = sqrt(sum_l |Psi^j_l0|^2), the

@@ -56,6 +56,8 @@ SIGNATURES = {
     "s2let_batch_map_layout": (_i, [_vp, _i, _i64p, _i64p, _ip, _ip]),
     "s2let_batch_group_plan": (_i, [_vp, _i, ctypes.POINTER(_vp), _i64p, _i64p, _i64p]),
     "s2let_batch_round_trip": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "s2let_wav_bandlimits": (_i, [_i, _i, _i, _i, _ip, _ip, _i]),
+    "s2let_wav_kernel": (_i, [_i, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_double)]),
     "s2let_wav_noise_std": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double)]),
     "s2let_wav_threshold": (_i, [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp]),
     "s2let_strerror": (ctypes.c_char_p, [_i]),

@@ -161,6 +161,36 @@ double bspline_kappa(int l, int B, int j, int L, int J)
     return std::sqrt(std::max(0.0, d));
 }
 
+void wav_bandlimits(int L, int B, int J0, int J, bool multires, bool bspline, int *n_scal, std::vector<int> &n_wav)
+{
+    auto ipow = [](long long b, int e) {
+        long long r = 1;
+        for (int i = 0; i < e; ++i) r = std::min<long long>(r * b, 1LL << 40);
+        return r;
+    };
+    auto cap = [&](int e) -> int {               // min(L, ceil(L / B^e)), e may be <= 0
+        if (e <= 0) return L;
+        const long long d = ipow(B, e);
+        return (int)std::min<long long>(L, (L + d - 1) / d);
+    };
+    *n_scal = !multires ? L : bspline ? cap(J - J0 - 1) : (int)std::min<long long>(L, ipow(B, J0));
+    n_wav.clear();
+    for (int j = J0; j <= J; ++j)
+        n_wav.push_back(!multires ? L : bspline ? cap(J - j - 2) : (int)std::min<long long>(L, ipow(B, j + 1)));
+}
+
+void wav_kernel(int L, int B, int J0, int J, bool bspline, int k, std::vector<double> &fac)
+{
+    fac.assign(L, 0.0);
+    for (int l = 0; l < L; ++l) {
+        if (bspline)
+            fac[l] = (k == 0) ? bspline_eta(l, B, J0, L, J) : bspline_kappa(l, B, J0 + k - 1, L, J);
+        else
+            fac[l] = (k == 0) ? eta_lambda(l / std::pow((double)B, J0), B)
+                              : kappa_lambda(l / std::pow((double)B, J0 + k - 1), B);
+    }
+}
+
 int jmax(int L, int B)
 {
     int J = 0;

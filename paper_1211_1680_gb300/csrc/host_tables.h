@@ -28,6 +28,16 @@ double bspline_k(double t, double lam, int L, int J);
 // all maps sum to one for every l (exact reconstruction)
 double bspline_eta(int l, int B, int J0, int L, int J);
 double bspline_kappa(int l, int B, int j, int L, int J);
+
+// Band-limits of the scaling map and of wavelet scales J0..J (Sect. 3.1): every
+// map at L without multiresolution; otherwise min(L, B^J0) and min(L, B^(j+1))
+// for the smooth family, min(L, ceil(L / B^(J-J0-1))) and min(L, ceil(L /
+// B^(J-j-2))) for the B-spline family (the ends of the kernels' supports).
+void wav_bandlimits(int L, int B, int J0, int J, bool multires, bool bspline, int *n_scal, std::vector<int> &n_wav);
+// Kernel factors of map k for degrees l < L: k = 0 the scaling function,
+// sqrt(4 pi/(2l+1)) Phi_l0 = eta(l / B^J0); k >= 1 scale j = J0 + k - 1,
+// sqrt(4 pi/(2l+1)) Psi^j_l0 = kappa(l / B^j) (Sect. 2.2).
+void wav_kernel(int L, int B, int J0, int J, bool bspline, int k, std::vector<double> &fac);
 int jmax(int L, int B);
 
 // Per band-limit tables (see fft.cuh and legendre.cuh for their meaning);

@@ -757,24 +757,10 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
     p->tc_split = (flags & S2LET_TC_SPLIT3) ? 3 : 2;
     p->quad_gemm = (prec == S2LET_PREC_FP32 || p->tc) && !(flags & S2LET_QUAD_FFT64);
     // band-limits (Sect. 3.1)
-    auto ipow = [](long long b, int e) {
-        long long r = 1;
-        for (int i = 0; i < e; ++i) r = std::min<long long>(r * b, 1LL << 40);
-        return r;
-    };
-    // B-spline family: scale j is band-limited by the end of its kernel's support,
-    // min(L, ceil(L / B^(J-j-2))), the scaling map by min(L, ceil(L / B^(J-J0-1)))
     const bool bspline = (flags & S2LET_KERNEL_BSPLINE) != 0;
-    auto cap = [&](int e) -> int {
-        if (e <= 0) return L;
-        const long long d = ipow(B, e);
-        return (int)std::min<long long>(L, (L + d - 1) / d);
-    };
-    p->n_scal = !p->multires ? L : bspline ? cap(J - J0 - 1) : (int)std::min<long long>(L, ipow(B, J0));
+    s2h::wav_bandlimits(L, B, J0, J, p->multires, bspline, &p->n_scal, p->n_wav);
     int64_t off = 0;
-    for (int j = J0; j <= J; ++j) {
-        const int N = !p->multires ? L : bspline ? cap(J - j - 2) : (int)std::min<long long>(L, ipow(B, j + 1));
-        p->n_wav.push_back(N);
+    for (int N : p->n_wav) {
         p->wav_off.push_back(off);
         off += map_elems(p.get(), N) * batch;
     }
@@ -806,14 +792,8 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
     if (err) return err;
     // kernel factors sqrt(4 pi/(2l+1)) Phi_l0 = eta(l / B^J0), sqrt(4 pi/(2l+1)) Psi^j_l0 = kappa(l / B^j)
     for (int k = 0; k <= J - J0 + 1; ++k) {
-        std::vector<double> fac(L);
-        for (int l = 0; l < L; ++l) {
-            if (bspline)
-                fac[l] = (k == 0) ? s2h::bspline_eta(l, B, J0, L, J) : s2h::bspline_kappa(l, B, J0 + k - 1, L, J);
-            else
-                fac[l] = (k == 0) ? s2h::eta_lambda(l / std::pow((double)B, J0), B)
-                                  : s2h::kappa_lambda(l / std::pow((double)B, J0 + k - 1), B);
-        }
+        std::vector<double> fac;
+        s2h::wav_kernel(L, B, J0, J, bspline, k, fac);
         // white noise of unit harmonic variance has, in this map, the per-sample
         // variance sum_l |Psi_l0|^2 = sum_l (2l+1)/(4 pi) fac_l^2 (Eq. noisemodel)
         double v = 0.0;
@@ -1128,6 +1108,39 @@ int s2let_plan_tuning(const s2let_plan *p, int N, int *tc_quad, int *tc_anal, in
     if (tc_anal) *tc_anal = p->tc && bd.tc_anal;
     if (tc_synth) *tc_synth = p->tc && bd.tc_synth;
     if (fft_threads_out) *fft_threads_out = bd.fft_th ? bd.fft_th : fft_threads(bd.M);
+    return S2LET_OK;
+}
+
+int s2let_wav_bandlimits(int L, int B, int J_min, int flags, int *N_scal, int *N_wav, int n_wav_cap)
+{
+    if (L < 2 || B < 2 || (flags & ~(S2LET_COMPLEX | S2LET_MULTIRES | S2LET_PREC_MASK | S2LET_QUAD_FFT64 |
+                                     S2LET_TC_SPLIT3 | S2LET_KERNEL_BSPLINE)))
+        return S2LET_ERR_ARG;
+    const int J = s2h::jmax(L, B);
+    if (J_min < 0 || J_min >= J) return S2LET_ERR_ARG;
+    const int ns = J - J_min + 1;
+    if (N_wav && n_wav_cap < ns) return S2LET_ERR_ARG;
+    int nsc = 0;
+    std::vector<int> nw;
+    s2h::wav_bandlimits(L, B, J_min, J, (flags & S2LET_MULTIRES) != 0, (flags & S2LET_KERNEL_BSPLINE) != 0, &nsc,
+                        nw);
+    if (N_scal) *N_scal = nsc;
+    if (N_wav)
+        for (int i = 0; i < ns; ++i) N_wav[i] = nw[i];
+    return ns;
+}
+
+int s2let_wav_kernel(int L, int B, int J_min, int flags, int j, double *fac)
+{
+    if (L < 2 || L > (1 << 16) || B < 2 || !fac || (flags & ~(S2LET_COMPLEX | S2LET_MULTIRES | S2LET_PREC_MASK |
+                                                             S2LET_QUAD_FFT64 | S2LET_TC_SPLIT3 |
+                                                             S2LET_KERNEL_BSPLINE)))
+        return S2LET_ERR_ARG;
+    const int J = s2h::jmax(L, B);
+    if (J_min < 0 || J_min >= J || (j != -1 && (j < J_min || j > J))) return S2LET_ERR_ARG;
+    std::vector<double> f;
+    s2h::wav_kernel(L, B, J_min, J, (flags & S2LET_KERNEL_BSPLINE) != 0, j == -1 ? 0 : j - J_min + 1, f);
+    std::copy(f.begin(), f.end(), fac);
     return S2LET_OK;
 }
 
