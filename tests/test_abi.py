@@ -65,3 +65,11 @@ def test_flag_constants_match_header():
     for k in ("S2LET_COMPLEX", "S2LET_MULTIRES", "S2LET_PREC_FP32", "S2LET_PREC_TF32X3", "S2LET_QUAD_FFT64",
               "S2LET_TC_SPLIT3", "S2LET_KERNEL_BSPLINE", "S2LET_ERR_ARG"):
         assert getattr(_lib, k) == defs[k], k
+
+
+def test_binding_rejects_unknown_kernel_family_without_gpu():
+    from paper_1211_1680_gb300.s2let import BatchPlan, Plan
+    with pytest.raises(ValueError):
+        Plan(32, 2, 0, kernel="needlet")
+    with pytest.raises(ValueError):
+        BatchPlan([32], [2], 0, kernel="spline")
