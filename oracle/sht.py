@@ -271,24 +271,6 @@ def forward_m(f, N, m):
     return (2.0 * math.pi / P) * out
 
 
-def inverse_m(xlm, N, m, ts=None):
-    """Order-m part of the inverse transform before the ring DFT:
-    F_m(theta_t) = sum_{l=|m|}^{N-1} x_l lambda_lm(theta_t); xlm[l - |m|] = x_l."""
-    ts = np.arange(N) if ts is None else np.asarray(ts)
-    s, sg, yy = sin_cos_theta(N, ts)
-    am = abs(m)
-    sgn = (-1.0) ** am if m < 0 else 1.0
-    out = np.zeros(len(ts), dtype=complex)
-    for i in range(len(ts)):
-        out[i] = sgn * np.dot(legendre_column(am, N, s[i], sg[i], yy[i]), xlm)
-    return out
-
-
-def ring_synthesis_m(Fm, N, m):
-    """The order-m term of the inverse ring DFT: F_m(theta_t) e^{i m phi_p}, shape (N, 2N-1)."""
-    return np.outer(Fm, _phase_m_phi([m], np.arange(2 * N - 1), 2 * N - 1)[0])
-
-
 # ---------------------------------------------------------------- adjoints
 def inverse_adjoint(g, N):
     """Conjugate transpose of inverse(): out_lm = sum_{t,p} g(theta_t, phi_p)

@@ -194,3 +194,32 @@ def test_transform_adjoints(N):
     lhs = np.vdot(x, sht.forward(g, N))
     rhs = np.vdot(sht.forward_adjoint(x, N), g)
     assert lhs == pytest.approx(rhs, rel=1e-13)
+
+
+@pytest.mark.parametrize("N", [1, 7, 33])
+def test_inverse_at_matches_full_grid(N):
+    """inverse_at (the checker of the full-size GPU maps) selects the right rings
+    and longitudes: it equals the full inverse transform on the same grid points,
+    with rings and longitudes scattered, repeated and out of order."""
+    flm = inputs.random_flm(N, 70 + N, real=False)
+    full = sht.inverse(flm, N)
+    rng = np.random.default_rng(N)
+    ts = rng.integers(0, N, size=min(N, 5) + 1)
+    ps = rng.integers(0, 2 * N - 1, size=min(2 * N - 1, 9) + 1)
+    got = sht.inverse_at(flm, N, ts, ps)
+    assert got.shape == (len(ts), len(ps))
+    assert np.max(np.abs(got - full[ts][:, ps])) < 1e-13
+
+
+def test_inverse_at_against_scipy():
+    """inverse_at at scattered grid points against the direct sum of scipy's Y_lm."""
+    N = 14
+    flm = inputs.random_flm(N, 5, real=False)
+    ts, ps = np.array([13, 0, 6, 6, 2]), np.array([26, 3, 0, 11])
+    th = np.pi * (2 * ts + 1) / (2 * N - 1)
+    ph = 2 * np.pi * ps / (2 * N - 1)
+    ref = np.zeros((len(ts), len(ps)), complex)
+    for l in range(N):
+        for m in range(-l, l + 1):
+            ref += flm[l * l + l + m] * special.sph_harm_y(l, m, th[:, None], ph[None, :])
+    assert np.max(np.abs(sht.inverse_at(flm, N, ts, ps) - ref)) < 1e-13
