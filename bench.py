@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--kernel", choices=["sd", "bspline"], default="sd",
                     help="generating functions: smooth scale-discretised (sd) or cubic B-spline")
     ap.add_argument("--denoise", action="store_true",
-                    help="each step denoises (Sect. 4.2): analysis, hard thresholding of the wavelet maps at "
+                    help="each step denoises (Sect. 4.3): analysis, hard thresholding of the wavelet maps at "
                          "3 sigma^j, synthesis")
     ap.add_argument("--full-res", action="store_true",
                     help="every wavelet and scaling map at L (the full-resolution transform) instead of the "

@@ -219,26 +219,30 @@ int s2let_plan_tuning(const s2let_plan *plan, int N, int *tc_quad, int *tc_anal,
                       int *fft_threads);
 
 /* ---- allocation-free inverse transform (no counterpart in the paper) -----
- * For callers that cannot allocate device memory: code that runs while a
- * stream is being captured (cudaMalloc is not allowed then), applications
- * whose device memory is handed out once by a framework or a fixed budget, and
- * real-time or embedded hosts that forbid allocation after start-up.  It
- * computes the same inverse MW transform as s2let_sht_inverse of an FP32 plan
- * (Eq. harmonicssynthesis, Sect. 2.1) without a plan and without calling
+ * For callers that cannot allocate device memory: applications whose device
+ * memory is handed out once by a framework or a fixed budget (a cudaMalloc of
+ * their own would fail or break that accounting), plug-ins that run inside a
+ * host program which owns the allocator, and real-time or embedded hosts that
+ * forbid allocation after start-up.  It computes the same inverse MW transform
+ * as s2let_sht_inverse of an FP32 plan, without a plan and without calling
  * cudaMalloc, cudaFree or any allocating library routine: its tables and work
  * buffers live in one statically sized device array inside the library
  * (S2LET_NOALLOC_SCRATCH_BYTES), which every GPU that loads the library holds
  * until the process exits.
  *   L:      band-limit, 2 <= L <= S2LET_NOALLOC_MAX_L (else S2LET_ERR_ARG)
  *   batch:  number of maps, 1 <= batch <= S2LET_NOALLOC_MAX_BATCH (else S2LET_ERR_ARG)
- *   flags:  S2LET_PREC_FP32, optionally | S2LET_COMPLEX (anything else: S2LET_ERR_ARG)
+ *   flags:  S2LET_PREC_FP32, optionally | S2LET_COMPLEX (any other bit: S2LET_ERR_ARG)
  *   flm:    device, batch x L*L complex float (index l*l + l + m), read only
  *   f:      device, batch maps of L x (2L-1) float (complex: interleaved), written
  * Set-up: the first call on a device, and every call whose (L, batch, complex)
- * differs from the previous call on that device, looks up the array's device
- * address (cudaGetSymbolAddress), copies tables into it and computes Legendre
- * seeds, synchronising the device; make that first call before any stream
- * capture.  The other calls only launch kernels on `stream`.
+ * differs from the previous call on that device, first waits for all work
+ * already queued on the device (cudaDeviceSynchronize: kernels of earlier
+ * calls, on any stream, still read the tables), then looks up the array's
+ * device address (cudaGetSymbolAddress), copies tables into it and computes
+ * Legendre seeds, synchronising the device again.  Make that first call before
+ * any stream capture; a call that needs the set-up while `stream` is being
+ * captured returns S2LET_ERR_UNSUPPORTED and does nothing.  The other calls
+ * only launch kernels on `stream`.
  * The array is shared by every call on a device and keeps the last call's
  * contents; calls whose kernels overlap on the GPU (different streams, no
  * ordering) race on it and must be serialised by the caller. */
@@ -261,7 +265,7 @@ int s2let_sht_inverse_noalloc(int L, int batch, int flags, const void *flm, void
 int s2let_wav_bandlimits(int L, int B, int J_min, int flags, int *N_scal, int *N_wav, int n_wav_cap);
 int s2let_wav_kernel(int L, int B, int J_min, int flags, int j, double *fac);
 
-/* Wavelet denoising by hard thresholding (Sect. 4.2).
+/* Wavelet denoising by hard thresholding (Sect. 4.3).
  *
  * s2let_wav_noise_std: *ratio = sigma^j / sigma = sqrt(sum_l |Psi^j_l0|^2), the
  *   standard deviation in scale j (j = -1: the scaling function Phi) of zero-mean
@@ -277,7 +281,7 @@ int s2let_wav_kernel(int L, int B, int J_min, int flags, int j, double *fac);
  *   precision on T^j rounded to it (complex: re*re + im*im < T*T, each operation
  *   rounded to nearest).  One kernel launch on `stream`; S2LET_ERR_ARG for a
  *   negative or non-finite sigma or nsigma or a NULL pointer.
- * Denoising (Sect. 4.2) is s2let_analysis, s2let_wav_threshold on f_wav, then
+ * Denoising (Sect. 4.3) is s2let_analysis, s2let_wav_threshold on f_wav, then
  * s2let_synthesis with the unchanged f_scal. */
 int s2let_wav_noise_std(const s2let_plan *plan, int j, double *ratio);
 int s2let_wav_threshold(s2let_plan *plan, void *f_wav, double sigma, double nsigma, void *stream);

@@ -118,7 +118,7 @@ def analysis_adjoint(g_wav, g_scal, L, B, J0, multires=True, real=True, kernel="
     return out.real.copy() if real else out
 
 
-# ---------------------------------------------------------------- denoising (Sect. 4.2)
+# ---------------------------------------------------------------- denoising (Sect. 4.3)
 def noise_std(L, B, J0, kernel="sd"):
     """(sigma^Phi / sigma, [sigma^j / sigma for j = J0..J]): the standard deviation,
     per unit harmonic noise variance, of white noise in the scaling map and in
@@ -136,7 +136,7 @@ def hard_threshold(f_wav, sigma, L, B, J0, nsigma=3.0, kernel="sd"):
 
 
 def denoise(y, sigma, L, B, J0, multires=True, real=True, nsigma=3.0, kernel="sd"):
-    """Sect. 4.2: wavelet analysis of the noisy map, hard thresholding of the wavelet
+    """Sect. 4.3: wavelet analysis of the noisy map, hard thresholding of the wavelet
     maps (the scaling map is kept), synthesis."""
     f_wav, f_scal = analysis(y, L, B, J0, multires, real, kernel=kernel)
     d_wav = hard_threshold(f_wav, sigma, L, B, J0, nsigma, kernel)
@@ -144,7 +144,7 @@ def denoise(y, sigma, L, B, J0, multires=True, real=True, nsigma=3.0, kernel="sd
 
 
 def snr_db(s, y, L):
-    """SNR(y) = 10 log10(||s||^2 / ||y - s||^2) with ||.||^2 the sum of |f_lm|^2 (Sect. 4.2)."""
+    """SNR(y) = 10 log10(||s||^2 / ||y - s||^2) with ||.||^2 the sum of |f_lm|^2 (Sect. 4.3)."""
     ds = sht.forward(s, L)
     dn = sht.forward(y - s, L)
     return 10.0 * math.log10(float(np.sum(np.abs(ds) ** 2)) / float(np.sum(np.abs(dn) ** 2)))

@@ -96,8 +96,12 @@ template <typename T> int put(unsigned char *dst, const std::vector<T> &h)
 }
 
 // Fill the tables for band-limit L into the scratch of the current device.
+// Earlier calls may still have kernels in flight that read the old tables (on
+// any stream, including a non-blocking one that the copies below would not
+// wait for), so the whole device is drained first.
 int setup(DevState &d, int L, int batch, int cplx)
 {
+    if (cudaDeviceSynchronize() != cudaSuccess) return S2LET_ERR_CUDA;
     if (!d.base) {
         void *ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) return S2LET_ERR_CUDA;
@@ -172,7 +176,7 @@ extern "C" int s2let_sht_inverse_noalloc(int L, int batch, int flags, const void
     if (L < 2 || L > S2LET_NOALLOC_MAX_L || batch < 1 || batch > S2LET_NOALLOC_MAX_BATCH || !flm || !f)
         return S2LET_ERR_ARG;
     if ((flags & S2LET_PREC_MASK) != S2LET_PREC_FP32) return S2LET_ERR_ARG;
-    if (flags & ~(S2LET_COMPLEX | S2LET_MULTIRES | S2LET_PREC_MASK)) return S2LET_ERR_ARG;
+    if (flags & ~(S2LET_COMPLEX | S2LET_PREC_MASK)) return S2LET_ERR_ARG;
     const int cplx = (flags & S2LET_COMPLEX) ? 1 : 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return S2LET_ERR_CUDA;
@@ -181,6 +185,10 @@ extern "C" int s2let_sht_inverse_noalloc(int L, int batch, int flags, const void
     std::lock_guard<std::mutex> lock(g_mu);
     DevState &d = g_dev[dev];
     if (d.L != L || d.batch != batch || d.cplx != cplx) {
+        // the set-up copies and synchronises, which a stream capture does not allow
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+            return S2LET_ERR_UNSUPPORTED;
         const int e = setup(d, L, batch, cplx);
         if (e) {
             d.L = 0;

@@ -934,7 +934,7 @@ template <typename R> int autotune_t(s2let_plan *p, cudaStream_t st)
 
 namespace {
 
-// ---------------------------------------------------------------- hard thresholding (Sect. 4.2)
+// ---------------------------------------------------------------- hard thresholding (Sect. 4.3)
 // The samples of scale s (R values of a real map, (re, im) pairs of a complex
 // map) are [begin[s], begin[s+1]) of the wavelet buffer; each is set to zero
 // where its modulus is below thr[s] (Eq. threshold).  Complex samples compare

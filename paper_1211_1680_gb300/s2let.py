@@ -195,7 +195,7 @@ class Plan:
         check("s2let_sht_inverse", _lib.lib().s2let_sht_inverse(self._h, a, o, _stream_handle(stream)))
         return f
 
-    # ---------------------------------------------------------------- denoising (Sect. 4.2)
+    # ---------------------------------------------------------------- denoising (Sect. 4.3)
     def noise_std(self, j):
         """sigma^j / sigma for scale j (j = -1: the scaling function)."""
         r = ctypes.c_double()
@@ -211,7 +211,7 @@ class Plan:
 
     def denoise(self, y, sigma, nsigma=3.0, out=None, stream=None):
         """Analysis, hard thresholding of the wavelet maps (the scaling maps are
-        kept), synthesis: the denoising of Sect. 4.2."""
+        kept), synthesis: the denoising of Sect. 4.3."""
         f_wav, f_scal = self.analysis(y, stream=stream)
         self.threshold(f_wav, sigma, nsigma, stream=stream)
         return self.synthesis(f_wav, f_scal, out, stream=stream)

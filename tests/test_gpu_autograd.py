@@ -44,7 +44,7 @@ def test_gradient_against_finite_differences():
             assert abs(fd.item() - an.item()) <= 1e-6 * abs(an.item()) + fd_noise
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5), ("tf32x3", 1e-5)])
 def test_gradient_against_oracle_adjoint(prec, tol):
     """L = 256: dLoss/df = A^T (2 w_j W^j) with the oracle's analysis and adjoint."""
     L, B, J0 = 256, 2, 2

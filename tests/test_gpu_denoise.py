@@ -1,4 +1,4 @@
-"""GPU: wavelet denoising by hard thresholding (Sect. 4.2) through the C ABI
+"""GPU: wavelet denoising by hard thresholding (Sect. 4.3) through the C ABI
 against the oracle: the per-scale noise standard deviations (Eq. noisemodel),
 the threshold decisions (Eq. threshold; bit-exact, taken in the plan's
 precision on both sides) and the denoised map."""

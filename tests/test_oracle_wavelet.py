@@ -107,7 +107,7 @@ def test_adjoint_dense_transpose():
 
 
 def test_white_noise_variance():
-    """Wavelet-space noise (Sect. 4.2): for white harmonic noise of variance
+    """Wavelet-space noise (Sect. 4.3): for white harmonic noise of variance
     sigma^2, E|W^j|^2 = sigma^2 sum_l |Psi^j_l0|^2 at every sample.  Averaged over
     the samples of several realisations it must agree to a few per cent."""
     L, B, J0 = 64, 2, 2
@@ -184,7 +184,7 @@ def test_bspline_multires_matches_full_resolution():
         assert np.max(np.abs(lm_f[n * n:])) < 1e-13 if n < L else True
 
 
-# ---------------------------------------------------------------- denoising (Sect. 4.2)
+# ---------------------------------------------------------------- denoising (Sect. 4.3)
 @pytest.mark.parametrize("L,B,J0,kernel", [(32, 2, 0, "sd"), (64, 3, 1, "sd"), (48, 2, 1, "bspline")])
 def test_noise_std_closed_form(L, B, J0, kernel):
     """By admissibility the squared noise ratios of all maps sum to
@@ -248,7 +248,7 @@ def spot_signal(L, spots=((0.9, 1.0, 1.0), (2.0, 4.0, -0.8), (1.4, 2.5, 0.6)), w
 def test_denoising_raises_snr():
     """Localised spots plus white noise of harmonic variance sigma^2 (Eq. noisevar)
     at SNR(y) near 5 dB: hard thresholding at 3 sigma^j (Eq. threshold) removes
-    most of the noise and raises the SNR by several dB (Sect. 4.2)."""
+    most of the noise and raises the SNR by several dB (Sect. 4.3)."""
     L, B, J0 = 32, 2, 0
     s = spot_signal(L)
     energy = float(np.sum(np.abs(sht.forward(s, L)) ** 2))
