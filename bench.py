@@ -33,13 +33,22 @@ METRIC = "wavelet round-trips/s, L=2048x64 maps, vs plain FP64 GPU path; max err
 UNIT = "map round-trips/s"
 SM_COUNT = 152
 FP32_LANES = 128
-TF32_PER_BF16 = 1.1 / 2.25      # nominal dense tensor rates (PFLOP/s per GPU)
-FLOPS_COUNTED = {
-    "leg_anal": "4 per (l, m, ring, map) product + 4 per recurrence value (l, m, ring)",
-    "leg_synth": "4 per (l, m, ring, map) product + 4 per recurrence value (l, m, ring)",
-    "theta_quad": "2 N^2 per real column (2 per map and order): the dense product G = Q F",
+FP64_FMA_PER_SM = 2            # FP64 FMA per clock per SM (GB300: 1.25 TFLOP/s FP64 nominal)
+TF32_PER_BF16 = 1.1 / 2.25     # nominal dense tensor rates (PFLOP/s per GPU)
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+# what each stage's algorithmic work is (the method's, not the kernels'):
+WORK = {
+    "ring_fwd": "bytes: the map read and its order-major spectrum F_m(theta_t) written",
+    "ring_inv": "bytes: the order-major spectrum read and the map written",
+    "theta_quad": "bytes: F_m(theta_t) read and G_m(theta_t) written (an O(N^2 log N) stage)",
+    "leg_anal": "flops: 4 per (l, m, ring, map) product of the contraction",
+    "leg_synth": "flops: 4 per (l, m, ring, map) product of the contraction",
+    "pack": "bytes: none counted (layout conversion of f_lm)",
 }
-
+# DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) per step of a
+# stage, for the kernels as they are now; a stage missing here has no capture
+# of its current kernels, and its traffic is reported as null
+TRAFFIC = {}
 
 # noise level of the --denoise steps: white noise of this harmonic standard
 # deviation would be thresholded at 3 sigma^j; against the C_l = 1/(l(l+1)) maps
@@ -69,8 +78,9 @@ def parse():
                     help="every wavelet and scaling map at L (the full-resolution transform) instead of the "
                          "multiresolution band-limits min(L, B^(j+1))")
     ap.add_argument("--fp64-batch", type=int, default=8)
+    ap.add_argument("--fp64-trips", type=int, default=3, help="timed round trips of the plain FP64 GPU path")
     ap.add_argument("--cpu-orders", type=int, default=128)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
                     help="autotune the plan (kernel choice per stage and band-limit) before the warm-up")
     ap.add_argument("--skip-fp64", action="store_true")
@@ -224,6 +234,87 @@ def run_reference(a, rank):
     return 0
 
 
+# ---------------------------------------------------------------- rooflines
+def peak_table(peaks):
+    """Peaks used for the roofline fractions: measured where the driver wrote
+    them (MEASURED_PEAKS.json), else the fallback figures; each with its source."""
+    def get(k):
+        if k in peaks:
+            return float(peaks[k]), "of measured"
+        return FALLBACK[k], "of fallback"
+    hbm, hsrc = get("hbm_gbs")
+    bf, bsrc = get("bf16_tflops_sustained")
+    mhz, msrc = get("sm_max_mhz")
+    return {
+        "hbm": (hbm, "GB/s", "HBM copy bandwidth hbm_gbs %.0f GB/s (%s)" % (hbm, hsrc)),
+        "tf32": (bf * TF32_PER_BF16, "TFLOP/s",
+                 "TF32 dense = bf16_tflops_sustained %.1f (%s) x 1.1/2.25 (nominal TF32/BF16 ratio)" % (bf, bsrc)),
+        "fp32": (SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12, "TFLOP/s",
+                 "derived: %d SMs x %d FP32 lanes x 2 flop/FMA x %.0f MHz (%s)" % (SM_COUNT, FP32_LANES, mhz, msrc)),
+        "fp64": (SM_COUNT * FP64_FMA_PER_SM * 2 * mhz * 1e6 / 1e12, "TFLOP/s",
+                 "derived: %d SMs x %d FP64 FMA/clk x 2 flop x %.0f MHz (%s)" % (SM_COUNT, FP64_FMA_PER_SM, mhz, msrc)),
+    }
+
+
+def plan_bandlimits(plan):
+    """Band-limits of the transforms in one round trip: each direction runs one
+    SHT at L and one per wavelet or scaling map."""
+    return [plan.L] + [n for (_, n, _, _) in plan.scales] + [plan.N_scal]
+
+
+def stage_roofline(name, st, steps, precision, pk, batch):
+    """Roofline record of one stage from its per-stage statistics: achieved =
+    algorithmic work / device time (all launches of the stage, so the average
+    over its launches weighted by their duration)."""
+    sec = st["ms"] / 1000.0
+    if sec <= 0:
+        return None
+    rec = {"ms_per_step": st["ms"] / steps, "launches_per_step": st["launches"] / steps, "work": WORK.get(name, "")}
+    if st["flops"] > 0:
+        key = {"tf32x3": "tf32", "fp32": "fp32", "fp64": "fp64"}[precision]
+        peak, unit, src = pk[key]
+        achieved = st["flops"] / sec / 1e12
+        rec.update(bound="tensor" if key == "tf32" else "alu", achieved=achieved, peak=peak, unit=unit,
+                   frac=achieved / peak, peak_source=src)
+        if key == "tf32":
+            rec["executed_mma_frac"] = 3.0 * achieved / peak
+            rec["executed_note"] = "split TF32 runs 3 MMAs per algorithmic product (hi*lo + lo*hi + hi*hi)"
+        # the three-term recurrence behind the products: 4 flops per lambda value; real
+        # maps share one value among the batch's maps (and re/im), so per step it is
+        # the contraction's count divided by the maps
+        rflops = st["flops"] / batch
+        rec["recurrence_tflops"] = rflops / sec / 1e12
+        rec["recurrence_frac_of_fp32_pipe"] = rflops / sec / 1e12 / pk["fp32"][0]
+    else:
+        peak, unit, src = pk["hbm"]
+        achieved = st["bytes"] / sec / 1e9
+        rec.update(bound="hbm", achieved=achieved, peak=peak, unit=unit, frac=achieved / peak, peak_source=src)
+    return rec
+
+
+def rooflines(stats, a, peaks, batch, bandlimits):
+    """(roofline of the dominant stage, Legendre sub-record, every stage's record)."""
+    pk = peak_table(peaks)
+    recs = {k: stage_roofline(k, v, a.steps, a.precision, pk, batch) for k, v in stats.items() if v["launches"]}
+    recs = {k: v for k, v in recs.items() if v is not None}
+    dom = max(recs, key=lambda k: recs[k]["ms_per_step"])
+    roof = dict(recs[dom])
+    roof["kernel"] = dom
+    tr = TRAFFIC.get(dom)
+    roof["traffic"] = tr["bytes_per_step"] if tr else None
+    if tr:
+        roof["traffic_note"] = tr["source"]
+    roof["note"] = "achieved and traffic are per step of the stage (all its launches)"
+    # the dense theta-quadrature products of FP32 / TF32X3 plans, as a labelled extra
+    if "theta_quad" in recs and a.precision != "fp64":
+        dense = sum(4.0 * n ** 3 * batch for n in bandlimits)   # forward SHTs: 2 N^2 per real column
+        recs["theta_quad"]["dense_equivalent_tflops"] = dense / (recs["theta_quad"]["ms_per_step"] / 1000) / 1e12
+        recs["theta_quad"]["dense_equivalent_note"] = ("if the stage ran as the dense product G = Q F at every "
+                                                       "band-limit: 2 N^2 flops per real column")
+    legendre = {k: recs[k] for k in ("leg_anal", "leg_synth") if k in recs}
+    return roof, legendre, recs
+
+
 # ---------------------------------------------------------------- GPU leg
 def check_errors(plan, x, fw, fs, out, flm, a):
     """Per-scale max relative error of map 0 against the oracle, on sampled rings:
@@ -278,11 +369,11 @@ def run_gpu(a, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     tuning = plan.autotune() if a.autotune else None
 
-    def step(src=x):
+    def step(src=x, dst=out):
         plan.analysis(src, fw, fs)
         if a.denoise:
             plan.threshold(fw, DENOISE_SIGMA)
-        plan.synthesis(fw, fs, out)
+        plan.synthesis(fw, fs, dst)
 
     for _ in range(a.warmup):
         step()
@@ -311,72 +402,7 @@ def run_gpu(a, rank, world, local_rank):
         ms = float(t.item())
     value = world * a.batch * a.steps / (ms / 1000.0)
 
-    # dominant kernel and its roofline
-    dom = max(stats, key=lambda k: stats[k]["ms"])
-    sd = stats[dom]
-    peaks = measured_peaks()
-    if sd["flops"] > 0 and a.precision == "tf32x3":
-        # a contraction stage on the tensor cores (split TF32: 3 MMAs per product).  Peak:
-        # TF32 dense from the measured sustained BF16 rate times the nominal TF32/BF16
-        # ratio (1.1 / 2.25 PFLOP/s), the stage being timed inside a long step
-        bf = peaks.get("bf16_tflops_sustained", 1700.0)
-        peak = bf * TF32_PER_BF16
-        achieved = sd["flops"] / (sd["ms"] / 1000.0) / 1e12 if sd["ms"] > 0 else 0.0
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": dom,
-                "peak_source": "TF32 dense = MEASURED_PEAKS.json bf16_tflops_sustained %.1f (of measured) x 1.1/2.25"
-                               % bf,
-                "flops_counted": FLOPS_COUNTED.get(dom, "") + " (algorithmic)",
-                "executed_mma_frac": 3.0 * achieved / peak,
-                "executed_note": "the split-TF32 product runs 3 MMAs per algorithmic multiply-add",
-                "avg_launch_ms": sd["ms"] / max(sd["timed"], 1)}
-        if dom == "theta_quad":
-            # DRAM bytes of one quadrature stage (two parity launches of k_quad_tcp): ncu measured
-            # 272.7 + 230.2 MB per launch at L = 1024, 64 maps (the F read and G written); the
-            # traffic grows with orders x rings x maps, i.e. L^2 x maps
-            roof["traffic"] = 2 * 502.9e6 * (a.L / 1024.0) ** 2 * a.batch / 64.0
-            roof["traffic_note"] = ("dram read+write per quadrature stage (2 launches), from one ncu capture at "
-                                    "L=1024 x 64 maps scaled by L^2 x maps; avg_launch_ms is per stage as well")
-        elif dom == "leg_anal":
-            # DRAM bytes of the full-band-limit analysis launch (k_leg_anal_tc): ncu measured
-            # 772.0 + 255.5 MB at L = 1024, 64 maps (G and the recurrence tables read, f_lm
-            # written); both grow with L^2 x maps.  The stage's launches at smaller band-limits
-            # (the wavelet synthesis) move less.
-            roof["traffic"] = 1027.5e6 * (a.L / 1024.0) ** 2 * a.batch / 64.0
-            roof["traffic_note"] = ("dram read+write of the full-band-limit launch, from one ncu capture at "
-                                    "L=1024 x 64 maps scaled by L^2 x maps")
-    elif sd["flops"] > 0:
-        # a contraction stage: FP32 (or FP64) FMA pipe; peak derived from unit counts and clock
-        mhz = peaks.get("sm_max_mhz", 2070.0)
-        if a.precision in ("fp32", "tf32x3"):
-            peak = SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12
-            pdesc = "derived: %d SMs x %d FP32 lanes x 2 flop/FMA x %.0f MHz (max SM clock)" % (
-                SM_COUNT, FP32_LANES, mhz)
-        else:
-            peak = SM_COUNT * 2 * 2 * mhz * 1e6 / 1e12
-            pdesc = "derived: %d SMs x 2 FP64 FMA/clk x 2 flop x %.0f MHz (assumed FP64 rate)" % (SM_COUNT, mhz)
-        achieved = sd["flops"] / (sd["ms"] / 1000.0) / 1e12 if sd["ms"] > 0 else 0.0
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": dom, "peak_source": pdesc,
-                "flops_counted": FLOPS_COUNTED.get(dom, ""),
-                "avg_launch_ms": sd["ms"] / max(sd["timed"], 1)}
-    else:
-        peak = peaks.get("hbm_gbs", 6800.0)
-        achieved = sd["bytes"] / (sd["ms"] / 1000.0) / 1e9 if sd["ms"] > 0 else 0.0
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": dom, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                "avg_launch_ms": sd["ms"] / max(sd["timed"], 1)}
-    # every contraction stage against the same pipe peak, for context
-    if a.precision == "tf32x3":
-        pipe = peaks.get("bf16_tflops_sustained", 1700.0) * TF32_PER_BF16
-    else:
-        pipe = roof["peak"] if roof["bound"] == "alu" else SM_COUNT * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) / 1e6
-    roof["all_stages"] = {k: {"ms_per_step": v["ms"] / a.steps,
-                              "tflops": (v["flops"] / (v["ms"] / 1000.0) / 1e12 if v["ms"] > 0 and v["flops"] else None),
-                              "frac_of_pipe": (v["flops"] / (v["ms"] / 1000.0) / 1e12 / pipe
-                                               if v["ms"] > 0 and v["flops"] else None),
-                              "gbs": (v["bytes"] / (v["ms"] / 1000.0) / 1e9 if v["ms"] > 0 and v["bytes"] else None)}
-                          for k, v in stats.items() if v["launches"]}
+    roof, legendre, all_stages = rooflines(stats, a, measured_peaks(), a.batch, plan_bandlimits(plan))
     total_ms = sum(s["ms"] for s in stats.values())
     stage_share = {k: {"share": (s["ms"] / total_ms if total_ms else 0.0), "ms_per_step": s["ms"] / a.steps,
                        "launches_per_step": s["launches"] / a.steps} for k, s in stats.items()}
@@ -386,34 +412,52 @@ def run_gpu(a, rank, world, local_rank):
            "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": {"fp32": "f32", "tf32x3": "tf32x3+f32", "fp64": "f64"}[a.precision], "data": "synthetic",
            "config": config(a),
-           "gpu_launches": launches, "roofline": roof, "stages": stage_share, "clocks": clk}
+           "gpu_launches": launches, "roofline": roof, "legendre": legendre, "stage_rooflines": all_stages,
+           "stages": stage_share, "clocks": clk}
     if tuning is not None:
         res["tuning"] = {str(n): t for n, t in tuning.items()}
 
-    # end to end: pinned host maps in, host maps out, copies inside the timed region
+    # end to end: pinned host maps in, host maps out, copies inside the timed region.
+    # Every step copies its input batch in and its result batch out; the copies of
+    # neighbouring steps run on two copy streams while a step computes
+    # (s2let.HostPipeline), so only the first copy-in and the last copy-out are exposed.
     if not a.skip_e2e:
+        from paper_1211_1680_gb300.s2let import HostPipeline
         xh = x.cpu().pin_memory()
-        oh = torch.empty_like(out, device="cpu").pin_memory()
-        xd = torch.empty_like(x)
-        step(xd.copy_(xh, non_blocking=True))
-        oh.copy_(out, non_blocking=True)
+        oh = [torch.empty_like(out, device="cpu").pin_memory() for _ in range(2)]
+        pipe = HostPipeline(x, out)
+
+        def e2e(n):
+            pipe.run(n, lambda k: xh, lambda k: oh[k % 2], lambda src, dst: step(src, dst))
+
+        e2e(2)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
-        for _ in range(a.e2e_steps):
-            xd.copy_(xh, non_blocking=True)
-            step(xd)
-            oh.copy_(out, non_blocking=True)
+        e2e(a.e2e_steps)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         if dist:
             t = torch.tensor([te], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             te = float(t.item())
+        # the copies alone, for the record (same pinned buffers, one of each direction)
+        c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        c0.record(stream)
+        pipe.din[0].copy_(xh, non_blocking=True)
+        c1.record(stream)
+        oh[0].copy_(pipe.dout[0], non_blocking=True)
+        c2.record(stream)
+        torch.cuda.synchronize()
         res["e2e"] = {"value": world * a.batch * a.e2e_steps / te, "unit": UNIT,
                       "h2d_bytes_per_step": xh.numel() * xh.element_size(),
-                      "d2h_bytes_per_step": oh.numel() * oh.element_size()}
+                      "d2h_bytes_per_step": oh[0].numel() * oh[0].element_size(),
+                      "steps": a.e2e_steps, "overlap": "copy-in of step k+1 and copy-out of step k-1 on two copy "
+                                                       "streams while step k computes",
+                      "h2d_gbs_alone": xh.numel() * xh.element_size() / (c0.elapsed_time(c1) / 1e3) / 1e9,
+                      "d2h_gbs_alone": xh.numel() * xh.element_size() / (c1.elapsed_time(c2) / 1e3) / 1e9}
+        del pipe
 
     if rank == 0 and not a.skip_check:
         if a.denoise:
@@ -436,15 +480,21 @@ def run_gpu(a, rank, world, local_rank):
         p64.analysis(x64, w64, s64)
         p64.synthesis(w64, s64, o64)
         torch.cuda.synchronize()
-        e0.record(stream)
-        p64.analysis(x64, w64, s64)
-        p64.synthesis(w64, s64, o64)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t64 = e0.elapsed_time(e1) / 1000.0
+        trips = []
+        for _ in range(a.fp64_trips):
+            e0.record(stream)
+            p64.analysis(x64, w64, s64)
+            p64.synthesis(w64, s64, o64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            trips.append(e0.elapsed_time(e1) / 1000.0)
+        t64 = statistics.median(trips)
         v64 = nb / t64
         res["fp64_path"] = {"value": v64, "unit": UNIT, "maps": nb, "ms_per_round_trip": 1000 * t64,
-                            "note": "plain FP64 GPU path, same L/B/J_min, %d maps per launch, 1 timed round trip" % nb}
+                            "ms_per_round_trip_each": [1000 * t for t in trips],
+                            "spread": (max(trips) - min(trips)) / t64,
+                            "note": "plain FP64 GPU path, same L/B/J_min, %d maps per launch; median of %d timed "
+                                    "round trips after one warm-up" % (nb, len(trips))}
         res["speedup_vs_fp64_path"] = value / world / v64
         del p64
 

@@ -194,12 +194,13 @@ int s2let_plan_profile(s2let_plan *plan, int enable);
 
 /* Totals for one stage since the last s2let_plan_profile(plan, 1): kernel
  * launches, device time in ms of the timed launches (this call synchronizes
- * their events), and the algorithmic FP operations and DRAM bytes those timed
- * launches stand for (Legendre stages: 4 flops per (l, m, ring, map) product
- * plus 4 per recurrence value; ring-DFT stages: the map, the ring-major
- * spectrum read or written by the DFT kernel and the two passes of the
- * transpose to or from the order-major spectrum; theta quadrature: its input
- * and output spectra).  Any output pointer may be NULL. */
+ * their events), and the algorithmic work those timed launches stand for,
+ * independent of how the kernels do it: Legendre stages count 4 flops per
+ * (l, m, ring, map) product (the recurrence that yields lambda_lm is not
+ * counted) and no bytes; ring-DFT stages count the bytes of the map and of
+ * its order-major spectrum (Sect. 3.2: ring FFTs); the theta quadrature counts
+ * the bytes of its input and output spectra and no flops.  Any output pointer
+ * may be NULL. */
 int s2let_plan_stage_stats(s2let_plan *plan, int stage, int64_t *launches, int64_t *timed, double *ms,
                            double *flops, double *bytes);
 

@@ -155,10 +155,13 @@ struct StageScope {
     }
 };
 
+// Algorithmic work of one Legendre stage at band-limit N: 4 flops per
+// (l, m, ring, map) product (real lambda times complex value); the recurrence
+// that produces lambda is not counted here.
 double legendre_flops(const s2let_plan *p, int N)
 {
     const double pairs = p->cplx ? (double)N * N : 0.5 * (double)N * (N + 1);
-    return 4.0 * pairs * N * p->batch + 4.0 * 0.5 * (double)N * (N + 1) * N;
+    return 4.0 * pairs * N * p->batch;
 }
 double spectrum_bytes(const s2let_plan *p, int N) { return (double)p->batch * nmi(p, N) * N * 2 * elem_size(p); }
 double map_bytes(const s2let_plan *p, int N) { return (double)p->batch * map_elems(p, N) * elem_size(p); }
@@ -196,7 +199,7 @@ int run_ring_fwd(const s2let_plan *p, const BandDev &bd, const void *f, void *F,
     const auto &T = fft_tab<R>(bd);
     const size_t sm = (size_t)padded_len(bd.M) * sizeof(cplx_t<R>);
     const int th = bd.fft_th ? bd.fft_th : fft_threads(bd.M);
-    StageScope sc(p, S2LET_STAGE_RING_FWD, st, 0.0, map_bytes(p, bd.N) + 3.0 * spectrum_bytes(p, bd.N), 2);
+    StageScope sc(p, S2LET_STAGE_RING_FWD, st, 0.0, map_bytes(p, bd.N) + spectrum_bytes(p, bd.N), 2);
     if (p->cplx) {
         k_ring_fwd_cplx<R><<<dim3(bd.N, p->batch), th, sm, st>>>((const cplx_t<R> *)f, (cplx_t<R> *)p->Ft, (R)scale,
                                                                   T);
@@ -218,7 +221,7 @@ int run_ring_inv(const s2let_plan *p, const BandDev &bd, const void *F, void *f,
     const auto &T = fft_tab<R>(bd);
     const size_t sm = (size_t)padded_len(bd.M) * sizeof(cplx_t<R>);
     const int th = bd.fft_th ? bd.fft_th : fft_threads(bd.M);
-    StageScope sc(p, S2LET_STAGE_RING_INV, st, 0.0, map_bytes(p, bd.N) + 3.0 * spectrum_bytes(p, bd.N), 2);
+    StageScope sc(p, S2LET_STAGE_RING_INV, st, 0.0, map_bytes(p, bd.N) + spectrum_bytes(p, bd.N), 2);
     // F[b][mi][t] -> Ft[b][t][mi]
     const int n = nmi(p, bd.N);
     k_transpose<cplx_t<R>><<<dim3((bd.N + 31) / 32, (n + 31) / 32, p->batch), dim3(32, 8), 0, st>>>(
@@ -244,8 +247,7 @@ void *run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream
     *err = S2LET_OK;
     if (std::is_same<R, float>::value && p->quad_gemm) {
         // two products, one per parity of m
-        StageScope sc(p, S2LET_STAGE_THETA_QUAD, st, 2.0 * bd.N * (double)bd.N * n * 2 * p->batch,
-                      2.0 * spectrum_bytes(p, bd.N), n > 1 ? 2 : 1);
+        StageScope sc(p, S2LET_STAGE_THETA_QUAD, st, 0.0, 2.0 * spectrum_bytes(p, bd.N), n > 1 ? 2 : 1);
         for (int par = 0; par < 2; ++par) {
             int mi0 = p->cplx ? (((bd.N - 1) & 1) ^ par) : par;
             if (mi0 >= n) continue;

@@ -217,6 +217,51 @@ class Plan:
         return self.synthesis(f_wav, f_scal, out, stream=stream)
 
 
+class HostPipeline:
+    """Streams batches of maps between pinned host memory and a plan's transforms
+    with the copies overlapped: while step k computes on the caller's stream,
+    step k+1's inputs are copied in (host -> device) on one copy stream and step
+    k-1's results out (device -> host) on another.  Device buffers are kept in
+    `depth` slots; CUDA events order each slot's copy-in, compute and copy-out,
+    so no slot is overwritten while it is still read.  Only data movement and
+    ordering live here: the transforms are whatever `compute` launches."""
+
+    def __init__(self, in_like, out_like, depth=2):
+        if depth < 2:
+            raise ValueError("depth must be at least 2")
+        self.depth = depth
+        self.din = [torch.empty_like(in_like) for _ in range(depth)]
+        self.dout = [torch.empty_like(out_like) for _ in range(depth)]
+        self.h2d = torch.cuda.Stream(device=in_like.device)
+        self.d2h = torch.cuda.Stream(device=in_like.device)
+        self.in_ready = [torch.cuda.Event() for _ in range(depth)]
+        self.computed = [torch.cuda.Event() for _ in range(depth)]
+        self.out_free = [torch.cuda.Event() for _ in range(depth)]
+
+    def run(self, n_steps, host_in, host_out, compute):
+        """For k < n_steps: copy host_in(k) in, compute(din, dout) on the current
+        stream, copy dout to host_out(k).  host_in / host_out return pinned host
+        tensors shaped like the device buffers.  Returns when every copy-out has
+        been queued; the caller synchronises."""
+        cs = torch.cuda.current_stream()
+        for k in range(n_steps):
+            s = k % self.depth
+            with torch.cuda.stream(self.h2d):
+                if k >= self.depth:
+                    self.h2d.wait_event(self.computed[s])       # step k - depth has read din[s]
+                self.din[s].copy_(host_in(k), non_blocking=True)
+                self.in_ready[s].record(self.h2d)
+            cs.wait_event(self.in_ready[s])
+            if k >= self.depth:
+                cs.wait_event(self.out_free[s])                  # step k - depth's result has left dout[s]
+            compute(self.din[s], self.dout[s])
+            self.computed[s].record(cs)
+            with torch.cuda.stream(self.d2h):
+                self.d2h.wait_event(self.computed[s])
+                host_out(k).copy_(self.dout[s], non_blocking=True)
+                self.out_free[s].record(self.d2h)
+
+
 class BatchPlan:
     """Maps of uneven band-limit L_i and dilation B_i (same J_min, real/complex and
     precision), transformed together: one plan per (L, B) group, and one CUDA

@@ -43,3 +43,51 @@ def test_reference_arm_json_line(extra):
 def test_reference_arm_other_ranks_print_nothing():
     assert _run(["--impl", "reference", "--L", "16", "--J-min", "0", "--steps", "1", "--warmup", "1"],
                 env={"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def test_stage_rooflines_follow_the_work_of_each_stage():
+    """The per-stage roofline records on synthetic stage statistics: byte-counted
+    stages (ring DFTs, quadrature) against HBM, the Legendre contractions against
+    the pipe of their precision, the dominant stage picked by time, and the
+    Legendre sub-record always present."""
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+    peaks = {"hbm_gbs": 6000.0, "bf16_tflops_sustained": 1800.0, "sm_max_mhz": 2000.0}
+    steps = 2
+    stats = {
+        "ring_fwd": dict(launches=4, timed=4, ms=20.0, flops=0.0, bytes=60e9),
+        "theta_quad": dict(launches=4, timed=4, ms=30.0, flops=0.0, bytes=12e9),
+        "leg_anal": dict(launches=4, timed=4, ms=50.0, flops=1e13, bytes=0.0),
+        "leg_synth": dict(launches=4, timed=4, ms=40.0, flops=1e13, bytes=0.0),
+        "ring_inv": dict(launches=4, timed=4, ms=20.0, flops=0.0, bytes=60e9),
+        "pack": dict(launches=0, timed=0, ms=0.0, flops=0.0, bytes=0.0),
+    }
+    a = types.SimpleNamespace(steps=steps, precision="tf32x3")
+    roof, leg, recs = bench.rooflines(stats, a, peaks, 64, [2048, 8, 4])
+    tf32 = 1800.0 * 1.1 / 2.25
+    assert roof["kernel"] == "leg_anal" and roof["bound"] == "tensor" and roof["unit"] == "TFLOP/s"
+    assert roof["achieved"] == pytest.approx(1e13 / 0.050 / 1e12)
+    assert roof["peak"] == pytest.approx(tf32) and roof["frac"] == pytest.approx(200.0 / tf32)
+    assert roof["executed_mma_frac"] == pytest.approx(3 * 200.0 / tf32)
+    assert "of measured" in roof["peak_source"] and roof["traffic"] is None
+    assert set(leg) == {"leg_anal", "leg_synth"}
+    assert leg["leg_synth"]["frac"] == pytest.approx(250.0 / tf32)
+    assert leg["leg_anal"]["recurrence_tflops"] == pytest.approx(1e13 / 64 / 0.050 / 1e12)
+    q = recs["theta_quad"]
+    assert q["bound"] == "hbm" and q["unit"] == "GB/s" and q["achieved"] == pytest.approx(400.0)
+    assert q["frac"] == pytest.approx(400.0 / 6000.0)
+    dense = 4.0 * (2048 ** 3 + 8 ** 3 + 4 ** 3) * 64
+    assert q["dense_equivalent_tflops"] == pytest.approx(dense / (15.0 / 1000) / 1e12)
+    assert recs["ring_fwd"]["achieved"] == pytest.approx(3000.0) and "pack" not in recs
+    # FP32 plans: the Legendre stages against the FP32 pipe, no MMA figure; fallback peaks
+    a32 = types.SimpleNamespace(steps=steps, precision="fp32")
+    roof32, leg32, _ = bench.rooflines(stats, a32, {}, 64, [2048])
+    fp32 = 152 * 128 * 2 * 2070.0 * 1e6 / 1e12
+    assert roof32["bound"] == "alu" and roof32["peak"] == pytest.approx(fp32)
+    assert "executed_mma_frac" not in roof32 and "of fallback" in roof32["peak_source"]
+    # a byte-bound stage that dominates is reported against HBM
+    stats2 = dict(stats, ring_fwd=dict(launches=4, timed=4, ms=90.0, flops=0.0, bytes=60e9))
+    roof2, _, _ = bench.rooflines(stats2, a, peaks, 64, [2048])
+    assert roof2["kernel"] == "ring_fwd" and roof2["bound"] == "hbm"
+    assert roof2["frac"] == pytest.approx(60e9 / 0.090 / 1e9 / 6000.0)
