@@ -34,6 +34,7 @@
 #ifndef S2LET_GPU_H
 #define S2LET_GPU_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -286,6 +287,32 @@ int s2let_wav_kernel(int L, int B, int J_min, int flags, int j, double *fac);
  * s2let_synthesis with the unchanged f_scal. */
 int s2let_wav_noise_std(const s2let_plan *plan, int j, double *ratio);
 int s2let_wav_threshold(s2let_plan *plan, void *f_wav, double sigma, double nsigma, void *stream);
+
+/* Device memory of plans.  By default plans (and the group plans of a batch)
+ * take their tables and workspace from cudaMalloc and return them with
+ * cudaFree.  s2let_set_allocator installs a process-wide hook instead:
+ * alloc(bytes, ctx) returns device memory of the current device aligned to
+ * 256 bytes, or NULL on failure; release(ptr, ctx) takes back what alloc
+ * returned.  Plans created while a hook is installed use it for every
+ * allocation, including the temporary ones of plan creation, and keep it until
+ * they are destroyed.  A failed (NULL) or misaligned allocation makes the plan
+ * creation return S2LET_ERR_ALLOC after releasing everything it allocated.
+ * alloc = release = NULL restores cudaMalloc / cudaFree; exactly one of them
+ * NULL is S2LET_ERR_ARG.  Transform calls never allocate.  Not part of the
+ * paper: it lets a host framework own the memory (e.g. a caching allocator)
+ * and lets tests simulate allocation failures. */
+typedef void *(*s2let_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*s2let_free_fn)(void *ptr, void *ctx);
+int s2let_set_allocator(s2let_alloc_fn alloc, s2let_free_fn release, void *ctx);
+
+/* Failure-path check, not part of the paper: launches on `stream` one small
+ * kernel whose two bounded waits -- the suspending and the polling kind that
+ * the tensor-core kernels use -- wait on barriers that nothing arrives at.
+ * They give up after their iteration limits (seconds), and the kernel sets the
+ * plan's error word as a tensor-core kernel does when a wait runs out, so that
+ * s2let_plan_status(plan) then returns S2LET_ERR_TIMEOUT for good.  The
+ * kernel issues no copy and no MMA; the plan's transforms are unaffected. */
+int s2let_plan_test_timeout(s2let_plan *plan, void *stream);
 
 /* Device-side status of a plan: S2LET_ERR_TIMEOUT if a bounded wait inside a
  * tensor-core kernel gave up since the plan was created (its results are then

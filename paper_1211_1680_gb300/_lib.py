@@ -30,6 +30,9 @@ _vp = ctypes.c_void_p
 _i = ctypes.c_int
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _ip = ctypes.POINTER(ctypes.c_int)
+# device-memory hook of s2let_set_allocator
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 SIGNATURES = {
     "s2let_jmax": (_i, [_i, _i]),
     "s2let_plan_create": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _i]),
@@ -42,6 +45,8 @@ SIGNATURES = {
     "s2let_sht_forward": (_i, [_vp, _vp, _vp, _vp]),
     "s2let_sht_inverse": (_i, [_vp, _vp, _vp, _vp]),
     "s2let_plan_status": (_i, [_vp]),
+    "s2let_plan_test_timeout": (_i, [_vp, _vp]),
+    "s2let_set_allocator": (_i, [ALLOC_FN, FREE_FN, _vp]),
     "s2let_plan_autotune": (_i, [_vp, _vp]),
     "s2let_batch_autotune": (_i, [_vp, _vp]),
     "s2let_plan_tuning": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),

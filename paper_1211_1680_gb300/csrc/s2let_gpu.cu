@@ -17,6 +17,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <type_traits>
 #include <vector>
@@ -39,11 +40,40 @@ constexpr int kMaxM = 8192;   // FFT length for kMaxL (next power of two >= 4 kM
 
 int fft_threads(int M) { return std::max(32, std::min(FFT_MAX_THREADS, M / 16)); }
 
-template <typename T> T *dev_upload(const std::vector<T> &h, std::vector<void *> &owned, int &err)
+// Device memory of plans: cudaMalloc / cudaFree, or the caller's hook
+// (s2let_set_allocator).  A plan keeps the hook it was created with.
+struct DevAlloc {
+    s2let_alloc_fn alloc = nullptr;
+    s2let_free_fn release = nullptr;
+    void *ctx = nullptr;
+};
+DevAlloc g_alloc;
+std::mutex g_alloc_mu;
+
+template <typename T> cudaError_t dm_alloc(const DevAlloc &a, T **p, size_t bytes)
+{
+    if (!a.alloc) return cudaMalloc(p, bytes);
+    void *q = a.alloc(bytes, a.ctx);
+    if (q && (reinterpret_cast<uintptr_t>(q) & 255)) {   // the kernels rely on cudaMalloc's alignment
+        a.release(q, a.ctx);
+        q = nullptr;
+    }
+    *p = static_cast<T *>(q);
+    return q ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+void dm_free(const DevAlloc &a, void *p)
+{
+    if (!p) return;
+    if (a.release) a.release(p, a.ctx);
+    else cudaFree(p);
+}
+
+template <typename T>
+T *dev_upload(const DevAlloc &mem, const std::vector<T> &h, std::vector<void *> &owned, int &err)
 {
     if (h.empty()) return nullptr;
     void *p = nullptr;
-    if (cudaMalloc(&p, h.size() * sizeof(T)) != cudaSuccess) {
+    if (dm_alloc(mem, &p, h.size() * sizeof(T)) != cudaSuccess) {
         err = S2LET_ERR_ALLOC;
         return nullptr;
     }
@@ -102,6 +132,7 @@ struct s2let_plan {
     int tc_split = 2;                       // TF32 parts per operand in the tensor-core products
     int *d_err = nullptr;                   // device error word (bounded waits)
     std::vector<void *> owned;
+    DevAlloc mem;                           // allocator of everything in `owned`
     // instrumentation
     struct Rec {
         int stage;
@@ -116,7 +147,10 @@ struct s2let_plan {
     ~s2let_plan()
     {
         for (cudaEvent_t e : evpool) cudaEventDestroy(e);
-        for (void *p : owned) cudaFree(p);
+        // cudaFree waits for the device; a hook's release may not, and kernels of
+        // this plan may still be running
+        if (mem.alloc) cudaDeviceSynchronize();
+        for (void *q : owned) dm_free(mem, q);
     }
 };
 
@@ -598,13 +632,13 @@ int build_quad_matrices(s2let_plan *p, BandDev &bd)
     const int N = bd.N;
     const size_t nn = (size_t)N * N;
     double2 *X = nullptr;
-    if (cudaMalloc(&X, nn * sizeof(double2)) != cudaSuccess) return S2LET_ERR_ALLOC;
+    if (dm_alloc(p->mem, &X, nn * sizeof(double2)) != cudaSuccess) return S2LET_ERR_ALLOC;
     cudaFuncSetAttribute(k_theta_quad<double, double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(padded_len(bd.M) * sizeof(double2)));
     int err = S2LET_OK;
     for (int par = 0; par < 2 && !err; ++par) {
         float *Q = nullptr;
-        if (cudaMalloc(&Q, nn * sizeof(float)) != cudaSuccess) {
+        if (dm_alloc(p->mem, &Q, nn * sizeof(float)) != cudaSuccess) {
             err = S2LET_ERR_ALLOC;
             break;
         }
@@ -616,7 +650,7 @@ int build_quad_matrices(s2let_plan *p, BandDev &bd)
         k_real_to_float<<<(unsigned)((nn + 255) / 256), 256>>>(X, Q, nn);
         if (p->tc && p->tc_split == 3) {
             float *Q3 = nullptr;
-            if (cudaMalloc(&Q3, 3 * nn * sizeof(float)) != cudaSuccess) {
+            if (dm_alloc(p->mem, &Q3, 3 * nn * sizeof(float)) != cudaSuccess) {
                 err = S2LET_ERR_ALLOC;
                 break;
             }
@@ -625,7 +659,7 @@ int build_quad_matrices(s2let_plan *p, BandDev &bd)
             k_split3_planes<<<(unsigned)((nn + 255) / 256), 256>>>(Q, Q3, nn);
         } else if (p->tc) {
             unsigned char *img = nullptr;
-            if (cudaMalloc(&img, quad_image_bytes(N)) != cudaSuccess) {
+            if (dm_alloc(p->mem, &img, quad_image_bytes(N)) != cudaSuccess) {
                 err = S2LET_ERR_ALLOC;
                 break;
             }
@@ -636,8 +670,9 @@ int build_quad_matrices(s2let_plan *p, BandDev &bd)
         }
         if (cudaGetLastError() != cudaSuccess) err = S2LET_ERR_CUDA;
     }
-    if (!err && cudaDeviceSynchronize() != cudaSuccess) err = S2LET_ERR_CUDA;
-    cudaFree(X);
+    // also on failure: kernels of the first parity may still read X
+    if (cudaDeviceSynchronize() != cudaSuccess && !err) err = S2LET_ERR_CUDA;
+    dm_free(p->mem, X);
     return err;
 }
 
@@ -661,18 +696,18 @@ int build_band_dev(s2let_plan *p, int N, BandDev &bd)
     bd.M = h.M;
     bd.logM = h.logM;
     auto &o = p->owned;
-    bd.fd.chirp = dev_upload(to_c<double2>(h.chirp), o, err);
-    bd.fd.bhat = dev_upload(to_c<double2>(h.bhat), o, err);
-    bd.fd.bhat_g = dev_upload(to_c<double2>(group_major(h.bhat, 1 << fft_rbf<double2>())), o, err);
-    bd.fd.what = dev_upload(to_c<double2>(h.what), o, err);
-    bd.fd.tw = dev_upload(to_c<double2>(h.tw), o, err);
-    bd.fd.phase = dev_upload(to_c<double2>(h.phase), o, err);
-    bd.ff.chirp = dev_upload(to_c<float2>(h.chirp), o, err);
-    bd.ff.bhat = dev_upload(to_c<float2>(h.bhat), o, err);
-    bd.ff.bhat_g = dev_upload(to_c<float2>(group_major(h.bhat, 1 << fft_rbf<float2>())), o, err);
-    bd.ff.what = dev_upload(to_c<float2>(h.what), o, err);
-    bd.ff.tw = dev_upload(to_c<float2>(h.tw), o, err);
-    bd.ff.phase = dev_upload(to_c<float2>(h.phase), o, err);
+    bd.fd.chirp = dev_upload(p->mem, to_c<double2>(h.chirp), o, err);
+    bd.fd.bhat = dev_upload(p->mem, to_c<double2>(h.bhat), o, err);
+    bd.fd.bhat_g = dev_upload(p->mem, to_c<double2>(group_major(h.bhat, 1 << fft_rbf<double2>())), o, err);
+    bd.fd.what = dev_upload(p->mem, to_c<double2>(h.what), o, err);
+    bd.fd.tw = dev_upload(p->mem, to_c<double2>(h.tw), o, err);
+    bd.fd.phase = dev_upload(p->mem, to_c<double2>(h.phase), o, err);
+    bd.ff.chirp = dev_upload(p->mem, to_c<float2>(h.chirp), o, err);
+    bd.ff.bhat = dev_upload(p->mem, to_c<float2>(h.bhat), o, err);
+    bd.ff.bhat_g = dev_upload(p->mem, to_c<float2>(group_major(h.bhat, 1 << fft_rbf<float2>())), o, err);
+    bd.ff.what = dev_upload(p->mem, to_c<float2>(h.what), o, err);
+    bd.ff.tw = dev_upload(p->mem, to_c<float2>(h.tw), o, err);
+    bd.ff.phase = dev_upload(p->mem, to_c<float2>(h.phase), o, err);
     bd.fd.N = h.N;
     bd.fd.P = h.P;
     bd.fd.M = h.M;
@@ -689,24 +724,24 @@ int build_band_dev(s2let_plan *p, int N, BandDev &bd)
         rf[t].xh = h.xh[t];
         rf[t].xl = h.xl[t];
     }
-    bd.ringd = dev_upload(rd, o, err);
-    bd.ringf = dev_upload(rf, o, err);
-    double *sinth = dev_upload(h.sinth, o, err);
+    bd.ringd = dev_upload(p->mem, rd, o, err);
+    bd.ringf = dev_upload(p->mem, rf, o, err);
+    double *sinth = dev_upload(p->mem, h.sinth, o, err);
     if (err) return err;
     // seeds: sectoral values, then the first significant degree per (m, t)
     const size_t nn = (size_t)N * N;
     double *mant = nullptr;
     int *expo = nullptr;
-    if (cudaMalloc(&mant, nn * sizeof(double)) != cudaSuccess) return S2LET_ERR_ALLOC;
-    if (cudaMalloc(&expo, nn * sizeof(int)) != cudaSuccess) {
-        cudaFree(mant);
+    if (dm_alloc(p->mem, &mant, nn * sizeof(double)) != cudaSuccess) return S2LET_ERR_ALLOC;
+    if (dm_alloc(p->mem, &expo, nn * sizeof(int)) != cudaSuccess) {
+        dm_free(p->mem, mant);
         return S2LET_ERR_ALLOC;
     }
     void *ls = nullptr, *seed = nullptr;
-    if (cudaMalloc(&ls, nn * sizeof(int)) != cudaSuccess || cudaMalloc(&seed, nn * sizeof(double2)) != cudaSuccess) {
-        cudaFree(mant);
-        cudaFree(expo);
-        if (ls) cudaFree(ls);
+    if (dm_alloc(p->mem, &ls, nn * sizeof(int)) != cudaSuccess || dm_alloc(p->mem, &seed, nn * sizeof(double2)) != cudaSuccess) {
+        dm_free(p->mem, mant);
+        dm_free(p->mem, expo);
+        if (ls) dm_free(p->mem, ls);
         return S2LET_ERR_ALLOC;
     }
     o.push_back(ls);
@@ -715,8 +750,8 @@ int build_band_dev(s2let_plan *p, int N, BandDev &bd)
     bd.seed = (double2 *)seed;
     if (p->quad_gemm) {
         if ((err = build_quad_matrices(p, bd))) {
-            cudaFree(mant);
-            cudaFree(expo);
+            dm_free(p->mem, mant);
+            dm_free(p->mem, expo);
             return err;
         }
     }
@@ -724,8 +759,8 @@ int build_band_dev(s2let_plan *p, int N, BandDev &bd)
     k_seed_start<<<(unsigned)((nn + 127) / 128), 128>>>(N, mant, expo, bd.ringd, p->coefd, p->L, bd.ls, bd.seed);
     cudaError_t ce = cudaGetLastError();
     if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
-    cudaFree(mant);
-    cudaFree(expo);
+    dm_free(p->mem, mant);
+    dm_free(p->mem, expo);
     return ce == cudaSuccess ? S2LET_OK : S2LET_ERR_CUDA;
 }
 
@@ -745,6 +780,10 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
 
     std::unique_ptr<s2let_plan> p(new (std::nothrow) s2let_plan());
     if (!p) return S2LET_ERR_ALLOC;
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_mu);
+        p->mem = g_alloc;
+    }
     p->L = L;
     p->B = B;
     p->J0 = J0;
@@ -776,7 +815,7 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
             cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return S2LET_ERR_CUDA;
     }
-    if (cudaMalloc(&p->d_err, sizeof(int)) != cudaSuccess) return S2LET_ERR_ALLOC;
+    if (dm_alloc(p->mem, &p->d_err, sizeof(int)) != cudaSuccess) return S2LET_ERR_ALLOC;
     p->owned.push_back(p->d_err);
     if (cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess) return S2LET_ERR_CUDA;
     // recurrence coefficients for degrees and orders < L
@@ -789,8 +828,8 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
         const float ah = (float)a[i], bh = (float)ab[i];
         cf[i] = make_float4(ah, (float)(a[i] - (double)ah), bh, (float)(ab[i] - (double)bh));
     }
-    p->coefd = dev_upload(cd, p->owned, err);
-    p->coeff = dev_upload(cf, p->owned, err);
+    p->coefd = dev_upload(p->mem, cd, p->owned, err);
+    p->coeff = dev_upload(p->mem, cf, p->owned, err);
     if (err) return err;
     // kernel factors sqrt(4 pi/(2l+1)) Phi_l0 = eta(l / B^J0), sqrt(4 pi/(2l+1)) Psi^j_l0 = kappa(l / B^j)
     for (int k = 0; k <= J - J0 + 1; ++k) {
@@ -802,10 +841,10 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
         for (int l = 0; l < L; ++l) v += (2.0 * l + 1.0) / (4.0 * M_PI) * fac[l] * fac[l];
         p->noise_ratio.push_back(std::sqrt(v));
         if (p->fp64) {
-            p->kfac.push_back(dev_upload(fac, p->owned, err));
+            p->kfac.push_back(dev_upload(p->mem, fac, p->owned, err));
         } else {
             std::vector<float> ff(fac.begin(), fac.end());
-            p->kfac.push_back(dev_upload(ff, p->owned, err));
+            p->kfac.push_back(dev_upload(p->mem, ff, p->owned, err));
         }
         if (err) return err;
     }
@@ -828,14 +867,14 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
     set_smem_limits(kMaxM);
     // workspace: two L-rectangles of complex values per map
     const size_t ws = (size_t)batch * nmi(p.get(), L) * L * 2 * elem_size(p.get());
-    if (cudaMalloc(&p->F, ws) != cudaSuccess) return S2LET_ERR_ALLOC;
+    if (dm_alloc(p->mem, &p->F, ws) != cudaSuccess) return S2LET_ERR_ALLOC;
     p->owned.push_back(p->F);
-    if (cudaMalloc(&p->flm, ws) != cudaSuccess) return S2LET_ERR_ALLOC;
+    if (dm_alloc(p->mem, &p->flm, ws) != cudaSuccess) return S2LET_ERR_ALLOC;
     p->owned.push_back(p->flm);
-    if (cudaMalloc(&p->Ft, ws) != cudaSuccess) return S2LET_ERR_ALLOC;
+    if (dm_alloc(p->mem, &p->Ft, ws) != cudaSuccess) return S2LET_ERR_ALLOC;
     p->owned.push_back(p->Ft);
     if (p->quad_gemm) {
-        if (cudaMalloc(&p->G, ws) != cudaSuccess) return S2LET_ERR_ALLOC;
+        if (dm_alloc(p->mem, &p->G, ws) != cudaSuccess) return S2LET_ERR_ALLOC;
         p->owned.push_back(p->G);
     }
     if (cudaGetLastError() != cudaSuccess) return S2LET_ERR_CUDA;
@@ -1013,6 +1052,34 @@ int run_threshold(const s2let_plan *p, void *f_wav, double sigma, double nsigma,
 
 }  // namespace
 
+// Failure-path check (s2let_plan_test_timeout): the two kinds of bounded wait
+// of the tensor-core kernels, each on an mbarrier that nothing arrives at.
+// Warp 0 waits with suspending try_wait polls (lt_wait), warp 1 with test_wait
+// polls (lt_spin); whichever runs out first raises the shared abort flag, the
+// other sees it and gives up too, and the error word is set as the tensor-core
+// kernels set it.  No copy or MMA is issued, so nothing is in flight at exit.
+__global__ void k_expire_waits(int *err)
+{
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    volatile int *abort = &abort_flag;
+    if (lane == 0) {
+        // phase 0 of a fresh barrier never completes without an arrival
+        if (warp == 0) lt_wait(&bar[0], 0, abort);
+        else lt_spin(&bar[1], 0, abort);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && abort_flag) atomicExch(err, 1);
+}
+
 extern "C" {
 
 int s2let_jmax(int L, int B)
@@ -1165,6 +1232,23 @@ int s2let_wav_threshold(s2let_plan *p, void *f_wav, double sigma, double nsigma,
     if ((int)p->n_wav.size() > kThrMaxScales) return S2LET_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     return S2_DISPATCH(run_threshold, p, f_wav, sigma, nsigma, st);
+}
+
+int s2let_set_allocator(s2let_alloc_fn alloc, s2let_free_fn release, void *ctx)
+{
+    if ((alloc == nullptr) != (release == nullptr)) return S2LET_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    g_alloc.alloc = alloc;
+    g_alloc.release = release;
+    g_alloc.ctx = alloc ? ctx : nullptr;
+    return S2LET_OK;
+}
+
+int s2let_plan_test_timeout(s2let_plan *p, void *stream)
+{
+    if (!p) return S2LET_ERR_ARG;
+    k_expire_waits<<<1, 64, 0, (cudaStream_t)stream>>>(p->d_err);
+    return cudaGetLastError() == cudaSuccess ? S2LET_OK : S2LET_ERR_CUDA;
 }
 
 int s2let_plan_status(s2let_plan *p)

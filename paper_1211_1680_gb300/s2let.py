@@ -31,6 +31,40 @@ def _kernel_flag(kernel):
     return S2LET_KERNEL_BSPLINE if kernel == "bspline" else 0
 
 
+_hook = None     # the installed allocator callbacks (kept alive while plans may use them)
+
+
+def set_allocator(alloc=None, release=None):
+    """Install a device-memory hook for plans created from now on
+    (s2let_set_allocator): alloc(nbytes) -> device address (int, 0 on failure),
+    release(address).  With no arguments, plans use cudaMalloc / cudaFree again.
+    The callbacks stay referenced here, so that plans created with them can free
+    their memory after the hook is replaced."""
+    global _hook
+    lib = _lib.lib()
+    if alloc is None and release is None:
+        check("s2let_set_allocator", lib.s2let_set_allocator(_lib.ALLOC_FN(), _lib.FREE_FN(), None))
+        return
+    a = _lib.ALLOC_FN(lambda n, ctx: alloc(int(n)) or None)
+    r = _lib.FREE_FN(lambda ptr, ctx: release(int(ptr)))
+    check("s2let_set_allocator", lib.s2let_set_allocator(a, r, None))
+    _keep.append((a, r))
+    _hook = (a, r)
+
+
+_keep = []
+
+
+def use_torch_allocator(device=None):
+    """Let PyTorch's caching allocator own the memory of plans created from now on."""
+    dev = torch.cuda.current_device() if device is None else device
+
+    def alloc(n):
+        return torch.cuda.caching_allocator_alloc(n, dev)
+
+    set_allocator(alloc, torch.cuda.caching_allocator_delete)
+
+
 class Plan:
     """A batched transform plan: `batch` maps of band-limit L, dilation B,
     lowest scale J_min (Sect. 2.2), real or complex, multiresolution or not,
@@ -90,6 +124,11 @@ class Plan:
     def status(self):
         """S2LET_OK, or S2LET_ERR_TIMEOUT if a bounded device wait gave up (synchronises)."""
         return _lib.lib().s2let_plan_status(self._h)
+
+    def test_timeout(self, stream=None):
+        """Failure-path check (s2let_plan_test_timeout): one kernel whose bounded
+        waits run out; status() reports S2LET_ERR_TIMEOUT afterwards."""
+        check("s2let_plan_test_timeout", _lib.lib().s2let_plan_test_timeout(self._h, _stream_handle(stream)))
 
     def close(self):
         if self._h:

@@ -73,3 +73,10 @@ def test_binding_rejects_unknown_kernel_family_without_gpu():
         Plan(32, 2, 0, kernel="needlet")
     with pytest.raises(ValueError):
         BatchPlan([32], [2], 0, kernel="spline")
+
+
+def test_allocator_hook_arguments_need_no_gpu():
+    L = _lib.lib()
+    a = _lib.ALLOC_FN(lambda n, c: None)
+    assert L.s2let_set_allocator(a, _lib.FREE_FN(), None) == _lib.S2LET_ERR_ARG
+    assert L.s2let_set_allocator(_lib.ALLOC_FN(), _lib.FREE_FN(), None) == _lib.S2LET_OK
