@@ -1,0 +1,396 @@
+// Mixed-radix FFTs of odd length P = 2N - 1 in shared memory (FP32), for the
+// band-limits whose P factors into the radices 13, 11, 9, 7, 5, 3 (P = 4095 =
+// 13 * 9 * 7 * 5 at N = 2048).  Unlike the Bluestein form of fft.cuh, which
+// computes a length-P DFT as a circular convolution of length M >= 2P - 1, the
+// transform works on the P samples directly: a quarter of the operations per
+// sample at P = 4095, and no chirp products whose intermediates exceed the
+// result by sqrt(P).
+//
+// Decimation in frequency, in place (Cooley-Tukey for composite lengths): with
+// P = R S' and n = j + S' q, k = s + R k', the DFT splits into R DFTs of
+// length S' of y_s[j] = w_P^{j s} sum_q x[j + S' q] w_R^{q s}, stored at
+// j + S' s.  Repeating this on every block leaves X_k at a mixed-radix
+// digit-reversed position pos(k) (tables below); natural order in, permuted
+// order out.  The transposed algorithm (twiddles before the radix-R DFTs,
+// passes in reverse order) takes permuted input to natural output, so a
+// product with a diagonal between a forward and an inverse transform needs no
+// permutation pass.  Radix-R DFTs of prime R pair x_k with x_{R-k}, so each
+// cosine and sine product serves two outputs; radix 9 is 3 x 3 in registers.
+#pragma once
+#include "common.cuh"
+#include "dft_consts.cuh"
+
+namespace s2g {
+
+// ---------------------------------------------------------------- factorisation
+struct MrFactors {
+    int n;          // number of passes, -1 if P has a prime factor above 13
+    int r[16];      // radices, first pass first
+};
+__host__ __device__ constexpr MrFactors mr_factors(int P)
+{
+    MrFactors f{0, {}};
+    const int cand[6] = {13, 11, 9, 7, 5, 3};
+    for (int i = 0; i < 6; ++i)
+        while (P > 1 && P % cand[i] == 0 && f.n < 16) {
+            f.r[f.n++] = cand[i];
+            P /= cand[i];
+        }
+    if (P != 1) f.n = -1;
+    return f;
+}
+// length of the sub-transforms entering pass i (P for pass 0)
+__host__ __device__ constexpr int mr_sub(int P, int i)
+{
+    const MrFactors f = mr_factors(P);
+    int S = P;
+    for (int k = 0; k < i; ++k) S /= f.r[k];
+    return S;
+}
+
+// The band-limits with mixed-radix kernels: P = 2N - 1 in this list.
+#define S2G_MR_LENGTHS(X) X(7) X(15) X(45) X(63) X(65) X(99) X(315) X(4095)
+__host__ __device__ constexpr bool mr_supported(int P)
+{
+    return P == 7 || P == 15 || P == 45 || P == 63 || P == 65 || P == 99 || P == 315 || P == 4095;
+}
+
+// Tables of one length P (device pointers, built on the host in FP64):
+//   tw[k]    = e^{-2 pi i k / P}, k < P
+//   rev[k]   = position of X_k after the forward passes
+//   shm[p]   = e^{-i a pi / P} at position p = rev[k], a = k (k < N) or k - P:
+//              the half-sample shift theta -> theta - pi/P of the quadrature
+//   shp[p]   = conj(shm[p]) / P
+//   ve[t]    = v(theta_t - pi/P) / P, vfold[t] (t < N): quadrature weights (k_quad_mr)
+struct MrTab {
+    const float2 *tw;
+    const int *rev;
+    const float2 *shm, *shp;
+    const float *ve, *vfold;
+};
+
+// ---------------------------------------------------------------- small DFTs
+template <bool INV> __device__ __forceinline__ float2 mr_twiddle(float2 x, float2 w)
+{
+    // x * w, or x * conj(w) for the inverse transform
+    return INV ? make_float2(fmaf(x.x, w.x, x.y * w.y), fmaf(x.y, w.x, -x.x * w.y))
+               : make_float2(fmaf(x.x, w.x, -x.y * w.y), fmaf(x.x, w.y, x.y * w.x));
+}
+
+// y_s = sum_q x_q e^{-+2 pi i q s / R} in place, R odd prime (pairing k, R-k):
+// y_0 = x_0 + sum a_k, y_s = A_s -+ i B_s, y_{R-s} = A_s +- i B_s with
+// a_k = x_k + x_{R-k}, b_k = x_k - x_{R-k}, A_s = x_0 + sum_k a_k cos(2 pi k s/R),
+// B_s = sum_k b_k sin(2 pi k s/R)
+template <int R, bool INV> __device__ __forceinline__ void mr_dft_prime(float2 (&x)[R])
+{
+    constexpr int H = (R - 1) / 2;
+    using K = DftConst<R>;
+    float2 a[H], b[H];
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+        a[k - 1] = make_float2(x[k].x + x[R - k].x, x[k].y + x[R - k].y);
+        b[k - 1] = make_float2(x[k].x - x[R - k].x, x[k].y - x[R - k].y);
+    }
+    float2 y0 = x[0];
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+        y0.x += a[k].x;
+        y0.y += a[k].y;
+    }
+#pragma unroll
+    for (int s = 1; s <= H; ++s) {
+        float2 A = x[0], B = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 1; k <= H; ++k) {
+            const int e = (k * s) % R;
+            const float c = K::c(e), sn = K::s(e);
+            A.x = fmaf(a[k - 1].x, c, A.x);
+            A.y = fmaf(a[k - 1].y, c, A.y);
+            B.x = fmaf(b[k - 1].x, sn, B.x);
+            B.y = fmaf(b[k - 1].y, sn, B.y);
+        }
+        // -i B = (B.y, -B.x)
+        if (INV) {
+            x[s] = make_float2(A.x - B.y, A.y + B.x);
+            x[R - s] = make_float2(A.x + B.y, A.y - B.x);
+        } else {
+            x[s] = make_float2(A.x + B.y, A.y - B.x);
+            x[R - s] = make_float2(A.x - B.y, A.y + B.x);
+        }
+    }
+    x[0] = y0;
+}
+
+template <bool INV> __device__ __forceinline__ void mr_dft3(float2 &x0, float2 &x1, float2 &x2)
+{
+    float2 v[3] = {x0, x1, x2};
+    mr_dft_prime<3, INV>(v);
+    x0 = v[0];
+    x1 = v[1];
+    x2 = v[2];
+}
+
+// radix 9 as 3 x 3: n = n1 + 3 n2, k = k2 + 3 k1; DFTs over n2, twiddles
+// w_9^{n1 k2}, DFTs over n1
+template <bool INV> __device__ __forceinline__ void mr_dft9(float2 (&x)[9])
+{
+    using K = DftConst<9>;
+#pragma unroll
+    for (int n1 = 0; n1 < 3; ++n1) mr_dft3<INV>(x[n1], x[n1 + 3], x[n1 + 6]);
+    // u[n1][k2] now at x[n1 + 3 k2]; twiddles for n1, k2 in {1, 2}
+#pragma unroll
+    for (int n1 = 1; n1 < 3; ++n1)
+#pragma unroll
+        for (int k2 = 1; k2 < 3; ++k2) {
+            const int e = n1 * k2;
+            x[n1 + 3 * k2] = mr_twiddle<INV>(x[n1 + 3 * k2], make_float2(K::c(e), -K::s(e)));
+        }
+    float2 y[9];
+#pragma unroll
+    for (int k2 = 0; k2 < 3; ++k2) {
+        float2 p = x[3 * k2], q = x[1 + 3 * k2], r = x[2 + 3 * k2];
+        mr_dft3<INV>(p, q, r);
+        y[k2] = p;          // k = k2 + 3 k1
+        y[k2 + 3] = q;
+        y[k2 + 6] = r;
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) x[i] = y[i];
+}
+
+template <int R, bool INV> __device__ __forceinline__ void mr_dft(float2 (&x)[R])
+{
+    if constexpr (R == 9) mr_dft9<INV>(x);
+    else mr_dft_prime<R, INV>(x);
+}
+
+// ---------------------------------------------------------------- passes
+// One pass over NF transforms of length P stored at buf + f P: radix R on
+// sub-transforms of length S (M = S / R butterflies each).  DIT: twiddles
+// before the radix-R DFT (transposed algorithm), else after it.
+template <int P, int R, int S, bool DIT, bool INV, int NF>
+__device__ __forceinline__ void mr_pass(float2 *buf, const float2 *__restrict__ tw)
+{
+    constexpr int M = S / R, NB = P / R, STP = P / S;
+    for (int i = threadIdx.x; i < NF * NB; i += blockDim.x) {
+        const int f = i / NB, r = i - f * NB;
+        const int blk = r / M, j = r - blk * M;
+        float2 *a = buf + f * P + blk * S + j;
+        float2 x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = a[q * M];
+        if (DIT && M > 1 && j > 0) {
+#pragma unroll
+            for (int s = 1; s < R; ++s) x[s] = mr_twiddle<INV>(x[s], __ldg(tw + STP * j * s));
+        }
+        mr_dft<R, INV>(x);
+        if (!DIT && M > 1 && j > 0) {
+#pragma unroll
+            for (int s = 1; s < R; ++s) x[s] = mr_twiddle<INV>(x[s], __ldg(tw + STP * j * s));
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) a[q * M] = x[q];
+    }
+    __syncthreads();
+}
+
+template <int P, int I, bool INV, int NF> __device__ __forceinline__ void mr_dif_from(float2 *buf, const float2 *tw)
+{
+    constexpr MrFactors F = mr_factors(P);
+    if constexpr (I < F.n) {
+        mr_pass<P, F.r[I], mr_sub(P, I), false, INV, NF>(buf, tw);
+        mr_dif_from<P, I + 1, INV, NF>(buf, tw);
+    }
+}
+template <int P, int I, bool INV, int NF> __device__ __forceinline__ void mr_dit_from(float2 *buf, const float2 *tw)
+{
+    constexpr MrFactors F = mr_factors(P);
+    if constexpr (I >= 0) {
+        mr_pass<P, F.r[I], mr_sub(P, I), true, INV, NF>(buf, tw);
+        mr_dit_from<P, I - 1, INV, NF>(buf, tw);
+    }
+}
+
+// NF transforms X_k = sum_n x_n e^{-+2 pi i n k / P} (unnormalised): natural
+// order in, X_k at rev[k] out.  The caller synchronises before the call.
+template <int P, bool INV, int NF> __device__ __forceinline__ void mr_fft_dif(float2 *buf, const float2 *tw)
+{
+    static_assert(mr_factors(P).n > 0, "P must factor into 3, 5, 7, 9, 11, 13");
+    mr_dif_from<P, 0, INV, NF>(buf, tw);
+}
+// The same transforms from X_k held at rev[k], natural order out.
+template <int P, bool INV, int NF> __device__ __forceinline__ void mr_fft_dit(float2 *buf, const float2 *tw)
+{
+    static_assert(mr_factors(P).n > 0, "P must factor into 3, 5, 7, 9, 11, 13");
+    mr_dit_from<P, mr_factors(P).n - 1, INV, NF>(buf, tw);
+}
+
+// ---------------------------------------------------------------- S1 / S6 for real maps
+// Eight rings per block, packed two by two as four complex sequences
+// z = f(theta_a, .) + i f(theta_b, .); the spectra are written (read) order-major,
+// F[b][m][t], t contiguous, so no transpose pass is needed: the eight rings of
+// a block are 64 contiguous bytes of every order's row.
+constexpr int MR_RINGS = 8;
+constexpr int MR_THREADS = 512;
+template <int P> constexpr size_t mr_ring_smem() { return (size_t)(MR_RINGS / 2) * P * sizeof(float2); }
+
+// F_m(theta_t) = scale sum_p f(theta_t, phi_p) e^{-i m phi_p}, m < N; grid (ceil(N/8), maps)
+template <int P>
+__global__ void __launch_bounds__(MR_THREADS) k_ring_fwd_real_mr(const float *__restrict__ f, float2 *__restrict__ F,
+                                                                 float scale, MrTab T)
+{
+    constexpr int N = (P + 1) / 2, NF = MR_RINGS / 2;
+    extern __shared__ __align__(16) float2 mr_buf[];
+    const int b = blockIdx.y, t0 = blockIdx.x * MR_RINGS;
+    const float *src = f + (size_t)b * N * P;
+    for (int i = threadIdx.x; i < NF * P; i += blockDim.x) {
+        const int q = i / P, p = i - q * P;
+        const int ta = t0 + 2 * q;
+        const float re = ta < N ? src[(size_t)ta * P + p] : 0.f;
+        const float im = ta + 1 < N ? src[(size_t)(ta + 1) * P + p] : 0.f;
+        mr_buf[i] = make_float2(re, im);
+    }
+    __syncthreads();
+    mr_fft_dif<P, false, NF>(mr_buf, T.tw);
+    // X_a(m) = (Z_m + conj Z_{P-m}) / 2, X_b(m) = (Z_m - conj Z_{P-m}) / (2i)
+    const float s = 0.5f * scale;
+    float2 *out = F + (size_t)b * N * N;
+    for (int i = threadIdx.x; i < N * NF; i += blockDim.x) {
+        const int m = i / NF, q = i - m * NF;
+        const int ta = t0 + 2 * q;
+        if (ta >= N) continue;
+        const float2 zk = mr_buf[q * P + __ldg(T.rev + m)];
+        const float2 zp = mr_buf[q * P + __ldg(T.rev + (m ? P - m : 0))];
+        const float2 xa = make_float2((zk.x + zp.x) * s, (zk.y - zp.y) * s);
+        const float2 xb = make_float2((zk.y + zp.y) * s, (zp.x - zk.x) * s);
+        float2 *o = out + (size_t)m * N + ta;
+        if ((N & 1) == 0) {                      // ta + 1 < N and 16-byte alignment
+            *reinterpret_cast<float4 *>(o) = make_float4(xa.x, xa.y, xb.x, xb.y);
+        } else {
+            o[0] = xa;
+            if (ta + 1 < N) o[1] = xb;
+        }
+    }
+}
+
+// f(theta_t, phi_p) = scale sum_m F_m(theta_t) e^{i m phi_p} with F_{-m} = conj F_m
+template <int P>
+__global__ void __launch_bounds__(MR_THREADS) k_ring_inv_real_mr(const float2 *__restrict__ F, float *__restrict__ f,
+                                                                 float scale, MrTab T)
+{
+    constexpr int N = (P + 1) / 2, NF = MR_RINGS / 2;
+    extern __shared__ __align__(16) float2 mr_buf[];
+    const int b = blockIdx.y, t0 = blockIdx.x * MR_RINGS;
+    const float2 *in = F + (size_t)b * N * N;
+    for (int i = threadIdx.x; i < N * NF; i += blockDim.x) {
+        const int m = i / NF, q = i - m * NF;
+        const int ta = t0 + 2 * q;
+        float2 xa = make_float2(0.f, 0.f), xb = xa;
+        const float2 *s = in + (size_t)m * N + ta;
+        if ((N & 1) == 0 && ta < N) {
+            const float4 v = *reinterpret_cast<const float4 *>(s);
+            xa = make_float2(v.x, v.y);
+            xb = make_float2(v.z, v.w);
+        } else {
+            if (ta < N) xa = s[0];
+            if (ta + 1 < N) xb = s[1];
+        }
+        // Z_m = xa + i xb, Z_{P-m} = conj(xa) + i conj(xb)
+        mr_buf[q * P + m] = make_float2(xa.x - xb.y, xa.y + xb.x);
+        if (m) mr_buf[q * P + P - m] = make_float2(xa.x + xb.y, xb.x - xa.y);
+    }
+    __syncthreads();
+    mr_fft_dif<P, true, NF>(mr_buf, T.tw);
+    float *dst = f + (size_t)b * N * P;
+    for (int i = threadIdx.x; i < NF * P; i += blockDim.x) {
+        const int q = i / P, p = i - q * P;
+        const int ta = t0 + 2 * q;
+        if (ta >= N) continue;
+        const float2 z = mr_buf[q * P + __ldg(T.rev + p)];
+        dst[(size_t)ta * P + p] = z.x * scale;
+        if (ta + 1 < N) dst[(size_t)(ta + 1) * P + p] = z.y * scale;
+    }
+}
+
+// ---------------------------------------------------------------- S2: theta quadrature
+// The MW quadrature of one column x_t = F_m(theta_t), t < N (parity sigma =
+// (-1)^m), as four length-P DFTs.  On the 2P-point grid phi_u = pi u / P the
+// product of two trigonometric polynomials of degree N - 1 is integrated exactly
+// against sin(theta) on [0, pi] by real weights v_u (their Fourier coefficients
+// are w(c) = int_0^pi e^{i c theta} sin(theta) dtheta for |c| <= P - 1).  The odd
+// points phi_{2t+1} are the rings theta_t; the even points are the rings shifted
+// by -pi/P, where band-limited values come from the shift K (DFT, phase
+// e^{-i a pi/P}, inverse DFT).  So with the extension x~ to the circle
+//   G~ = v_odd * x~ + K^T (v_even * (K x~)),   K^T = shift by +pi/P,
+// and the fold G_t = G~_t + sigma G~_{P-1-t} (t < N - 1) gives the same linear map
+// as the dense G = Q_sigma F (both are fixed by the integrals against every
+// trigonometric polynomial of degree N - 1).  With x~_{P-1-t} = sigma x_t the
+// v_odd term folds to vfold_t x_t.  CPB columns per block; columns are the rows
+// [b][mi] of the order-major spectra, m = mi - m_offset.
+template <int P> constexpr int mr_quad_cpb() { return P > 2048 ? 4 : 8; }
+template <int P> constexpr size_t mr_quad_smem() { return (size_t)mr_quad_cpb<P>() * P * sizeof(float2); }
+
+template <int P>
+__global__ void __launch_bounds__(MR_THREADS) k_quad_mr(const float2 *__restrict__ Fin, float2 *__restrict__ Gout,
+                                                        int nmi, int m_offset, int ncols, MrTab T)
+{
+    constexpr int N = (P + 1) / 2, CPB = mr_quad_cpb<P>();
+    extern __shared__ __align__(16) float2 mr_buf[];
+    const int c0 = blockIdx.x * CPB;
+    // extension to the circle
+    for (int i = threadIdx.x; i < CPB * P; i += blockDim.x) {
+        const int q = i / P, t = i - q * P, col = c0 + q;
+        float2 v = make_float2(0.f, 0.f);
+        if (col < ncols) {
+            const float2 *x = Fin + (size_t)col * N;
+            if (t < N) {
+                v = x[t];
+            } else {
+                const int m = col % nmi - m_offset;
+                v = x[P - 1 - t];
+                if (m & 1) v = make_float2(-v.x, -v.y);
+            }
+        }
+        mr_buf[i] = v;
+    }
+    __syncthreads();
+    // K x~: DFT, shift phases, inverse DFT (its 1/P is in ve)
+    mr_fft_dif<P, false, CPB>(mr_buf, T.tw);
+    for (int i = threadIdx.x; i < CPB * P; i += blockDim.x) {
+        const float2 w = __ldg(T.shm + (i % P));
+        mr_buf[i] = mr_twiddle<false>(mr_buf[i], w);
+    }
+    __syncthreads();
+    mr_fft_dit<P, true, CPB>(mr_buf, T.tw);
+    for (int i = threadIdx.x; i < CPB * P; i += blockDim.x) {
+        const float v = __ldg(T.ve + (i % P));
+        mr_buf[i].x *= v;
+        mr_buf[i].y *= v;
+    }
+    __syncthreads();
+    // K^T: DFT, conjugate phases (with 1/P), inverse DFT
+    mr_fft_dif<P, false, CPB>(mr_buf, T.tw);
+    for (int i = threadIdx.x; i < CPB * P; i += blockDim.x) {
+        const float2 w = __ldg(T.shp + (i % P));
+        mr_buf[i] = mr_twiddle<false>(mr_buf[i], w);
+    }
+    __syncthreads();
+    mr_fft_dit<P, true, CPB>(mr_buf, T.tw);
+    // fold, plus the odd-point term
+    for (int i = threadIdx.x; i < CPB * N; i += blockDim.x) {
+        const int q = i / N, t = i - q * N, col = c0 + q;
+        if (col >= ncols) continue;
+        const int m = col % nmi - m_offset;
+        float2 g = mr_buf[q * P + t];
+        if (t < N - 1) {
+            const float2 h = mr_buf[q * P + P - 1 - t];
+            g.x += (m & 1) ? -h.x : h.x;
+            g.y += (m & 1) ? -h.y : h.y;
+        }
+        const float2 x = Fin[(size_t)col * N + t];
+        const float vf = __ldg(T.vfold + t);
+        Gout[(size_t)col * N + t] = make_float2(fmaf(vf, x.x, g.x), fmaf(vf, x.y, g.y));
+    }
+}
+
+}  // namespace s2g

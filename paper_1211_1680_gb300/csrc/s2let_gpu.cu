@@ -24,6 +24,7 @@
 
 #include "../../include/s2let_gpu.h"
 #include "fft.cuh"
+#include "fft_mr.cuh"
 #include "gemm_fp32.cuh"
 #include "tc_kernels.cuh"
 #include "legendre_tc.cuh"
@@ -68,6 +69,11 @@ void dm_free(const DevAlloc &a, void *p)
     else cudaFree(p);
 }
 
+template <typename K> void allow_smem_p(K kernel, size_t bytes)
+{
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 template <typename T>
 T *dev_upload(const DevAlloc &mem, const std::vector<T> &h, std::vector<void *> &owned, int &err)
 {
@@ -108,6 +114,11 @@ struct BandDev {
     // stage in TF32X3 plans, and the ring-DFT block size (0: M/16)
     bool tc_quad = true, tc_anal = true, tc_synth = true;
     int fft_th = 0;
+    // FP32 / TF32X3 plans, P = 2N - 1 with a mixed-radix kernel (fft_mr.cuh): ring
+    // DFTs of real maps on the P samples, and the theta quadrature in its FFT form
+    // (mr_quad; else the dense product)
+    bool has_mr = false, mr_quad = true;
+    MrTab mr{};
 };
 
 }  // namespace
@@ -226,6 +237,85 @@ template <> LegTab<float> leg_tab<float>(const s2let_plan *p, const BandDev &b)
     return t;
 }
 
+// ------------------------------------------------------------ mixed-radix kernels
+// Launches KERNEL<P> for the P of the band (one of S2G_MR_LENGTHS).
+#define S2G_MR_CASE(P_)                                                        \
+    case P_:                                                                   \
+        S2G_MR_LAUNCH(P_);                                                     \
+        break;
+#define S2G_MR_SWITCH(P) \
+    switch (P) { S2G_MR_LENGTHS(S2G_MR_CASE) default: break; }
+
+template <int P> void mr_set_smem()
+{
+    allow_smem_p(k_ring_fwd_real_mr<P>, mr_ring_smem<P>());
+    allow_smem_p(k_ring_inv_real_mr<P>, mr_ring_smem<P>());
+    allow_smem_p(k_quad_mr<P>, mr_quad_smem<P>());
+}
+
+// Position of X_k after the forward passes (mixed-radix digit reversal):
+// pos(k) = (P / R1) (k mod R1) + pos'(k div R1) over the remaining radices.
+int mr_pos(int k, int P, const MrFactors &f, int i)
+{
+    if (i >= f.n) return 0;
+    const int R = f.r[i], M = P / R;
+    return M * (k % R) + mr_pos(k / R, M, f, i + 1);
+}
+
+// Tables of fft_mr.cuh for band-limit N, in FP64 rounded to FP32.
+int build_mr_tables(s2let_plan *p, int N, BandDev &bd)
+{
+    const int P = 2 * N - 1;
+    const MrFactors f = mr_factors(P);
+    std::vector<float2> tw(P), shm(P), shp(P);
+    std::vector<int> rev(P);
+    for (int k = 0; k < P; ++k) {
+        double sn, cs;
+        s2h::sincospi_rat(2 * (int64_t)k, P, &sn, &cs);           // 2 pi k / P
+        tw[k] = make_float2((float)cs, (float)-sn);
+        rev[k] = mr_pos(k, P, f, 0);
+    }
+    for (int k = 0; k < P; ++k) {
+        const int a = k < N ? k : k - P;
+        double sn, cs;
+        s2h::sincospi_rat(a, P, &sn, &cs);                        // a pi / P
+        shm[rev[k]] = make_float2((float)cs, (float)-sn);
+        shp[rev[k]] = make_float2((float)(cs / P), (float)(sn / P));
+    }
+    // weights on phi_u = pi u / P, u < 2P: v_u = (1/2) sum_{|c| <= P-1} w(c) e^{-i c phi_u}
+    //   = 1 + sum_{c = 2, 4, .., P-1} 2 cos(c phi_u) / (1 - c^2) + (pi/2) sin(phi_u),
+    // so that sum_u v_u g(phi_u) = P int_0^pi g(theta) sin(theta) dtheta for every
+    // trigonometric polynomial g of degree <= P - 1 (the scale of the dense Q)
+    std::vector<double> v(2 * P);
+    for (int u = 0; u < 2 * P; ++u) {
+        double s1, c1, s2, c2;
+        s2h::sincospi_rat(u, P, &s1, &c1);                        // phi_u
+        s2h::sincospi_rat(2 * (int64_t)u, P, &s2, &c2);           // 2 phi_u
+        // e^{i c phi} by rotation with e^{2 i phi}; error grows like c eps
+        double re = c2, im = s2, acc = 1.0;
+        for (int c = 2; c <= P - 1; c += 2) {
+            acc += 2.0 * re / (1.0 - (double)c * c);
+            const double nr = re * c2 - im * s2, ni = re * s2 + im * c2;
+            re = nr;
+            im = ni;
+        }
+        v[u] = acc + 0.5 * M_PI * s1;
+    }
+    std::vector<float> ve(P), vfold(N);
+    for (int t = 0; t < P; ++t) ve[t] = (float)(v[2 * t] / P);
+    for (int t = 0; t < N; ++t) vfold[t] = (float)(t < N - 1 ? v[2 * t + 1] + v[2 * (P - 1 - t) + 1] : v[2 * t + 1]);
+    int err = S2LET_OK;
+    auto &o = p->owned;
+    bd.mr.tw = dev_upload(p->mem, tw, o, err);
+    bd.mr.rev = dev_upload(p->mem, rev, o, err);
+    bd.mr.shm = dev_upload(p->mem, shm, o, err);
+    bd.mr.shp = dev_upload(p->mem, shp, o, err);
+    bd.mr.ve = dev_upload(p->mem, ve, o, err);
+    bd.mr.vfold = dev_upload(p->mem, vfold, o, err);
+    if (!err) bd.has_mr = true;
+    return err;
+}
+
 // ------------------------------------------------------------ stage launchers
 template <typename R>
 int run_ring_fwd(const s2let_plan *p, const BandDev &bd, const void *f, void *F, double scale, cudaStream_t st)
@@ -233,6 +323,18 @@ int run_ring_fwd(const s2let_plan *p, const BandDev &bd, const void *f, void *F,
     const auto &T = fft_tab<R>(bd);
     const size_t sm = (size_t)padded_len(bd.M) * sizeof(cplx_t<R>);
     const int th = bd.fft_th ? bd.fft_th : fft_threads(bd.M);
+    if (std::is_same<R, float>::value && !p->cplx && bd.has_mr) {
+        // samples -> order-major spectrum in one kernel
+        StageScope sc(p, S2LET_STAGE_RING_FWD, st, 0.0, map_bytes(p, bd.N) + spectrum_bytes(p, bd.N), 1);
+        const dim3 grid((bd.N + MR_RINGS - 1) / MR_RINGS, p->batch);
+#define S2G_MR_LAUNCH(P_)                                                                                        \
+    k_ring_fwd_real_mr<P_><<<grid, MR_THREADS, mr_ring_smem<P_>(), st>>>((const float *)f, (float2 *)F, (float)scale, \
+                                                                         bd.mr)
+        S2G_MR_SWITCH(bd.P)
+#undef S2G_MR_LAUNCH
+        S2_LAUNCH_CHECK();
+        return S2LET_OK;
+    }
     StageScope sc(p, S2LET_STAGE_RING_FWD, st, 0.0, map_bytes(p, bd.N) + spectrum_bytes(p, bd.N), 2);
     if (p->cplx) {
         k_ring_fwd_cplx<R><<<dim3(bd.N, p->batch), th, sm, st>>>((const cplx_t<R> *)f, (cplx_t<R> *)p->Ft, (R)scale,
@@ -255,6 +357,17 @@ int run_ring_inv(const s2let_plan *p, const BandDev &bd, const void *F, void *f,
     const auto &T = fft_tab<R>(bd);
     const size_t sm = (size_t)padded_len(bd.M) * sizeof(cplx_t<R>);
     const int th = bd.fft_th ? bd.fft_th : fft_threads(bd.M);
+    if (std::is_same<R, float>::value && !p->cplx && bd.has_mr) {
+        StageScope sc(p, S2LET_STAGE_RING_INV, st, 0.0, map_bytes(p, bd.N) + spectrum_bytes(p, bd.N), 1);
+        const dim3 grid((bd.N + MR_RINGS - 1) / MR_RINGS, p->batch);
+#define S2G_MR_LAUNCH(P_)                                                                                        \
+    k_ring_inv_real_mr<P_><<<grid, MR_THREADS, mr_ring_smem<P_>(), st>>>((const float2 *)F, (float *)f, (float)scale, \
+                                                                         bd.mr)
+        S2G_MR_SWITCH(bd.P)
+#undef S2G_MR_LAUNCH
+        S2_LAUNCH_CHECK();
+        return S2LET_OK;
+    }
     StageScope sc(p, S2LET_STAGE_RING_INV, st, 0.0, map_bytes(p, bd.N) + spectrum_bytes(p, bd.N), 2);
     // F[b][mi][t] -> Ft[b][t][mi]
     const int n = nmi(p, bd.N);
@@ -279,6 +392,18 @@ void *run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream
     const int n = nmi(p, bd.N);
     const int off = p->cplx ? bd.N - 1 : 0;
     *err = S2LET_OK;
+    if (std::is_same<R, float>::value && p->quad_gemm && bd.has_mr && bd.mr_quad) {
+        // FFT form: four length-P DFTs per column
+        StageScope sc(p, S2LET_STAGE_THETA_QUAD, st, 0.0, 2.0 * spectrum_bytes(p, bd.N), 1);
+        const int ncols = n * p->batch;
+#define S2G_MR_LAUNCH(P_)                                                                                     \
+    k_quad_mr<P_><<<(ncols + mr_quad_cpb<P_>() - 1) / mr_quad_cpb<P_>(), MR_THREADS, mr_quad_smem<P_>(), st>>>( \
+        (const float2 *)F, (float2 *)p->G, n, off, ncols, bd.mr)
+        S2G_MR_SWITCH(bd.P)
+#undef S2G_MR_LAUNCH
+        if (cudaGetLastError() != cudaSuccess) *err = S2LET_ERR_CUDA;
+        return p->G;
+    }
     if (std::is_same<R, float>::value && p->quad_gemm) {
         // two products, one per parity of m
         StageScope sc(p, S2LET_STAGE_THETA_QUAD, st, 0.0, 2.0 * spectrum_bytes(p, bd.N), n > 1 ? 2 : 1);
@@ -609,6 +734,9 @@ void set_smem_limits(int Mmax)
     allow_smem(k_theta_quad<double, double, 16>, d);
     allow_smem(k_theta_quad<double, float, 16>, d);
     allow_smem(k_theta_quad<float, float, 16>, f);
+#define S2G_MR_SMEM(P_) mr_set_smem<P_>();
+    S2G_MR_LENGTHS(S2G_MR_SMEM)
+#undef S2G_MR_SMEM
 }
 
 __global__ void k_unit_rows(double2 *X, int N)
@@ -748,6 +876,13 @@ int build_band_dev(s2let_plan *p, int N, BandDev &bd)
     o.push_back(seed);
     bd.ls = (int *)ls;
     bd.seed = (double2 *)seed;
+    if (!p->fp64 && mr_supported(bd.P)) {
+        if ((err = build_mr_tables(p, N, bd))) {
+            dm_free(p->mem, mant);
+            dm_free(p->mem, expo);
+            return err;
+        }
+    }
     if (p->quad_gemm) {
         if ((err = build_quad_matrices(p, bd))) {
             dm_free(p->mem, mant);
@@ -946,11 +1081,17 @@ template <typename R> int autotune_t(s2let_plan *p, cudaStream_t st)
         bd.fft_th = best_th;
         if (p->tc) {
             // each contraction stage: tensor-core kernel or CUDA-core GEMM kernel
+            bd.mr_quad = false;
             bd.tc_quad = true;
             const float q1 = time_best(st, [&] { run_theta_quad<R>(p, bd, p->F, st, &e); });
             bd.tc_quad = false;
             const float q0 = time_best(st, [&] { run_theta_quad<R>(p, bd, p->F, st, &e); });
             bd.tc_quad = q1 <= q0;
+            if (bd.has_mr) {
+                bd.mr_quad = true;
+                const float q2 = time_best(st, [&] { run_theta_quad<R>(p, bd, p->F, st, &e); });
+                bd.mr_quad = q2 <= std::min(q0, q1);
+            }
             bd.tc_synth = true;
             const float s1 = time_best(st, [&] { run_synth<R>(p, bd, p->flm, nullptr, 1.0, p->F, st); });
             bd.tc_synth = false;

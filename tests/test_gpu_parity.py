@@ -199,3 +199,53 @@ def test_autotuned_plan_keeps_parity(prec, real):
     rec = from_dev_map(plan.synthesis(fw_d, fs_d), real)
     assert rel_err(rec, f) < TOL[prec]
     assert plan.status() == 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("L", [4, 8, 23, 32, 33, 50, 158])
+def test_mixed_radix_band_limits(L, prec):
+    """Band-limits whose ring length P = 2L - 1 factors into 3, 5, 7, 9, 11, 13
+    (7, 15, 45, 63, 65, 99, 315) run the mixed-radix ring DFTs (real maps) and
+    the FFT form of the theta quadrature: forward and inverse transforms of
+    three real maps against the oracle, and a not band-limited map forward."""
+    seeds = [61, 62, 63]
+    plan = Plan(L, 2, 0, batch=len(seeds), real=True, multires=True, precision=prec)
+    flm = np.stack([inputs.random_flm(L, s, True, "cl" if L > 30 else "white") for s in seeds])
+    f_ref = np.stack([sht.inverse(x, L, real=True) for x in flm])
+    f_gpu = from_dev_map(plan.sht_inverse(flm_to_dev(flm, plan.dtype)), True)
+    assert rel_err(f_gpu, f_ref) < TOL[prec]
+    g = flm_from_dev(plan.sht_forward(to_dev_map(f_ref, plan.dtype, True)))
+    assert rel_err(g, np.stack([sht.forward(x, L) for x in f_ref])) < TOL[prec]
+    x = np.stack([inputs.random_map((L, 2 * L - 1), 70 + s) for s in range(len(seeds))])
+    g = flm_from_dev(plan.sht_forward(to_dev_map(x, plan.dtype, True)))
+    assert rel_err(g, np.stack([sht.forward(v, L) for v in x])) < TOL[prec]
+    assert plan.status() == 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_mixed_radix_wavelets(prec):
+    """L = 158 (P = 315 = 9 x 7 x 5) with multiresolution bands at 4, 8, 32
+    (mixed radix) and 16, 64, 128 (Bluestein, dense quadrature): analysis maps,
+    synthesis of the oracle's maps, and the adjoint."""
+    L, B, J0 = 158, 2, 1
+    seeds = [81, 82]
+    f = _maps(L, seeds, True, "cl")
+    plan = Plan(L, B, J0, batch=len(seeds), real=True, multires=True, precision=prec)
+    fw_d, fs_d = plan.analysis(to_dev_map(f, plan.dtype, True))
+    ref = [wavelet.analysis(x, L, B, J0, True, True) for x in f]
+    for i, view in enumerate(plan.wavelet_views(fw_d)):
+        assert rel_err(from_dev_map(view, True), np.stack([r[0][i] for r in ref])) < TOL[prec], "scale %d" % (J0 + i)
+    assert rel_err(from_dev_map(fs_d, True), np.stack([r[1] for r in ref])) < TOL[prec]
+    fw_in = torch.cat([to_dev_map(np.stack([r[0][i] for r in ref]), plan.dtype, True).reshape(-1)
+                       for i in range(len(ref[0][0]))])
+    rec = from_dev_map(plan.synthesis(fw_in, to_dev_map(np.stack([r[1] for r in ref]), plan.dtype, True)), True)
+    assert rel_err(rec, f) < TOL[prec]
+    n_scal, n_wav = kernels.bandlimits(L, B, J0, True)
+    gws = [[inputs.random_map((n, 2 * n - 1), 400 * b + i) for i, n in enumerate(n_wav)] for b in range(2)]
+    gss = [inputs.random_map((n_scal, 2 * n_scal - 1), 57 + b) for b in range(2)]
+    gw = torch.cat([to_dev_map(np.stack([g[i] for g in gws]), plan.dtype, True).reshape(-1)
+                    for i in range(len(n_wav))])
+    got = from_dev_map(plan.adjoint(gw, to_dev_map(np.stack(gss), plan.dtype, True)), True)
+    want = np.stack([wavelet.analysis_adjoint(gws[b], gss[b], L, B, J0, True, True) for b in range(2)])
+    assert rel_err(got, want) < TOL[prec]
+    assert plan.status() == 0
