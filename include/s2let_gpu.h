@@ -216,7 +216,9 @@ int s2let_plan_stage_stats(s2let_plan *plan, int stage, int64_t *launches, int64
  * uses the tensor-core kernels and M/16 threads. */
 int s2let_plan_autotune(s2let_plan *plan, void *stream);
 
-/* The choices in force for band-limit N of the plan (1 = tensor-core kernel). */
+/* The choices in force for band-limit N of the plan: 1 = tensor-core kernel,
+ * 0 = CUDA-core kernel; *tc_quad = 2: the theta quadrature runs in its FFT form
+ * (mixed-radix, FP32) instead of a dense product. */
 int s2let_plan_tuning(const s2let_plan *plan, int N, int *tc_quad, int *tc_anal, int *tc_synth,
                       int *fft_threads);
 

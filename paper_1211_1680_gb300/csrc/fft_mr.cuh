@@ -48,6 +48,17 @@ __host__ __device__ constexpr int mr_sub(int P, int i)
     return S;
 }
 
+// Offset of pass i's twiddles in the per-pass table: pass i (radix R, M = S / R)
+// holds w_S^{j s} at (s - 1) M + j, s = 1..R-1, j < M, so that the threads of a
+// pass, which run over consecutive j, read consecutive entries.
+__host__ __device__ constexpr int mr_tw_off(int P, int i)
+{
+    const MrFactors f = mr_factors(P);
+    int off = 0;
+    for (int k = 0; k < i; ++k) off += (f.r[k] - 1) * (mr_sub(P, k) / f.r[k]);
+    return off;
+}
+
 // The band-limits with mixed-radix kernels: P = 2N - 1 in this list.
 #define S2G_MR_LENGTHS(X) X(7) X(15) X(45) X(63) X(65) X(99) X(315) X(4095)
 __host__ __device__ constexpr bool mr_supported(int P)
@@ -56,7 +67,7 @@ __host__ __device__ constexpr bool mr_supported(int P)
 }
 
 // Tables of one length P (device pointers, built on the host in FP64):
-//   tw[k]    = e^{-2 pi i k / P}, k < P
+//   tw       per-pass twiddles (mr_tw_off), w_S = e^{-2 pi i / S}
 //   rev[k]   = position of X_k after the forward passes
 //   shm[p]   = e^{-i a pi / P} at position p = rev[k], a = k (k < N) or k - P:
 //              the half-sample shift theta -> theta - pi/P of the quadrature
@@ -165,93 +176,110 @@ template <int R, bool INV> __device__ __forceinline__ void mr_dft(float2 (&x)[R]
 }
 
 // ---------------------------------------------------------------- passes
-// One pass over NF transforms of length P stored at buf + f P: radix R on
-// sub-transforms of length S (M = S / R butterflies each).  DIT: twiddles
-// before the radix-R DFT (transposed algorithm), else after it.
-template <int P, int R, int S, bool DIT, bool INV, int NF>
-__device__ __forceinline__ void mr_pass(float2 *buf, const float2 *__restrict__ tw)
+// One pass over NF transforms of length P: radix R on sub-transforms of length
+// S (M = S / R butterflies each).  DIT: twiddles before the radix-R DFT
+// (transposed algorithm), else after it.  Element pos of transform f is read
+// with ld(f, pos) and written with st(f, pos, v): shared memory for inner
+// passes, global memory or a product with a table for the first and last.
+template <int P, int R, int S, int TWO, bool DIT, bool INV, int NF, class LD, class ST>
+__device__ __forceinline__ void mr_pass(const float2 *__restrict__ twp, LD ld, ST st)
 {
-    constexpr int M = S / R, NB = P / R, STP = P / S;
+    constexpr int M = S / R, NB = P / R;
+    const float2 *tw = twp + TWO;
     for (int i = threadIdx.x; i < NF * NB; i += blockDim.x) {
         const int f = i / NB, r = i - f * NB;
         const int blk = r / M, j = r - blk * M;
-        float2 *a = buf + f * P + blk * S + j;
+        const int base = blk * S + j;
         float2 x[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) x[q] = a[q * M];
+        for (int q = 0; q < R; ++q) x[q] = ld(f, base + q * M);
         if (DIT && M > 1 && j > 0) {
 #pragma unroll
-            for (int s = 1; s < R; ++s) x[s] = mr_twiddle<INV>(x[s], __ldg(tw + STP * j * s));
+            for (int s = 1; s < R; ++s) x[s] = mr_twiddle<INV>(x[s], __ldg(tw + (s - 1) * M + j));
         }
         mr_dft<R, INV>(x);
         if (!DIT && M > 1 && j > 0) {
 #pragma unroll
-            for (int s = 1; s < R; ++s) x[s] = mr_twiddle<INV>(x[s], __ldg(tw + STP * j * s));
+            for (int s = 1; s < R; ++s) x[s] = mr_twiddle<INV>(x[s], __ldg(tw + (s - 1) * M + j));
         }
 #pragma unroll
-        for (int q = 0; q < R; ++q) a[q * M] = x[q];
+        for (int q = 0; q < R; ++q) st(f, base + q * M, x[q]);
     }
     __syncthreads();
 }
 
-template <int P, int I, bool INV, int NF> __device__ __forceinline__ void mr_dif_from(float2 *buf, const float2 *tw)
+// shared-memory element access of NF transforms stored at buf + f P
+template <int P> struct MrSmem {
+    float2 *buf;
+    __device__ __forceinline__ float2 operator()(int f, int pos) const { return buf[f * P + pos]; }
+    __device__ __forceinline__ void operator()(int f, int pos, float2 v) const { buf[f * P + pos] = v; }
+};
+
+// passes I, I+1, .. (DIF) or I, I-1, .. (DIT); the first pass executed loads
+// with ld, the last one stores with st, all others use shared memory
+template <int P, int I, bool DIT, bool INV, int NF, class LD, class ST>
+__device__ __forceinline__ void mr_run(float2 *buf, const float2 *tw, LD ld, ST st)
 {
     constexpr MrFactors F = mr_factors(P);
-    if constexpr (I < F.n) {
-        mr_pass<P, F.r[I], mr_sub(P, I), false, INV, NF>(buf, tw);
-        mr_dif_from<P, I + 1, INV, NF>(buf, tw);
-    }
-}
-template <int P, int I, bool INV, int NF> __device__ __forceinline__ void mr_dit_from(float2 *buf, const float2 *tw)
-{
-    constexpr MrFactors F = mr_factors(P);
-    if constexpr (I >= 0) {
-        mr_pass<P, F.r[I], mr_sub(P, I), true, INV, NF>(buf, tw);
-        mr_dit_from<P, I - 1, INV, NF>(buf, tw);
+    constexpr int first = DIT ? F.n - 1 : 0, last = DIT ? 0 : F.n - 1;
+    if constexpr (I >= 0 && I < F.n) {
+        constexpr int R = F.r[I], S = mr_sub(P, I), TWO = mr_tw_off(P, I);
+        const MrSmem<P> sm{buf};
+        if constexpr (I == first && I == last) mr_pass<P, R, S, TWO, DIT, INV, NF>(tw, ld, st);
+        else if constexpr (I == first) mr_pass<P, R, S, TWO, DIT, INV, NF>(tw, ld, sm);
+        else if constexpr (I == last) mr_pass<P, R, S, TWO, DIT, INV, NF>(tw, sm, st);
+        else mr_pass<P, R, S, TWO, DIT, INV, NF>(tw, sm, sm);
+        mr_run<P, DIT ? I - 1 : I + 1, DIT, INV, NF>(buf, tw, ld, st);
     }
 }
 
-// NF transforms X_k = sum_n x_n e^{-+2 pi i n k / P} (unnormalised): natural
-// order in, X_k at rev[k] out.  The caller synchronises before the call.
+// NF transforms X_k = sum_n x_n e^{-+2 pi i n k / P} (unnormalised): x_n = ld(f, n)
+// in natural order, X_k handed to st(f, rev[k], X_k).  The block synchronises
+// at the end of every pass.
+template <int P, bool INV, int NF, class LD, class ST>
+__device__ __forceinline__ void mr_fft_dif(float2 *buf, const float2 *tw, LD ld, ST st)
+{
+    static_assert(mr_factors(P).n > 0, "P must factor into 3, 5, 7, 9, 11, 13");
+    mr_run<P, 0, false, INV, NF>(buf, tw, ld, st);
+}
 template <int P, bool INV, int NF> __device__ __forceinline__ void mr_fft_dif(float2 *buf, const float2 *tw)
 {
-    static_assert(mr_factors(P).n > 0, "P must factor into 3, 5, 7, 9, 11, 13");
-    mr_dif_from<P, 0, INV, NF>(buf, tw);
+    mr_fft_dif<P, INV, NF>(buf, tw, MrSmem<P>{buf}, MrSmem<P>{buf});
 }
-// The same transforms from X_k held at rev[k], natural order out.
-template <int P, bool INV, int NF> __device__ __forceinline__ void mr_fft_dit(float2 *buf, const float2 *tw)
+// The same transforms from X_k = ld(f, rev[k]), natural order out: st(f, n, x_n).
+template <int P, bool INV, int NF, class LD, class ST>
+__device__ __forceinline__ void mr_fft_dit(float2 *buf, const float2 *tw, LD ld, ST st)
 {
     static_assert(mr_factors(P).n > 0, "P must factor into 3, 5, 7, 9, 11, 13");
-    mr_dit_from<P, mr_factors(P).n - 1, INV, NF>(buf, tw);
+    mr_run<P, mr_factors(P).n - 1, true, INV, NF>(buf, tw, ld, st);
 }
 
 // ---------------------------------------------------------------- S1 / S6 for real maps
-// Eight rings per block, packed two by two as four complex sequences
+// Four rings per block, packed two by two as two complex sequences
 // z = f(theta_a, .) + i f(theta_b, .); the spectra are written (read) order-major,
-// F[b][m][t], t contiguous, so no transpose pass is needed: the eight rings of
-// a block are 64 contiguous bytes of every order's row.
-constexpr int MR_RINGS = 8;
-constexpr int MR_THREADS = 512;
+// F[b][m][t], t contiguous, so no transpose pass is needed: the four rings of a
+// block are 32 contiguous bytes of every order's row.  Three blocks fit an SM.
+constexpr int MR_RINGS = 4;
+constexpr int MR_THREADS = 256;
 template <int P> constexpr size_t mr_ring_smem() { return (size_t)(MR_RINGS / 2) * P * sizeof(float2); }
 
-// F_m(theta_t) = scale sum_p f(theta_t, phi_p) e^{-i m phi_p}, m < N; grid (ceil(N/8), maps)
+// F_m(theta_t) = scale sum_p f(theta_t, phi_p) e^{-i m phi_p}, m < N; grid (ceil(N/4), maps)
 template <int P>
-__global__ void __launch_bounds__(MR_THREADS) k_ring_fwd_real_mr(const float *__restrict__ f, float2 *__restrict__ F,
-                                                                 float scale, MrTab T)
+__global__ void __launch_bounds__(MR_THREADS, 3) k_ring_fwd_real_mr(const float *__restrict__ f,
+                                                                    float2 *__restrict__ F, float scale, MrTab T)
 {
     constexpr int N = (P + 1) / 2, NF = MR_RINGS / 2;
     extern __shared__ __align__(16) float2 mr_buf[];
     const int b = blockIdx.y, t0 = blockIdx.x * MR_RINGS;
     const float *src = f + (size_t)b * N * P;
-    for (int i = threadIdx.x; i < NF * P; i += blockDim.x) {
-        const int q = i / P, p = i - q * P;
+    // the first pass reads the ring pairs from global memory
+    auto ld = [&](int q, int p) -> float2 {
         const int ta = t0 + 2 * q;
         const float re = ta < N ? src[(size_t)ta * P + p] : 0.f;
         const float im = ta + 1 < N ? src[(size_t)(ta + 1) * P + p] : 0.f;
-        mr_buf[i] = make_float2(re, im);
-    }
-    __syncthreads();
-    mr_fft_dif<P, false, NF>(mr_buf, T.tw);
+        return make_float2(re, im);
+    };
+    mr_fft_dif<P, false, NF>(mr_buf, T.tw, ld, MrSmem<P>{mr_buf});
     // X_a(m) = (Z_m + conj Z_{P-m}) / 2, X_b(m) = (Z_m - conj Z_{P-m}) / (2i)
     const float s = 0.5f * scale;
     float2 *out = F + (size_t)b * N * N;
@@ -273,10 +301,12 @@ __global__ void __launch_bounds__(MR_THREADS) k_ring_fwd_real_mr(const float *__
     }
 }
 
-// f(theta_t, phi_p) = scale sum_m F_m(theta_t) e^{i m phi_p} with F_{-m} = conj F_m
+// f(theta_t, phi_p) = scale sum_m F_m(theta_t) e^{i m phi_p} with F_{-m} = conj F_m:
+// the spectra go to their permuted positions, the transposed passes bring the
+// samples out in natural order and the last one writes them to the map rows.
 template <int P>
-__global__ void __launch_bounds__(MR_THREADS) k_ring_inv_real_mr(const float2 *__restrict__ F, float *__restrict__ f,
-                                                                 float scale, MrTab T)
+__global__ void __launch_bounds__(MR_THREADS, 3) k_ring_inv_real_mr(const float2 *__restrict__ F,
+                                                                    float *__restrict__ f, float scale, MrTab T)
 {
     constexpr int N = (P + 1) / 2, NF = MR_RINGS / 2;
     extern __shared__ __align__(16) float2 mr_buf[];
@@ -296,20 +326,17 @@ __global__ void __launch_bounds__(MR_THREADS) k_ring_inv_real_mr(const float2 *_
             if (ta + 1 < N) xb = s[1];
         }
         // Z_m = xa + i xb, Z_{P-m} = conj(xa) + i conj(xb)
-        mr_buf[q * P + m] = make_float2(xa.x - xb.y, xa.y + xb.x);
-        if (m) mr_buf[q * P + P - m] = make_float2(xa.x + xb.y, xb.x - xa.y);
+        mr_buf[q * P + __ldg(T.rev + m)] = make_float2(xa.x - xb.y, xa.y + xb.x);
+        if (m) mr_buf[q * P + __ldg(T.rev + P - m)] = make_float2(xa.x + xb.y, xb.x - xa.y);
     }
     __syncthreads();
-    mr_fft_dif<P, true, NF>(mr_buf, T.tw);
     float *dst = f + (size_t)b * N * P;
-    for (int i = threadIdx.x; i < NF * P; i += blockDim.x) {
-        const int q = i / P, p = i - q * P;
+    auto st = [&](int q, int p, float2 z) {
         const int ta = t0 + 2 * q;
-        if (ta >= N) continue;
-        const float2 z = mr_buf[q * P + __ldg(T.rev + p)];
-        dst[(size_t)ta * P + p] = z.x * scale;
+        if (ta < N) dst[(size_t)ta * P + p] = z.x * scale;
         if (ta + 1 < N) dst[(size_t)(ta + 1) * P + p] = z.y * scale;
-    }
+    };
+    mr_fft_dit<P, true, NF>(mr_buf, T.tw, MrSmem<P>{mr_buf}, st);
 }
 
 // ---------------------------------------------------------------- S2: theta quadrature
@@ -325,67 +352,58 @@ __global__ void __launch_bounds__(MR_THREADS) k_ring_inv_real_mr(const float2 *_
 // and the fold G_t = G~_t + sigma G~_{P-1-t} (t < N - 1) gives the same linear map
 // as the dense G = Q_sigma F (both are fixed by the integrals against every
 // trigonometric polynomial of degree N - 1).  With x~_{P-1-t} = sigma x_t the
-// v_odd term folds to vfold_t x_t.  CPB columns per block; columns are the rows
-// [b][mi] of the order-major spectra, m = mi - m_offset.
-template <int P> constexpr int mr_quad_cpb() { return P > 2048 ? 4 : 8; }
+// v_odd term folds to vfold_t x_t.  The products with the phases and weights
+// ride on the last pass of each transform; the extension on the first.
+// CPB columns per block; columns are the rows [b][mi] of the order-major
+// spectra, m = mi - m_offset.
+template <int P> constexpr int mr_quad_cpb() { return P > 2048 ? 2 : 8; }
 template <int P> constexpr size_t mr_quad_smem() { return (size_t)mr_quad_cpb<P>() * P * sizeof(float2); }
 
 template <int P>
-__global__ void __launch_bounds__(MR_THREADS) k_quad_mr(const float2 *__restrict__ Fin, float2 *__restrict__ Gout,
-                                                        int nmi, int m_offset, int ncols, MrTab T)
+__global__ void __launch_bounds__(MR_THREADS, 3) k_quad_mr(const float2 *__restrict__ Fin, float2 *__restrict__ Gout,
+                                                           int nmi, int m_offset, int ncols, MrTab T)
 {
     constexpr int N = (P + 1) / 2, CPB = mr_quad_cpb<P>();
     extern __shared__ __align__(16) float2 mr_buf[];
+    __shared__ float sgn[CPB];
     const int c0 = blockIdx.x * CPB;
-    // extension to the circle
-    for (int i = threadIdx.x; i < CPB * P; i += blockDim.x) {
-        const int q = i / P, t = i - q * P, col = c0 + q;
-        float2 v = make_float2(0.f, 0.f);
-        if (col < ncols) {
-            const float2 *x = Fin + (size_t)col * N;
-            if (t < N) {
-                v = x[t];
-            } else {
-                const int m = col % nmi - m_offset;
-                v = x[P - 1 - t];
-                if (m & 1) v = make_float2(-v.x, -v.y);
-            }
-        }
-        mr_buf[i] = v;
+    if (threadIdx.x < CPB) {
+        const int col = c0 + threadIdx.x;
+        sgn[threadIdx.x] = (col < ncols && ((col % nmi - m_offset) & 1)) ? -1.f : 1.f;
     }
     __syncthreads();
-    // K x~: DFT, shift phases, inverse DFT (its 1/P is in ve)
-    mr_fft_dif<P, false, CPB>(mr_buf, T.tw);
-    for (int i = threadIdx.x; i < CPB * P; i += blockDim.x) {
-        const float2 w = __ldg(T.shm + (i % P));
-        mr_buf[i] = mr_twiddle<false>(mr_buf[i], w);
-    }
-    __syncthreads();
-    mr_fft_dit<P, true, CPB>(mr_buf, T.tw);
-    for (int i = threadIdx.x; i < CPB * P; i += blockDim.x) {
-        const float v = __ldg(T.ve + (i % P));
-        mr_buf[i].x *= v;
-        mr_buf[i].y *= v;
-    }
-    __syncthreads();
+    const MrSmem<P> sm{mr_buf};
+    // K x~: DFT of the extension (read from global memory), shift phases, inverse DFT
+    auto ext = [&](int q, int t) -> float2 {
+        const int col = c0 + q;
+        if (col >= ncols) return make_float2(0.f, 0.f);
+        const float2 *x = Fin + (size_t)col * N;
+        if (t < N) return x[t];
+        const float2 v = x[P - 1 - t];
+        return make_float2(sgn[q] * v.x, sgn[q] * v.y);
+    };
+    mr_fft_dif<P, false, CPB>(mr_buf, T.tw, ext, [&](int q, int pos, float2 v) {
+        mr_buf[q * P + pos] = mr_twiddle<false>(v, __ldg(T.shm + pos));
+    });
+    // (its 1/P is in ve) times the weights of the shifted points
+    mr_fft_dit<P, true, CPB>(mr_buf, T.tw, sm, [&](int q, int t, float2 v) {
+        const float w = __ldg(T.ve + t);
+        mr_buf[q * P + t] = make_float2(v.x * w, v.y * w);
+    });
     // K^T: DFT, conjugate phases (with 1/P), inverse DFT
-    mr_fft_dif<P, false, CPB>(mr_buf, T.tw);
-    for (int i = threadIdx.x; i < CPB * P; i += blockDim.x) {
-        const float2 w = __ldg(T.shp + (i % P));
-        mr_buf[i] = mr_twiddle<false>(mr_buf[i], w);
-    }
-    __syncthreads();
-    mr_fft_dit<P, true, CPB>(mr_buf, T.tw);
+    mr_fft_dif<P, false, CPB>(mr_buf, T.tw, sm, [&](int q, int pos, float2 v) {
+        mr_buf[q * P + pos] = mr_twiddle<false>(v, __ldg(T.shp + pos));
+    });
+    mr_fft_dit<P, true, CPB>(mr_buf, T.tw, sm, sm);
     // fold, plus the odd-point term
     for (int i = threadIdx.x; i < CPB * N; i += blockDim.x) {
         const int q = i / N, t = i - q * N, col = c0 + q;
         if (col >= ncols) continue;
-        const int m = col % nmi - m_offset;
         float2 g = mr_buf[q * P + t];
         if (t < N - 1) {
             const float2 h = mr_buf[q * P + P - 1 - t];
-            g.x += (m & 1) ? -h.x : h.x;
-            g.y += (m & 1) ? -h.y : h.y;
+            g.x = fmaf(sgn[q], h.x, g.x);
+            g.y = fmaf(sgn[q], h.y, g.y);
         }
         const float2 x = Fin[(size_t)col * N + t];
         const float vf = __ldg(T.vfold + t);

@@ -267,14 +267,18 @@ int build_mr_tables(s2let_plan *p, int N, BandDev &bd)
 {
     const int P = 2 * N - 1;
     const MrFactors f = mr_factors(P);
-    std::vector<float2> tw(P), shm(P), shp(P);
+    std::vector<float2> tw(std::max(1, mr_tw_off(P, f.n))), shm(P), shp(P);
     std::vector<int> rev(P);
-    for (int k = 0; k < P; ++k) {
-        double sn, cs;
-        s2h::sincospi_rat(2 * (int64_t)k, P, &sn, &cs);           // 2 pi k / P
-        tw[k] = make_float2((float)cs, (float)-sn);
-        rev[k] = mr_pos(k, P, f, 0);
+    for (int i = 0; i < f.n; ++i) {
+        const int R = f.r[i], S = mr_sub(P, i), M = S / R, off = mr_tw_off(P, i);
+        for (int s = 1; s < R; ++s)
+            for (int j = 0; j < M; ++j) {
+                double sn, cs;
+                s2h::sincospi_rat(2 * (int64_t)j * s, S, &sn, &cs);   // 2 pi j s / S
+                tw[off + (s - 1) * M + j] = make_float2((float)cs, (float)-sn);
+            }
     }
+    for (int k = 0; k < P; ++k) rev[k] = mr_pos(k, P, f, 0);
     for (int k = 0; k < P; ++k) {
         const int a = k < N ? k : k - P;
         double sn, cs;
@@ -1314,7 +1318,7 @@ int s2let_plan_tuning(const s2let_plan *p, int N, int *tc_quad, int *tc_anal, in
     auto it = p->bands.find(N);
     if (it == p->bands.end()) return S2LET_ERR_ARG;
     const BandDev &bd = it->second;
-    if (tc_quad) *tc_quad = p->tc && bd.tc_quad;
+    if (tc_quad) *tc_quad = (!p->fp64 && p->quad_gemm && bd.has_mr && bd.mr_quad) ? 2 : (p->tc && bd.tc_quad);
     if (tc_anal) *tc_anal = p->tc && bd.tc_anal;
     if (tc_synth) *tc_synth = p->tc && bd.tc_synth;
     if (fft_threads_out) *fft_threads_out = bd.fft_th ? bd.fft_th : fft_threads(bd.M);

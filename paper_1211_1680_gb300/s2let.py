@@ -112,13 +112,13 @@ class Plan:
         return self.tuning()
 
     def tuning(self):
-        """{band-limit: {"tc_quad", "tc_anal", "tc_synth": bool, "fft_threads": int}}."""
+        """{band-limit: {"tc_quad", "fft_quad", "tc_anal", "tc_synth": bool, "fft_threads": int}}."""
         out = {}
         for n in sorted({self.L, self.N_scal} | {s[1] for s in self.scales}):
             v = [ctypes.c_int() for _ in range(4)]
             check("s2let_plan_tuning", _lib.lib().s2let_plan_tuning(self._h, n, *[ctypes.byref(x) for x in v]))
-            out[n] = {"tc_quad": bool(v[0].value), "tc_anal": bool(v[1].value), "tc_synth": bool(v[2].value),
-                      "fft_threads": v[3].value}
+            out[n] = {"tc_quad": v[0].value == 1, "fft_quad": v[0].value == 2, "tc_anal": bool(v[1].value),
+                      "tc_synth": bool(v[2].value), "fft_threads": v[3].value}
         return out
 
     def status(self):

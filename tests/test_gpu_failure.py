@@ -70,7 +70,9 @@ def test_plan_memory_from_the_hook():
     hook = _Counting()
     plan = _create_with(hook)
     n = hook.calls
-    assert n > 10 and len(hook.live) == n          # every table and buffer came from the hook
+    # every table and buffer came from the hook (the temporaries of plan creation
+    # went back to it already)
+    assert n > 10 and 10 < len(hook.live) < n
     assert _inverse_parity(plan, 40) < TOL["tf32x3"]
     plan.close()
     assert hook.live == {}                          # and went back to it
