@@ -69,6 +69,9 @@ extern "C" {
 #define S2LET_TC_SPLIT3 0x200    /* TF32X3 plans only: split operands in three
                                     TF32 parts (6 MMAs per product) instead of
                                     two (3 MMAs)                               */
+#define S2LET_QUAD_DENSE 0x800   /* FP32 / TF32X3 plans: the dense quadrature
+                                    product at every band-limit, also where the
+                                    FFT form (mixed-radix ring length) exists  */
 #define S2LET_KERNEL_BSPLINE 0x400 /* B-spline generating functions (footnote of
                                     Sect. 2.2) instead of the smooth scale-
                                     discretised ones: k(t) = 3/2 B_3(2 t B^(J-1)

@@ -24,6 +24,7 @@ S2LET_PREC_TF32X3 = 0x20
 S2LET_QUAD_FFT64 = 0x100
 S2LET_TC_SPLIT3 = 0x200
 S2LET_KERNEL_BSPLINE = 0x400
+S2LET_QUAD_DENSE = 0x800
 
 # every symbol the header declares, with (restype, argtypes)
 _vp = ctypes.c_void_p

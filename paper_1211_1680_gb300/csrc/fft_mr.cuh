@@ -354,30 +354,52 @@ __global__ void __launch_bounds__(MR_THREADS, 3) k_ring_inv_real_mr(const float2
 // trigonometric polynomial of degree N - 1).  With x~_{P-1-t} = sigma x_t the
 // v_odd term folds to vfold_t x_t.  The products with the phases and weights
 // ride on the last pass of each transform; the extension on the first.
-// CPB columns per block; columns are the rows [b][mi] of the order-major
-// spectra, m = mi - m_offset.
+// In FP32 the FFT form spreads each column's rounding error evenly over theta,
+// where the dense product keeps it local; for the smallest orders, whose
+// Legendre functions are largest at the poles, that raised the error of the
+// finest wavelet maps at L = 2048 near the poles tenfold, to 1.8e-5.  So the
+// orders |m| <= MR_QUAD_DENSE_M stay with the dense product (measured at L =
+// 2048: 8.6e-7 with that split, 1.1e-6 all dense) and this kernel takes the rest.
+// CPB columns per block; column c of map b is the row [b][mi] of the
+// order-major spectra with mi = mstart + r + (r >= seg0 ? gap : 0), r = c mod K
+// (K columns per map), m = mi - m_offset.
+constexpr int MR_QUAD_DENSE_M = 32;
 template <int P> constexpr int mr_quad_cpb() { return P > 2048 ? 2 : 8; }
 template <int P> constexpr size_t mr_quad_smem() { return (size_t)mr_quad_cpb<P>() * P * sizeof(float2); }
 
+struct MrCols {
+    int nmi, m_offset, K, mstart, seg0, gap, ncols;
+};
+
 template <int P>
 __global__ void __launch_bounds__(MR_THREADS, 3) k_quad_mr(const float2 *__restrict__ Fin, float2 *__restrict__ Gout,
-                                                           int nmi, int m_offset, int ncols, MrTab T)
+                                                           MrCols C, MrTab T)
 {
     constexpr int N = (P + 1) / 2, CPB = mr_quad_cpb<P>();
     extern __shared__ __align__(16) float2 mr_buf[];
     __shared__ float sgn[CPB];
+    __shared__ int rowof[CPB];       // [b][mi] row of each column of the block, -1 past the end
     const int c0 = blockIdx.x * CPB;
     if (threadIdx.x < CPB) {
-        const int col = c0 + threadIdx.x;
-        sgn[threadIdx.x] = (col < ncols && ((col % nmi - m_offset) & 1)) ? -1.f : 1.f;
+        const int c = c0 + threadIdx.x;
+        int row = -1;
+        float sg = 1.f;
+        if (c < C.ncols) {
+            const int b = c / C.K, r = c - b * C.K;
+            const int mi = C.mstart + r + (r >= C.seg0 ? C.gap : 0);
+            row = b * C.nmi + mi;
+            sg = ((mi - C.m_offset) & 1) ? -1.f : 1.f;
+        }
+        rowof[threadIdx.x] = row;
+        sgn[threadIdx.x] = sg;
     }
     __syncthreads();
     const MrSmem<P> sm{mr_buf};
     // K x~: DFT of the extension (read from global memory), shift phases, inverse DFT
     auto ext = [&](int q, int t) -> float2 {
-        const int col = c0 + q;
-        if (col >= ncols) return make_float2(0.f, 0.f);
-        const float2 *x = Fin + (size_t)col * N;
+        const int row = rowof[q];
+        if (row < 0) return make_float2(0.f, 0.f);
+        const float2 *x = Fin + (size_t)row * N;
         if (t < N) return x[t];
         const float2 v = x[P - 1 - t];
         return make_float2(sgn[q] * v.x, sgn[q] * v.y);
@@ -397,17 +419,17 @@ __global__ void __launch_bounds__(MR_THREADS, 3) k_quad_mr(const float2 *__restr
     mr_fft_dit<P, true, CPB>(mr_buf, T.tw, sm, sm);
     // fold, plus the odd-point term
     for (int i = threadIdx.x; i < CPB * N; i += blockDim.x) {
-        const int q = i / N, t = i - q * N, col = c0 + q;
-        if (col >= ncols) continue;
+        const int q = i / N, t = i - q * N, row = rowof[q];
+        if (row < 0) continue;
         float2 g = mr_buf[q * P + t];
         if (t < N - 1) {
             const float2 h = mr_buf[q * P + P - 1 - t];
             g.x = fmaf(sgn[q], h.x, g.x);
             g.y = fmaf(sgn[q], h.y, g.y);
         }
-        const float2 x = Fin[(size_t)col * N + t];
+        const float2 x = Fin[(size_t)row * N + t];
         const float vf = __ldg(T.vfold + t);
-        Gout[(size_t)col * N + t] = make_float2(fmaf(vf, x.x, g.x), fmaf(vf, x.y, g.y));
+        Gout[(size_t)row * N + t] = make_float2(fmaf(vf, x.x, g.x), fmaf(vf, x.y, g.y));
     }
 }
 

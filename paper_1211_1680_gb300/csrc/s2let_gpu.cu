@@ -396,25 +396,20 @@ void *run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream
     const int n = nmi(p, bd.N);
     const int off = p->cplx ? bd.N - 1 : 0;
     *err = S2LET_OK;
-    if (std::is_same<R, float>::value && p->quad_gemm && bd.has_mr && bd.mr_quad) {
-        // FFT form: four length-P DFTs per column
-        StageScope sc(p, S2LET_STAGE_THETA_QUAD, st, 0.0, 2.0 * spectrum_bytes(p, bd.N), 1);
-        const int ncols = n * p->batch;
-#define S2G_MR_LAUNCH(P_)                                                                                     \
-    k_quad_mr<P_><<<(ncols + mr_quad_cpb<P_>() - 1) / mr_quad_cpb<P_>(), MR_THREADS, mr_quad_smem<P_>(), st>>>( \
-        (const float2 *)F, (float2 *)p->G, n, off, ncols, bd.mr)
-        S2G_MR_SWITCH(bd.P)
-#undef S2G_MR_LAUNCH
-        if (cudaGetLastError() != cudaSuccess) *err = S2LET_ERR_CUDA;
-        return p->G;
-    }
     if (std::is_same<R, float>::value && p->quad_gemm) {
-        // two products, one per parity of m
-        StageScope sc(p, S2LET_STAGE_THETA_QUAD, st, 0.0, 2.0 * spectrum_bytes(p, bd.N), n > 1 ? 2 : 1);
+        // Dense products G = Q_sigma F, one per parity of m, over all orders, or
+        // with the FFT form over |m| > MR_QUAD_DENSE_M only (see fft_mr.cuh)
+        const bool fft = bd.has_mr && bd.mr_quad && bd.N - 1 > MR_QUAD_DENSE_M;
+        const int mcut = fft ? MR_QUAD_DENSE_M : bd.N;
+        const int lo = p->cplx ? std::max(0, bd.N - 1 - mcut) : 0;
+        const int hi = p->cplx ? std::min(n - 1, bd.N - 1 + mcut) : std::min(n - 1, mcut);
+        StageScope sc(p, S2LET_STAGE_THETA_QUAD, st, 0.0, 2.0 * spectrum_bytes(p, bd.N), (fft ? 1 : 0) + 2);
         for (int par = 0; par < 2; ++par) {
-            int mi0 = p->cplx ? (((bd.N - 1) & 1) ^ par) : par;
-            if (mi0 >= n) continue;
-            const int nj = (n - 1 - mi0) / 2 + 1;
+            // first row at or after lo whose order has parity par
+            const int want = p->cplx ? (((bd.N - 1) & 1) ^ par) : par;
+            const int mi0 = lo + ((want - lo) & 1);
+            if (mi0 > hi) continue;
+            const int nj = (hi - mi0) / 2 + 1;
             const int npairs = nj * p->batch;
             dim3 grid((bd.N + QG_BM - 1) / QG_BM, (npairs + QG_BN / 2 - 1) / (QG_BN / 2));
             if (p->tc && bd.tc_quad && p->tc_split == 2) {
@@ -429,6 +424,28 @@ void *run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream
             else
                 k_quad_gemm<<<grid, 256, 0, st>>>(par ? bd.Qo : bd.Qe, (const float2 *)F, (float2 *)p->G, bd.N, n,
                                                   mi0, nj, npairs);
+        }
+        if (fft) {
+            MrCols C;
+            C.nmi = n;
+            C.m_offset = off;
+            if (p->cplx) {
+                C.mstart = 0;
+                C.seg0 = bd.N - 1 - mcut;
+                C.gap = 2 * mcut + 1;
+                C.K = 2 * C.seg0;
+            } else {
+                C.mstart = mcut + 1;
+                C.seg0 = n;
+                C.gap = 0;
+                C.K = n - mcut - 1;
+            }
+            C.ncols = C.K * p->batch;
+#define S2G_MR_LAUNCH(P_)                                                                                          \
+    k_quad_mr<P_><<<(C.ncols + mr_quad_cpb<P_>() - 1) / mr_quad_cpb<P_>(), MR_THREADS, mr_quad_smem<P_>(), st>>>( \
+        (const float2 *)F, (float2 *)p->G, C, bd.mr)
+            S2G_MR_SWITCH(bd.P)
+#undef S2G_MR_LAUNCH
         }
         if (cudaGetLastError() != cudaSuccess) *err = S2LET_ERR_CUDA;
         return p->G;
@@ -881,6 +898,7 @@ int build_band_dev(s2let_plan *p, int N, BandDev &bd)
     bd.ls = (int *)ls;
     bd.seed = (double2 *)seed;
     if (!p->fp64 && mr_supported(bd.P)) {
+        bd.mr_quad = !(p->flags & S2LET_QUAD_DENSE);
         if ((err = build_mr_tables(p, N, bd))) {
             dm_free(p->mem, mant);
             dm_free(p->mem, expo);
@@ -912,10 +930,11 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
     const int prec = flags & S2LET_PREC_MASK;
     if (prec != S2LET_PREC_FP64 && prec != S2LET_PREC_FP32 && prec != S2LET_PREC_TF32X3) return S2LET_ERR_ARG;
     if (flags & ~(S2LET_COMPLEX | S2LET_MULTIRES | S2LET_PREC_MASK | S2LET_QUAD_FFT64 | S2LET_TC_SPLIT3 |
-                  S2LET_KERNEL_BSPLINE))
+                  S2LET_KERNEL_BSPLINE | S2LET_QUAD_DENSE))
         return S2LET_ERR_ARG;
     if ((flags & S2LET_TC_SPLIT3) && prec != S2LET_PREC_TF32X3) return S2LET_ERR_ARG;
     if ((flags & S2LET_QUAD_FFT64) && prec == S2LET_PREC_FP64) return S2LET_ERR_ARG;
+    if ((flags & S2LET_QUAD_DENSE) && (prec == S2LET_PREC_FP64 || (flags & S2LET_QUAD_FFT64))) return S2LET_ERR_ARG;
 
     std::unique_ptr<s2let_plan> p(new (std::nothrow) s2let_plan());
     if (!p) return S2LET_ERR_ALLOC;
@@ -1091,7 +1110,7 @@ template <typename R> int autotune_t(s2let_plan *p, cudaStream_t st)
             bd.tc_quad = false;
             const float q0 = time_best(st, [&] { run_theta_quad<R>(p, bd, p->F, st, &e); });
             bd.tc_quad = q1 <= q0;
-            if (bd.has_mr) {
+            if (bd.has_mr && !(p->flags & S2LET_QUAD_DENSE)) {
                 bd.mr_quad = true;
                 const float q2 = time_best(st, [&] { run_theta_quad<R>(p, bd, p->F, st, &e); });
                 bd.mr_quad = q2 <= std::min(q0, q1);

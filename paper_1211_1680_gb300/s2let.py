@@ -8,7 +8,8 @@ import torch
 
 from . import _lib
 from ._lib import (S2LET_COMPLEX, S2LET_MULTIRES, S2LET_PREC_FP32, S2LET_PREC_FP64,  # noqa: F401
-                   S2LET_KERNEL_BSPLINE, S2LET_PREC_TF32X3, S2LET_QUAD_FFT64, S2LET_TC_SPLIT3, check)
+                   S2LET_KERNEL_BSPLINE, S2LET_PREC_TF32X3, S2LET_QUAD_DENSE, S2LET_QUAD_FFT64, S2LET_TC_SPLIT3,
+                   check)
 
 PRECISIONS = {"fp64": S2LET_PREC_FP64, "fp32": S2LET_PREC_FP32, "tf32x3": S2LET_PREC_TF32X3}
 
@@ -72,13 +73,15 @@ class Plan:
     (smooth scale-discretised) or "bspline" (footnote of Sect. 2.2)."""
 
     def __init__(self, L, B, J_min, batch=1, real=True, multires=True, precision="fp64",
-                 quad_fft64=False, tc_split3=False, device=None, kernel="sd"):
+                 quad_fft64=False, tc_split3=False, device=None, kernel="sd", quad_dense=False):
         flags = (0 if real else S2LET_COMPLEX) | (S2LET_MULTIRES if multires else 0) | PRECISIONS[precision]
         flags |= _kernel_flag(kernel)
         if quad_fft64:
             flags |= S2LET_QUAD_FFT64
         if tc_split3:
             flags |= S2LET_TC_SPLIT3
+        if quad_dense:
+            flags |= S2LET_QUAD_DENSE
         self.L, self.B, self.J_min, self.batch = L, B, J_min, batch
         self.real, self.multires, self.precision, self.kernel = real, multires, precision, kernel
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)

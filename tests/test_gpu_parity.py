@@ -229,7 +229,7 @@ def test_mixed_radix_wavelets(prec):
     synthesis of the oracle's maps, and the adjoint."""
     L, B, J0 = 158, 2, 1
     seeds = [81, 82]
-    f = _maps(L, seeds, True, "cl")
+    f = _maps(L, seeds, True)
     plan = Plan(L, B, J0, batch=len(seeds), real=True, multires=True, precision=prec)
     fw_d, fs_d = plan.analysis(to_dev_map(f, plan.dtype, True))
     ref = [wavelet.analysis(x, L, B, J0, True, True) for x in f]
@@ -248,4 +248,21 @@ def test_mixed_radix_wavelets(prec):
     got = from_dev_map(plan.adjoint(gw, to_dev_map(np.stack(gss), plan.dtype, True)), True)
     want = np.stack([wavelet.analysis_adjoint(gws[b], gss[b], L, B, J0, True, True) for b in range(2)])
     assert rel_err(got, want) < TOL[prec]
+    assert plan.status() == 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_fft_quadrature_complex_maps(prec):
+    """Complex maps at L = 158: the FFT-form quadrature takes the orders
+    |m| > 32 on both sides of the order-major rows, the dense product the
+    middle ones (ring DFTs by Bluestein)."""
+    L = 158
+    flm = np.stack([inputs.random_flm(L, s, False) for s in (91, 92)])
+    f_ref = np.stack([sht.inverse(x, L) for x in flm])
+    plan = Plan(L, 2, 1, batch=2, real=False, multires=True, precision=prec)
+    g = flm_from_dev(plan.sht_forward(to_dev_map(f_ref, plan.dtype, False)))
+    assert rel_err(g, flm) < TOL[prec]
+    x = np.stack([inputs.random_map((L, 2 * L - 1), 95 + s, False) for s in range(2)])
+    g = flm_from_dev(plan.sht_forward(to_dev_map(x, plan.dtype, False)))
+    assert rel_err(g, np.stack([sht.forward(v, L) for v in x])) < TOL[prec]
     assert plan.status() == 0
