@@ -1337,7 +1337,10 @@ int s2let_plan_tuning(const s2let_plan *p, int N, int *tc_quad, int *tc_anal, in
     auto it = p->bands.find(N);
     if (it == p->bands.end()) return S2LET_ERR_ARG;
     const BandDev &bd = it->second;
-    if (tc_quad) *tc_quad = (!p->fp64 && p->quad_gemm && bd.has_mr && bd.mr_quad) ? 2 : (p->tc && bd.tc_quad);
+    if (tc_quad)
+        *tc_quad = (!p->fp64 && p->quad_gemm && bd.has_mr && bd.mr_quad && bd.N - 1 > MR_QUAD_DENSE_M)
+                       ? 2
+                       : (p->tc && bd.tc_quad);
     if (tc_anal) *tc_anal = p->tc && bd.tc_anal;
     if (tc_synth) *tc_synth = p->tc && bd.tc_synth;
     if (fft_threads_out) *fft_threads_out = bd.fft_th ? bd.fft_th : fft_threads(bd.M);
