@@ -37,6 +37,14 @@ __host__ __device__ constexpr MrFactors mr_factors(int P)
             P /= cand[i];
         }
     if (P != 1) f.n = -1;
+    // the largest radix second to last: with the lane order of mr_pass this keeps the
+    // passes' shared-memory accesses nearly free of bank conflicts (P = 4095:
+    // 9, 7, 13, 5 take 1.12 times the ideal wavefronts, 13, 9, 7, 5 took 1.36)
+    if (f.n >= 3) {
+        const int r0 = f.r[0];
+        for (int i = 0; i < f.n - 2; ++i) f.r[i] = f.r[i + 1];
+        f.r[f.n - 2] = r0;
+    }
     return f;
 }
 // length of the sub-transforms entering pass i (P for pass 0)
@@ -181,14 +189,20 @@ template <int R, bool INV> __device__ __forceinline__ void mr_dft(float2 (&x)[R]
 // (transposed algorithm), else after it.  Element pos of transform f is read
 // with ld(f, pos) and written with st(f, pos, v): shared memory for inner
 // passes, global memory or a product with a table for the first and last.
+// Lanes take consecutive butterflies j of a sub-transform (contiguous addresses)
+// where there are at least 16 of them; in the late passes, where there are
+// fewer, consecutive sub-transforms blk (addresses an odd stride S apart, which
+// fall in distinct banks) and share their twiddles.
 template <int P, int R, int S, int TWO, bool DIT, bool INV, int NF, class LD, class ST>
 __device__ __forceinline__ void mr_pass(const float2 *__restrict__ twp, LD ld, ST st)
 {
-    constexpr int M = S / R, NB = P / R;
+    constexpr int M = S / R, NB = P / R, NBLK = P / S;
+    constexpr bool BLK_FAST = M < 16;
     const float2 *tw = twp + TWO;
     for (int i = threadIdx.x; i < NF * NB; i += blockDim.x) {
         const int f = i / NB, r = i - f * NB;
-        const int blk = r / M, j = r - blk * M;
+        const int blk = BLK_FAST ? r % NBLK : r / M;
+        const int j = BLK_FAST ? r / NBLK : r - blk * M;
         const int base = blk * S + j;
         float2 x[R];
 #pragma unroll
