@@ -193,31 +193,40 @@ template <int R, bool INV> __device__ __forceinline__ void mr_dft(float2 (&x)[R]
 // where there are at least 16 of them; in the late passes, where there are
 // fewer, consecutive sub-transforms blk (addresses an odd stride S apart, which
 // fall in distinct banks) and share their twiddles.
+// A thread runs the same butterfly of every transform of the block, so its
+// twiddles are loaded once for NF butterflies.
 template <int P, int R, int S, int TWO, bool DIT, bool INV, int NF, class LD, class ST>
 __device__ __forceinline__ void mr_pass(const float2 *__restrict__ twp, LD ld, ST st)
 {
     constexpr int M = S / R, NB = P / R, NBLK = P / S;
     constexpr bool BLK_FAST = M < 16;
     const float2 *tw = twp + TWO;
-    for (int i = threadIdx.x; i < NF * NB; i += blockDim.x) {
-        const int f = i / NB, r = i - f * NB;
+    for (int r = threadIdx.x; r < NB; r += blockDim.x) {
         const int blk = BLK_FAST ? r % NBLK : r / M;
         const int j = BLK_FAST ? r / NBLK : r - blk * M;
         const int base = blk * S + j;
-        float2 x[R];
+        float2 w[R > 1 ? R - 1 : 1];
+        if (M > 1 && j > 0) {
 #pragma unroll
-        for (int q = 0; q < R; ++q) x[q] = ld(f, base + q * M);
-        if (DIT && M > 1 && j > 0) {
-#pragma unroll
-            for (int s = 1; s < R; ++s) x[s] = mr_twiddle<INV>(x[s], __ldg(tw + (s - 1) * M + j));
+            for (int s = 1; s < R; ++s) w[s - 1] = __ldg(tw + (s - 1) * M + j);
         }
-        mr_dft<R, INV>(x);
-        if (!DIT && M > 1 && j > 0) {
+#pragma unroll 1
+        for (int f = 0; f < NF; ++f) {
+            float2 x[R];
 #pragma unroll
-            for (int s = 1; s < R; ++s) x[s] = mr_twiddle<INV>(x[s], __ldg(tw + (s - 1) * M + j));
+            for (int q = 0; q < R; ++q) x[q] = ld(f, base + q * M);
+            if (DIT && M > 1 && j > 0) {
+#pragma unroll
+                for (int s = 1; s < R; ++s) x[s] = mr_twiddle<INV>(x[s], w[s - 1]);
+            }
+            mr_dft<R, INV>(x);
+            if (!DIT && M > 1 && j > 0) {
+#pragma unroll
+                for (int s = 1; s < R; ++s) x[s] = mr_twiddle<INV>(x[s], w[s - 1]);
+            }
+#pragma unroll
+            for (int q = 0; q < R; ++q) st(f, base + q * M, x[q]);
         }
-#pragma unroll
-        for (int q = 0; q < R; ++q) st(f, base + q * M, x[q]);
     }
     __syncthreads();
 }
