@@ -45,10 +45,17 @@ WORK = {
     "leg_synth": "flops: 4 per (l, m, ring, map) product of the contraction",
     "pack": "bytes: none counted (layout conversion of f_lm)",
 }
-# DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) per step of a
-# stage, for the kernels as they are now; a stage missing here has no capture
-# of its current kernels, and its traffic is reported as null
-TRAFFIC = {}
+# DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
+# stage's kernel at band-limit N with `batch` maps, from one capture of the kernel
+# as it is now, scaled by N^2 x maps (the stage's data grow so); a stage missing
+# here has no capture of its current kernels, and its traffic is reported as null
+TRAFFIC = {
+    # k_leg_anal_tc, full-band-limit launch at L = 1024, 64 maps: 772.0 + 255.5 MB
+    # (G and the recurrence tables read, f_lm written), profiles/quad_anal_tc_L1024_b64_tf32x3.md
+    "leg_anal": {"bytes_at": (1024, 64, 1027.5e6),
+                 "source": "ncu dram read+write of k_leg_anal_tc at L=1024 x 64 maps (1027.5 MB per launch), "
+                           "scaled by N^2 x maps to every launch of the step"},
+}
 
 # noise level of the --denoise steps: white noise of this harmonic standard
 # deviation would be thresholded at 3 sigma^j; against the C_l = 1/(l(l+1)) maps
@@ -300,10 +307,17 @@ def rooflines(stats, a, peaks, batch, bandlimits):
     dom = max(recs, key=lambda k: recs[k]["ms_per_step"])
     roof = dict(recs[dom])
     roof["kernel"] = dom
-    tr = TRAFFIC.get(dom)
-    roof["traffic"] = tr["bytes_per_step"] if tr else None
+    tr = TRAFFIC.get(dom) if a.precision == "tf32x3" else None
     if tr:
+        n0, b0, by = tr["bytes_at"]
+        # one launch of the stage per transform direction and band-limit of the round trip
+        roof["traffic"] = sum(by * (n / n0) ** 2 * batch / b0 for n in bandlimits)
         roof["traffic_note"] = tr["source"]
+        roof["traffic_vs_algorithmic_note"] = ("the Legendre stages have no algorithmic bytes of their own "
+                                               "(contraction flops are their work); traffic is the G and table "
+                                               "reads and f_lm writes")
+    else:
+        roof["traffic"] = None
     roof["note"] = "achieved and traffic are per step of the stage (all its launches)"
     # the dense theta-quadrature products of FP32 / TF32X3 plans, as a labelled extra
     if "theta_quad" in recs and a.precision != "fp64":

@@ -70,7 +70,9 @@ def test_stage_rooflines_follow_the_work_of_each_stage():
     assert roof["achieved"] == pytest.approx(1e13 / 0.050 / 1e12)
     assert roof["peak"] == pytest.approx(tf32) and roof["frac"] == pytest.approx(200.0 / tf32)
     assert roof["executed_mma_frac"] == pytest.approx(3 * 200.0 / tf32)
-    assert "of measured" in roof["peak_source"] and roof["traffic"] is None
+    assert "of measured" in roof["peak_source"]
+    # measured DRAM bytes of the analysis kernel scaled to the step's launches (N^2 x maps)
+    assert roof["traffic"] == pytest.approx(1027.5e6 * ((2048 / 1024) ** 2 + (8 / 1024) ** 2 + (4 / 1024) ** 2))
     assert set(leg) == {"leg_anal", "leg_synth"}
     assert leg["leg_synth"]["frac"] == pytest.approx(250.0 / tf32)
     assert leg["leg_anal"]["recurrence_tflops"] == pytest.approx(1e13 / 64 / 0.050 / 1e12)
@@ -89,5 +91,5 @@ def test_stage_rooflines_follow_the_work_of_each_stage():
     # a byte-bound stage that dominates is reported against HBM
     stats2 = dict(stats, ring_fwd=dict(launches=4, timed=4, ms=90.0, flops=0.0, bytes=60e9))
     roof2, _, _ = bench.rooflines(stats2, a, peaks, 64, [2048])
-    assert roof2["kernel"] == "ring_fwd" and roof2["bound"] == "hbm"
+    assert roof2["kernel"] == "ring_fwd" and roof2["bound"] == "hbm" and roof2["traffic"] is None
     assert roof2["frac"] == pytest.approx(60e9 / 0.090 / 1e9 / 6000.0)
