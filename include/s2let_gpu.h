@@ -95,7 +95,11 @@ int s2let_jmax(int L, int B);
  * lambda, an integer >= 2 here) and lowest wavelet scale J_min, 0 <= J_min < J
  * (Sect. 2.2).  Builds the kernel tables Phi_l0, Psi^j_l0 (Sect. 2.2), the
  * Legendre seeds and the FFT tables on the current device and allocates the
- * workspace.  Limits: 3 <= L <= 2048, 1 <= batch.  On error *plan is NULL. */
+ * workspace.  Limits: 3 <= L <= 4096, 1 <= batch (else S2LET_ERR_ARG); FP64
+ * plans and S2LET_QUAD_FFT64 only up to L = 2048 (their shared-memory FFTs of
+ * length M >= 4L - 3 would exceed the SM's shared memory; S2LET_ERR_UNSUPPORTED).
+ * The MW sampling theorem is stable to such band-limits (Sect. 2.1).  On error
+ * *plan is NULL. */
 int s2let_plan_create(s2let_plan **plan, int L, int B, int J_min, int flags, int batch);
 
 /* Free a plan and everything it owns (NULL is accepted). */

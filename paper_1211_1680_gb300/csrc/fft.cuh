@@ -574,13 +574,17 @@ __global__ void __launch_bounds__(FFT_MAX_THREADS, sizeof(R) == 4 ? 2 : 1) k_rin
 // The linear map x -> G is real and symmetric, so the same kernel also applies
 // its transpose.  Q is the compute type (FP64 by default), R the storage type.
 // parity < 0: sigma from m = mi - m_offset; parity 0 / 1: sigma = +1 / -1 for every row.
+// gbuf: the block's transform buffer in global memory (padded_len(M) values per
+// block) instead of shared memory, for lengths whose buffer exceeds it (the
+// plan-time FP64 quadrature matrices at N > 2048); VPT >= M / blockDim.x.
 template <typename Q, typename R, int VPT>
 __global__ void k_theta_quad(const cplx_t<R> *__restrict__ Fin, cplx_t<R> *__restrict__ Gout,
-                             int nmi, int m_offset, Q qscale, FftTab<cplx_t<Q>> T, int parity)
+                             int nmi, int m_offset, Q qscale, FftTab<cplx_t<Q>> T, int parity,
+                             cplx_t<Q> *gbuf = nullptr)
 {
     using C = cplx_t<Q>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *buf = reinterpret_cast<C *>(smem_raw);
+    C *buf = gbuf ? gbuf + (size_t)blockIdx.x * padded_len(T.M) : reinterpret_cast<C *>(smem_raw);
     const int N = T.N, P = T.P, M = T.M;
     const int mi = blockIdx.x, b = blockIdx.y;
     const int m = mi - m_offset;

@@ -340,24 +340,31 @@ struct LaSync {
 constexpr int LA_SYNC_BYTES = 256;
 static_assert(sizeof(LaSync) <= LA_SYNC_BYTES, "sync block");
 static_assert(LA_NR % LA_NA == 0 && LA_NR % LA_NB == 0 && LA_NR % LA_NACC == 0, "barrier ring");
+// The recurrence states of all rings stay in shared memory up to this
+// band-limit (226 KB in all at 2048); above it they live in a global buffer of
+// N float4 per block (st_g), read and written at each degree tile like the
+// shared copy.
+constexpr int LA_ST_SMEM_MAX = 2048;
 __host__ __device__ constexpr size_t la_anal_smem(int N)
 {
-    return (size_t)LA_SYNC_OFF + LA_SYNC_BYTES + (size_t)N * sizeof(float4) + (size_t)((N + 31) / 32) * sizeof(int) +
-           1024;
+    return (size_t)LA_SYNC_OFF + LA_SYNC_BYTES + (size_t)(N <= LA_ST_SMEM_MAX ? N : 0) * sizeof(float4) +
+           (size_t)((N + 31) / 32) * sizeof(int) + 1024;
 }
 
 template <bool CPLX>
 static __global__ void __launch_bounds__(LT_ANAL_THREADS, 1)
     k_leg_anal_tc(const float2 *__restrict__ Gin, int N, const float *__restrict__ kfac, float scale, int accumulate,
-                  float2 *__restrict__ dst, int Ldst, int B, LegTab<float> tab, int *err)
+                  float2 *__restrict__ dst, int Ldst, int B, LegTab<float> tab, int *err, float4 *st_g)
 {
     using Cols = LegCols<CPLX>;
     constexpr int BT = Cols::BT;
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
     unsigned char *smem = lt_align(smem_dyn);
     LaSync &sy = *reinterpret_cast<LaSync *>(smem + LA_SYNC_OFF);
-    float4 *st = reinterpret_cast<float4 *>(smem + LA_SYNC_OFF + LA_SYNC_BYTES);
-    int *gmin = reinterpret_cast<int *>(st + N);
+    float4 *sts = reinterpret_cast<float4 *>(smem + LA_SYNC_OFF + LA_SYNC_BYTES);
+    const bool st_shared = N <= LA_ST_SMEM_MAX;
+    float4 *st = st_shared ? sts : st_g + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * N;
+    int *gmin = reinterpret_cast<int *>(st_shared ? sts + N : sts);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m = blockIdx.x, b0 = blockIdx.y * BT;
     const bool two = CPLX && m > 0;

@@ -36,8 +36,9 @@ using namespace s2g;
 
 namespace {
 
-constexpr int kMaxL = 2048;
-constexpr int kMaxM = 8192;   // FFT length for kMaxL (next power of two >= 4 kMaxL - 3)
+constexpr int kMaxL = 4096;
+constexpr int kMaxM = 16384;  // FFT length for kMaxL (next power of two >= 4 kMaxL - 3)
+constexpr int kMaxL64 = 2048; // FP64 plans: their shared-memory FFTs of length M hold 16 M bytes
 
 int fft_threads(int M) { return std::max(32, std::min(FFT_MAX_THREADS, M / 16)); }
 
@@ -138,6 +139,7 @@ struct s2let_plan {
     int nsm = 0;                            // SMs of the plan's device
     void *F = nullptr, *flm = nullptr, *G = nullptr;   // workspace
     void *Ft = nullptr;                                // ring-major spectra of the ring DFTs
+    float4 *anal_st = nullptr;                         // TF32X3, L > 2048: recurrence states of k_leg_anal_tc
     bool quad_gemm = false;                 // FP32 plans: theta quadrature as a dense FP32 product
     bool tc = false;                        // TF32X3 plans: dense products on the tensor cores
     int tc_split = 2;                       // TF32 parts per operand in the tensor-core products
@@ -552,11 +554,11 @@ int run_anal(const s2let_plan *p, const BandDev &bd, const void *G, const void *
         if (p->tc && bd.tc_anal && p->cplx)
             k_leg_anal_tc<true><<<grid, LT_ANAL_THREADS, la_anal_smem(bd.N), st>>>(
                 (const float2 *)G, bd.N, (const float *)kfac, (float)scale, acc, (float2 *)dst, p->L, p->batch, tab,
-                p->d_err);
+                p->d_err, p->anal_st);
         else if (p->tc && bd.tc_anal)
             k_leg_anal_tc<false><<<grid, LT_ANAL_THREADS, la_anal_smem(bd.N), st>>>(
                 (const float2 *)G, bd.N, (const float *)kfac, (float)scale, acc, (float2 *)dst, p->L, p->batch, tab,
-                p->d_err);
+                p->d_err, p->anal_st);
         else if (p->cplx)
             k_leg_anal_gemm<true><<<grid, 256, sm, st>>>((const float2 *)G, bd.N, (const float *)kfac, (float)scale,
                                                          acc, (float2 *)dst, p->L, p->batch, tab);
@@ -732,9 +734,12 @@ template <typename K> void allow_smem(K kernel, size_t bytes)
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// FP32 kernels up to kMaxM, FP64 kernels (and the plan-time FP64 quadrature in
+// shared memory) up to the FFT length of kMaxL64
 void set_smem_limits(int Mmax)
 {
-    const size_t d = (size_t)padded_len(Mmax) * sizeof(double2), f = (size_t)padded_len(Mmax) * sizeof(float2);
+    const size_t d = (size_t)padded_len(std::min(Mmax, kMaxM / 2)) * sizeof(double2),
+                 f = (size_t)padded_len(Mmax) * sizeof(float2);
     allow_smem(k_ring_fwd_real<double>, d);
     allow_smem(k_ring_fwd_cplx<double>, d);
     allow_smem(k_ring_inv_real<double>, d);
@@ -748,8 +753,8 @@ void set_smem_limits(int Mmax)
     allow_smem(k_quad_tc<3, 2>, TqShape<3, 2>::SMEM);
     allow_smem(k_leg_synth_tc<false>, ls_synth_smem());
     allow_smem(k_leg_synth_tc<true>, ls_synth_smem());
-    allow_smem(k_leg_anal_tc<false>, la_anal_smem(kMaxL));
-    allow_smem(k_leg_anal_tc<true>, la_anal_smem(kMaxL));
+    allow_smem(k_leg_anal_tc<false>, la_anal_smem(LA_ST_SMEM_MAX));
+    allow_smem(k_leg_anal_tc<true>, la_anal_smem(LA_ST_SMEM_MAX));
     allow_smem(k_leg_anal_gemm<false>, anal_gemm_smem(kMaxL));
     allow_smem(k_leg_anal_gemm<true>, anal_gemm_smem(kMaxL));
     allow_smem(k_theta_quad<double, double, 16>, d);
@@ -794,8 +799,26 @@ int build_quad_matrices(s2let_plan *p, BandDev &bd)
         p->owned.push_back(Q);
         (par ? bd.Qo : bd.Qe) = Q;
         k_unit_rows<<<(unsigned)((nn + 255) / 256), 256>>>(X, N);
-        k_theta_quad<double, double, 16><<<dim3(N, 1), fft_threads(bd.M), padded_len(bd.M) * sizeof(double2)>>>(
-            X, X, N, 0, 1.0, bd.fd, par);
+        if (bd.M <= kMaxM / 2) {
+            k_theta_quad<double, double, 16><<<dim3(N, 1), fft_threads(bd.M), padded_len(bd.M) * sizeof(double2)>>>(
+                X, X, N, 0, 1.0, bd.fd, par);
+        } else {
+            // the FP64 transform buffer exceeds shared memory: global scratch for
+            // QB columns at a time (fft_threads(M) = 512 threads, M / 512 <= 32 values each)
+            constexpr int QB = 512;
+            double2 *scratch = nullptr;
+            if (dm_alloc(p->mem, &scratch, (size_t)QB * padded_len(bd.M) * sizeof(double2)) != cudaSuccess) {
+                err = S2LET_ERR_ALLOC;
+                break;
+            }
+            for (int c0 = 0; c0 < N; c0 += QB) {
+                const int nb = std::min(QB, N - c0);
+                k_theta_quad<double, double, 32><<<dim3(nb, 1), fft_threads(bd.M), 0>>>(
+                    X + (size_t)c0 * N, X + (size_t)c0 * N, nb, 0, 1.0, bd.fd, par, scratch);
+            }
+            cudaDeviceSynchronize();
+            dm_free(p->mem, scratch);
+        }
         k_real_to_float<<<(unsigned)((nn + 255) / 256), 256>>>(X, Q, nn);
         if (p->tc && p->tc_split == 3) {
             float *Q3 = nullptr;
@@ -934,6 +957,7 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
         return S2LET_ERR_ARG;
     if ((flags & S2LET_TC_SPLIT3) && prec != S2LET_PREC_TF32X3) return S2LET_ERR_ARG;
     if ((flags & S2LET_QUAD_FFT64) && prec == S2LET_PREC_FP64) return S2LET_ERR_ARG;
+    if (L > kMaxL64 && (prec == S2LET_PREC_FP64 || (flags & S2LET_QUAD_FFT64))) return S2LET_ERR_UNSUPPORTED;
     if ((flags & S2LET_QUAD_DENSE) && (prec == S2LET_PREC_FP64 || (flags & S2LET_QUAD_FFT64))) return S2LET_ERR_ARG;
 
     std::unique_ptr<s2let_plan> p(new (std::nothrow) s2let_plan());
@@ -1034,6 +1058,13 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
     if (p->quad_gemm) {
         if (dm_alloc(p->mem, &p->G, ws) != cudaSuccess) return S2LET_ERR_ALLOC;
         p->owned.push_back(p->G);
+    }
+    if (p->tc && L > LA_ST_SMEM_MAX) {
+        // one block per (order, batch tile) of the analysis at band-limit L, N float4 each
+        const int bt = p->cplx ? LegCols<true>::BT : LegCols<false>::BT;
+        const size_t nst = (size_t)L * ((batch + bt - 1) / bt) * L;
+        if (dm_alloc(p->mem, &p->anal_st, nst * sizeof(float4)) != cudaSuccess) return S2LET_ERR_ALLOC;
+        p->owned.push_back(p->anal_st);
     }
     if (cudaGetLastError() != cudaSuccess) return S2LET_ERR_CUDA;
     *out = p.release();

@@ -49,7 +49,11 @@ def test_plan_argument_errors_need_no_gpu():
     assert L.s2let_plan_create(ctypes.byref(h), 2, 2, 0, 0, 1) == _lib.S2LET_ERR_ARG
     assert L.s2let_plan_create(ctypes.byref(h), 32, 1, 0, 0, 1) == _lib.S2LET_ERR_ARG
     assert L.s2let_plan_create(ctypes.byref(h), 32, 2, 0, 0x1000, 1) == _lib.S2LET_ERR_ARG
-    assert L.s2let_plan_create(ctypes.byref(h), 4096, 2, 0, 0, 1) == _lib.S2LET_ERR_ARG
+    assert L.s2let_plan_create(ctypes.byref(h), 4097, 2, 0, _lib.S2LET_PREC_TF32X3, 1) == _lib.S2LET_ERR_ARG
+    # FP64 plans stop at L = 2048 (their shared-memory FFTs), FP32 / TF32X3 plans at 4096
+    assert L.s2let_plan_create(ctypes.byref(h), 4096, 2, 0, 0, 1) == _lib.S2LET_ERR_UNSUPPORTED
+    assert L.s2let_plan_create(ctypes.byref(h), 2049, 2, 0, _lib.S2LET_PREC_FP32 | _lib.S2LET_QUAD_FFT64,
+                               1) == _lib.S2LET_ERR_UNSUPPORTED
     assert L.s2let_plan_create(ctypes.byref(h), 32, 2, 0, 0, 0) == _lib.S2LET_ERR_ARG
     assert not h.value
 
