@@ -787,8 +787,9 @@ int build_quad_matrices(s2let_plan *p, BandDev &bd)
     const size_t nn = (size_t)N * N;
     double2 *X = nullptr;
     if (dm_alloc(p->mem, &X, nn * sizeof(double2)) != cudaSuccess) return S2LET_ERR_ALLOC;
-    cudaFuncSetAttribute(k_theta_quad<double, double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(padded_len(bd.M) * sizeof(double2)));
+    if (bd.M <= kMaxM / 2)   // above, the transform buffer is in global memory (no shared-memory attribute)
+        cudaFuncSetAttribute(k_theta_quad<double, double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(padded_len(bd.M) * sizeof(double2)));
     int err = S2LET_OK;
     for (int par = 0; par < 2 && !err; ++par) {
         float *Q = nullptr;
