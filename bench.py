@@ -94,9 +94,11 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-check", action="store_true")
-    ap.add_argument("--workload", choices=["l2048x64", "batch256"], default="l2048x64",
+    ap.add_argument("--workload", choices=["l2048x64", "batch256", "grad"], default="l2048x64",
                     help="batch256: 256 complex maps of uneven L in {128..2048} and B in {2, 3}, J_min=1, "
-                         "one graph launch per round trip")
+                         "one graph launch per round trip; grad: the loss sum_j 2^-j ||W^j||^2 and its "
+                         "gradient (adjoint kernel) at L=1024 x 16 real maps, and with per-scale "
+                         "recomputation for one map at L=4096")
     return ap.parse_args()
 
 
@@ -578,6 +580,74 @@ def run_batch256(a, rank, world, local_rank):
     return 0
 
 
+def run_grad(a, rank, world, local_rank):
+    """Differentiation workload: loss = sum_j 2^-j ||W^j||^2 (wavelet scales) of real
+    maps and its gradient with respect to the maps.  (1) 16 maps at L = 1024, B = 2,
+    J_min = 2: backward through the adjoint kernel (s2let_adjoint), and with per-scale
+    recomputation; (2) one map at L = 4096 with per-scale recomputation.  A step is
+    one forward + backward; the value is maps per second of the first case."""
+    import torch
+    from paper_1211_1680_gb300 import inputs
+    from paper_1211_1680_gb300.autograd import scale_energy_loss, scale_energy_loss_recompute
+    from paper_1211_1680_gb300.s2let import Plan
+
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    out = {}
+    for (L, nb, label) in ((1024, 16, "L1024x16"), (4096, 1, "L4096x1")):
+        plan = Plan(L, 2, 2, batch=nb, real=True, multires=True, precision=a.precision)
+        flm = inputs.random_flm_batch(L, [5000 + rank * nb + i for i in range(nb)], real=True, kind="cl")
+        x = plan.sht_inverse(torch.from_numpy(np.stack([flm.real, flm.imag], -1)).to("cuda", plan.dtype)
+                             .contiguous())
+        f = x.clone().requires_grad_(True)
+        rec = {}
+        variants = [("recompute", scale_energy_loss_recompute)]
+        if L <= 2048:
+            variants.insert(0, ("adjoint", scale_energy_loss))
+        for name, loss_fn in variants:
+            def step():
+                loss = loss_fn(f, plan)
+                (g,) = torch.autograd.grad(loss, f)
+                return g
+            torch.cuda.reset_peak_memory_stats()
+            ms = timed(step, a.steps, a.warmup)
+            rec[name] = {"ms_per_step": ms, "maps_per_s": nb / (ms / 1000.0),
+                         "peak_torch_bytes": torch.cuda.max_memory_allocated()}
+        if "adjoint" in rec:
+            g1 = torch.autograd.grad(scale_energy_loss(f, plan), f)[0]
+            g2 = torch.autograd.grad(scale_energy_loss_recompute(f, plan), f)[0]
+            rec["recompute_vs_adjoint_rel_diff"] = float(((g2 - g1).abs().max() / g1.abs().max()).item())
+        out[label] = rec
+        del plan, x, f
+        torch.cuda.empty_cache()
+    first = out["L1024x16"]["adjoint"]
+    res = {"metric": "loss + gradient evaluations of sum_j 2^-j ||W^j||^2 (maps/s), L=1024 x 16 real maps",
+           "value": world * first["maps_per_s"], "unit": "maps/s", "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": first["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": {"fp32": "f32", "tf32x3": "tf32x3+f32", "fp64": "f64"}[a.precision],
+           "data": "synthetic",
+           "config": {"workload": "loss + gradient: L=1024 x 16 real maps (adjoint kernel and per-scale "
+                                  "recomputation), L=4096 x 1 map (per-scale recomputation); B=2, J_min=2, "
+                                  "f_lm ~ C_l=1/(l(l+1))"},
+           "cases": out}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     a = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -591,6 +661,8 @@ def main():
     try:
         if a.workload == "batch256":
             return run_batch256(a, rank, world, local_rank)
+        if a.workload == "grad":
+            return run_grad(a, rank, world, local_rank)
         return run_gpu(a, rank, world, local_rank)
     finally:
         if world > 1:

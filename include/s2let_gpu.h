@@ -212,6 +212,27 @@ int s2let_plan_profile(s2let_plan *plan, int enable);
 int s2let_plan_stage_stats(s2let_plan *plan, int stage, int64_t *launches, int64_t *timed, double *ms,
                            double *flops, double *bytes);
 
+/* Pieces of the analysis for gradients that recompute one scale at a time
+ * (the analysis is W^j = Inv_{N_j}(sqrt(4 pi/(2l+1)) Psi^j*_l0 f_lm), f_lm =
+ * Fwd_L(f), Eqs. wav2 and wav4; the transposes are under the Euclidean inner
+ * product of the stored arrays, as for s2let_adjoint):
+ * s2let_wav_scale: the maps w of scale j (j = -1: the scaling maps) of the
+ *   plan's batch from harmonic coefficients flm (device, batch x L*L complex,
+ *   index l*l + l + m; real maps: the coefficients of a real map).  w is
+ *   batch maps at that scale's band-limit (the layout of one block of f_wav).
+ * s2let_wav_scale_adjoint: glm += the transpose of s2let_wav_scale applied to
+ *   the maps g (same layouts; glm accumulates, so the caller zeroes it first).
+ * s2let_sht_forward_adjoint: gf = the transpose of s2let_sht_forward applied to
+ *   glm.  So the gradient of a loss of the wavelet maps is
+ *   s2let_sht_forward_adjoint(sum_j s2let_wav_scale_adjoint(dloss/dW^j)), with
+ *   each W^j recomputed from f_lm when it is needed.
+ * All use the plan's workspace (a call must not overlap another call of the same
+ * plan) and run asynchronously on `stream`; S2LET_ERR_ARG for a j outside
+ * {-1, J_min..J} or a NULL pointer. */
+int s2let_wav_scale(s2let_plan *plan, int j, const void *flm, void *w, void *stream);
+int s2let_wav_scale_adjoint(s2let_plan *plan, int j, const void *g, void *glm, void *stream);
+int s2let_sht_forward_adjoint(s2let_plan *plan, const void *glm, void *gf, void *stream);
+
 /* Autotuner.  For every band-limit of the plan, times the candidate kernels of
  * each stage on the plan's own workspace (contents ignored) with the plan's
  * batch, and keeps the fastest: the ring-DFT block size (M/8, M/16, M/32 or

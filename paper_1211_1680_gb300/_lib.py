@@ -45,6 +45,9 @@ SIGNATURES = {
     "s2let_adjoint": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "s2let_sht_forward": (_i, [_vp, _vp, _vp, _vp]),
     "s2let_sht_inverse": (_i, [_vp, _vp, _vp, _vp]),
+    "s2let_wav_scale": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "s2let_wav_scale_adjoint": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "s2let_sht_forward_adjoint": (_i, [_vp, _vp, _vp, _vp]),
     "s2let_plan_status": (_i, [_vp]),
     "s2let_plan_test_timeout": (_i, [_vp, _vp]),
     "s2let_set_allocator": (_i, [ALLOC_FN, FREE_FN, _vp]),

@@ -604,6 +604,35 @@ __global__ void k_pack(const cplx_t<R> *__restrict__ rect, cplx_t<R> *__restrict
     out[i] = v;
 }
 
+// out[i] += the packed value of k_pack (for gradients accumulated over scales)
+template <typename R>
+__global__ void k_pack_add(const cplx_t<R> *__restrict__ rect, cplx_t<R> *__restrict__ out, int L, int cplx, int B)
+{
+    const size_t n = (size_t)L * L;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * B) return;
+    const int b = (int)(i / n);
+    const int idx = (int)(i % n);
+    int ll = (int)sqrtf((float)idx);
+    while ((ll + 1) * (ll + 1) <= idx) ++ll;
+    while (ll * ll > idx) --ll;
+    const int m = idx - ll * ll - ll;
+    const int nm = cplx ? 2 * L - 1 : L;
+    cplx_t<R> v;
+    if (cplx) {
+        v = rect[((size_t)b * nm + (m + L - 1)) * L + ll];
+    } else if (m >= 0) {
+        v = rect[((size_t)b * nm + m) * L + ll];
+    } else {
+        v = cconj(rect[((size_t)b * nm + (-m)) * L + ll]);
+        if ((-m) & 1) {
+            v.x = -v.x;
+            v.y = -v.y;
+        }
+    }
+    out[i] = cadd(out[i], v);
+}
+
 template <typename R>
 __global__ void k_unpack(const cplx_t<R> *__restrict__ in, cplx_t<R> *__restrict__ rect, int L, int cplx, int B)
 {
@@ -676,6 +705,13 @@ std::vector<MapRef> map_order(const s2let_plan *p)
     return v;
 }
 
+// Scale k of the plan: 0 = scaling map, 1 + i = wavelet scale J0 + i.
+MapRef map_ref(const s2let_plan *p, int k)
+{
+    if (k == 0) return {0, p->n_scal, 0, true};
+    return {k, p->n_wav[k - 1], p->wav_off[k - 1], false};
+}
+
 template <typename R> int analysis_t(s2let_plan *p, const void *f, void *fw, void *fs, cudaStream_t st)
 {
     int e = sht_fwd_to_rect<R>(p, f, st);
@@ -722,6 +758,61 @@ template <typename R> int adjoint_t(s2let_plan *p, const void *gw, const void *g
     }
     // forward-transform adjoint: Legendre sum (2 pi / P), quadrature (symmetric), ring DFT (1/P)
     const BandDev &bl = p->bands.at(p->L);
+    if ((e = run_synth<R>(p, bl, p->flm, nullptr, 2.0 * M_PI / bl.P, p->F, st))) return e;
+    void *G = run_theta_quad<R>(p, bl, p->F, st, &e);
+    if (e) return e;
+    return run_ring_inv<R>(p, bl, G, gf, 1.0 / bl.P, st);
+}
+
+// Pieces of the analysis for gradients with per-scale recomputation.
+// The map of scale k (k = 0: scaling, k = 1 + j - J0: wavelet scale j) from
+// harmonic coefficients in the public layout: W = Inv_{N_k}(c_k f_lm).
+template <typename R> int wav_scale_t(s2let_plan *p, int k, const void *flm, void *w, cudaStream_t st)
+{
+    const MapRef mr = map_ref(p, k);
+    const size_t n = (size_t)p->batch * nmi(p, p->L) * p->L;
+    {
+        StageScope sc(p, S2LET_STAGE_PACK, st, 0.0, 0.0);
+        k_unpack<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const cplx_t<R> *)flm, (cplx_t<R> *)p->flm,
+                                                                 p->L, p->cplx, p->batch);
+    }
+    S2_LAUNCH_CHECK();
+    const BandDev &bd = p->bands.at(mr.N);
+    int e;
+    if ((e = run_synth<R>(p, bd, p->flm, p->kfac[mr.k], 1.0, p->F, st))) return e;
+    return run_ring_inv<R>(p, bd, p->F, w, 1.0, st);
+}
+
+// glm (public layout) += c_k Inv_{N_k}^T(g): the transpose of wav_scale_t.
+template <typename R> int wav_scale_adjoint_t(s2let_plan *p, int k, const void *g, void *glm, cudaStream_t st)
+{
+    const MapRef mr = map_ref(p, k);
+    const BandDev &bd = p->bands.at(mr.N);
+    const size_t rect = (size_t)p->batch * nmi(p, p->L) * p->L * 2 * elem_size(p);
+    if (cudaMemsetAsync(p->flm, 0, rect, st) != cudaSuccess) return S2LET_ERR_CUDA;   // degrees >= N_k
+    int e;
+    if ((e = run_ring_fwd<R>(p, bd, g, p->F, 1.0, st))) return e;
+    if ((e = run_anal<R>(p, bd, p->F, p->kfac[mr.k], 1.0, 0, p->flm, st))) return e;
+    const size_t n = (size_t)p->batch * p->L * p->L;
+    StageScope sc(p, S2LET_STAGE_PACK, st, 0.0, 0.0);
+    k_pack_add<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const cplx_t<R> *)p->flm, (cplx_t<R> *)glm, p->L,
+                                                               p->cplx, p->batch);
+    S2_LAUNCH_CHECK();
+    return S2LET_OK;
+}
+
+// gf = Fwd_L^T(glm): the transpose of the forward transform (the last part of adjoint_t).
+template <typename R> int sht_forward_adjoint_t(s2let_plan *p, const void *glm, void *gf, cudaStream_t st)
+{
+    const size_t n = (size_t)p->batch * nmi(p, p->L) * p->L;
+    {
+        StageScope sc(p, S2LET_STAGE_PACK, st, 0.0, 0.0);
+        k_unpack<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const cplx_t<R> *)glm, (cplx_t<R> *)p->flm,
+                                                                 p->L, p->cplx, p->batch);
+    }
+    S2_LAUNCH_CHECK();
+    const BandDev &bl = p->bands.at(p->L);
+    int e;
     if ((e = run_synth<R>(p, bl, p->flm, nullptr, 2.0 * M_PI / bl.P, p->F, st))) return e;
     void *G = run_theta_quad<R>(p, bl, p->F, st, &e);
     if (e) return e;
@@ -1342,6 +1433,35 @@ int s2let_adjoint(s2let_plan *p, const void *g_wav, const void *g_scal, void *g_
 {
     if (!p || !g_wav || !g_scal || !g_f) return S2LET_ERR_ARG;
     return S2_DISPATCH(adjoint_t, p, g_wav, g_scal, g_f, (cudaStream_t)stream);
+}
+
+static int scale_index(const s2let_plan *p, int j)
+{
+    if (j == -1) return 0;
+    if (j < p->J0 || j > p->J) return -1;
+    return 1 + j - p->J0;
+}
+
+int s2let_wav_scale(s2let_plan *p, int j, const void *flm, void *w, void *stream)
+{
+    if (!p || !flm || !w) return S2LET_ERR_ARG;
+    const int k = scale_index(p, j);
+    if (k < 0) return S2LET_ERR_ARG;
+    return S2_DISPATCH(wav_scale_t, p, k, flm, w, (cudaStream_t)stream);
+}
+
+int s2let_wav_scale_adjoint(s2let_plan *p, int j, const void *g, void *glm, void *stream)
+{
+    if (!p || !g || !glm) return S2LET_ERR_ARG;
+    const int k = scale_index(p, j);
+    if (k < 0) return S2LET_ERR_ARG;
+    return S2_DISPATCH(wav_scale_adjoint_t, p, k, g, glm, (cudaStream_t)stream);
+}
+
+int s2let_sht_forward_adjoint(s2let_plan *p, const void *glm, void *gf, void *stream)
+{
+    if (!p || !glm || !gf) return S2LET_ERR_ARG;
+    return S2_DISPATCH(sht_forward_adjoint_t, p, glm, gf, (cudaStream_t)stream);
 }
 
 int s2let_sht_forward(s2let_plan *p, const void *f, void *flm, void *stream)

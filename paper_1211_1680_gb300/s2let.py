@@ -237,6 +237,43 @@ class Plan:
         check("s2let_sht_inverse", _lib.lib().s2let_sht_inverse(self._h, a, o, _stream_handle(stream)))
         return f
 
+    # ---------------------------------------------------------------- per-scale pieces (gradients)
+    def scale_bandlimit(self, j):
+        """Band-limit of scale j's maps (j = -1: the scaling maps)."""
+        if j == -1:
+            return self.N_scal
+        for (jj, n, _, _) in self.scales:
+            if jj == j:
+                return n
+        raise ValueError("no scale %r" % (j,))
+
+    def wav_scale(self, j, flm, w=None, stream=None):
+        """The maps of scale j (j = -1: scaling) from harmonic coefficients flm."""
+        n = self.scale_bandlimit(j)
+        if w is None:
+            w = self.empty_map(n)
+        a = self._chk(flm, self.batch * self.L * self.L * 2, "flm")
+        o = self._chk(w, self._map_numel(n), "w")
+        check("s2let_wav_scale", _lib.lib().s2let_wav_scale(self._h, j, a, o, _stream_handle(stream)))
+        return w
+
+    def wav_scale_adjoint(self, j, g, glm, stream=None):
+        """glm += the transpose of wav_scale(j) applied to the maps g."""
+        n = self.scale_bandlimit(j)
+        a = self._chk(g, self._map_numel(n), "g")
+        o = self._chk(glm, self.batch * self.L * self.L * 2, "glm")
+        check("s2let_wav_scale_adjoint", _lib.lib().s2let_wav_scale_adjoint(self._h, j, a, o, _stream_handle(stream)))
+        return glm
+
+    def sht_forward_adjoint(self, glm, gf=None, stream=None):
+        """gf = the transpose of sht_forward applied to glm."""
+        if gf is None:
+            gf = self.empty_map()
+        a = self._chk(glm, self.batch * self.L * self.L * 2, "glm")
+        o = self._chk(gf, self._map_numel(self.L), "gf")
+        check("s2let_sht_forward_adjoint", _lib.lib().s2let_sht_forward_adjoint(self._h, a, o, _stream_handle(stream)))
+        return gf
+
     # ---------------------------------------------------------------- denoising (Sect. 4.3)
     def noise_std(self, j):
         """sigma^j / sigma for scale j (j = -1: the scaling function)."""
