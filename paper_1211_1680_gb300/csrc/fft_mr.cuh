@@ -238,22 +238,104 @@ template <int P> struct MrSmem {
     __device__ __forceinline__ void operator()(int f, int pos, float2 v) const { buf[f * P + pos] = v; }
 };
 
-// passes I, I+1, .. (DIF) or I, I-1, .. (DIT); the first pass executed loads
-// with ld, the last one stores with st, all others use shared memory
+// passes I, I+1, .., LAST (DIF) or I, I-1, .., LAST (DIT); the first pass executed
+// loads with ld, the last one stores with st, all others use shared memory
+template <int P, int I, int LAST, bool DIT, bool INV, int NF, class LD, class ST>
+__device__ __forceinline__ void mr_run_range(float2 *buf, const float2 *tw, LD ld, ST st, int first)
+{
+    constexpr MrFactors F = mr_factors(P);
+    if constexpr (I >= 0 && I < F.n && (DIT ? I >= LAST : I <= LAST)) {
+        constexpr int R = F.r[I], S = mr_sub(P, I), TWO = mr_tw_off(P, I);
+        const MrSmem<P> sm{buf};
+        const bool is_first = I == first;
+        if constexpr (I == LAST) {
+            if (is_first) mr_pass<P, R, S, TWO, DIT, INV, NF>(tw, ld, st);
+            else mr_pass<P, R, S, TWO, DIT, INV, NF>(tw, sm, st);
+        } else {
+            if (is_first) mr_pass<P, R, S, TWO, DIT, INV, NF>(tw, ld, sm);
+            else mr_pass<P, R, S, TWO, DIT, INV, NF>(tw, sm, sm);
+        }
+        mr_run_range<P, DIT ? I - 1 : I + 1, LAST, DIT, INV, NF>(buf, tw, ld, st, first);
+    }
+}
 template <int P, int I, bool DIT, bool INV, int NF, class LD, class ST>
 __device__ __forceinline__ void mr_run(float2 *buf, const float2 *tw, LD ld, ST st)
 {
     constexpr MrFactors F = mr_factors(P);
-    constexpr int first = DIT ? F.n - 1 : 0, last = DIT ? 0 : F.n - 1;
-    if constexpr (I >= 0 && I < F.n) {
-        constexpr int R = F.r[I], S = mr_sub(P, I), TWO = mr_tw_off(P, I);
-        const MrSmem<P> sm{buf};
-        if constexpr (I == first && I == last) mr_pass<P, R, S, TWO, DIT, INV, NF>(tw, ld, st);
-        else if constexpr (I == first) mr_pass<P, R, S, TWO, DIT, INV, NF>(tw, ld, sm);
-        else if constexpr (I == last) mr_pass<P, R, S, TWO, DIT, INV, NF>(tw, sm, st);
-        else mr_pass<P, R, S, TWO, DIT, INV, NF>(tw, sm, sm);
-        mr_run<P, DIT ? I - 1 : I + 1, DIT, INV, NF>(buf, tw, ld, st);
+    mr_run_range<P, I, DIT ? 0 : F.n - 1, DIT, INV, NF>(buf, tw, ld, st, I);
+}
+
+// Two passes fused on the same butterflies, with a product by a table between
+// them, where a transform's last pass and the next transform's first pass act
+// on the same groups of elements:
+//   mr_pass_dif_last_dit_first: the last forward (DIF) pass, tab1[pos], the first
+//     inverse (DIT) pass (M = 1, no twiddles); tab1 complex
+//   mr_pass_dit_last_dif_first: the last inverse (DIT) pass (pass 0), tab2[pos],
+//     the first forward (DIF) pass (pass 0), sharing the twiddles; tab2 real
+// Each saves one round trip of the transforms through shared memory.
+template <int P, int NF>
+__device__ __forceinline__ void mr_pass_dif_last_dit_first(float2 *buf, const float2 *__restrict__ tab1)
+{
+    constexpr MrFactors F = mr_factors(P);
+    constexpr int I = F.n - 1, R = F.r[I], S = mr_sub(P, I), NB = P / R;
+    static_assert(S == R, "last pass of length R");
+    for (int r = threadIdx.x; r < NB; r += blockDim.x) {
+        const int base = r * S;
+#pragma unroll 1
+        for (int f = 0; f < NF; ++f) {
+            float2 x[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) x[q] = buf[f * P + base + q];
+            mr_dft<R, false>(x);
+#pragma unroll
+            for (int q = 0; q < R; ++q) x[q] = mr_twiddle<false>(x[q], __ldg(tab1 + base + q));
+            mr_dft<R, true>(x);
+#pragma unroll
+            for (int q = 0; q < R; ++q) buf[f * P + base + q] = x[q];
+        }
     }
+    __syncthreads();
+}
+template <int P, int NF>
+__device__ __forceinline__ void mr_pass_dit_last_dif_first(float2 *buf, const float2 *__restrict__ twp,
+                                                           const float *__restrict__ tab2)
+{
+    constexpr MrFactors F = mr_factors(P);
+    constexpr int R = F.r[0], M = P / R, TWO = mr_tw_off(P, 0);
+    // pass 0 has one sub-transform (S = P): its lanes run over the butterflies j either way
+    const float2 *tw = twp + TWO;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        float2 w[R - 1];
+        if (j > 0) {
+#pragma unroll
+            for (int s = 1; s < R; ++s) w[s - 1] = __ldg(tw + (s - 1) * M + j);
+        }
+#pragma unroll 1
+        for (int f = 0; f < NF; ++f) {
+            float2 x[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) x[q] = buf[f * P + j + q * M];
+            if (j > 0) {
+#pragma unroll
+                for (int s = 1; s < R; ++s) x[s] = mr_twiddle<true>(x[s], w[s - 1]);
+            }
+            mr_dft<R, true>(x);
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const float v = __ldg(tab2 + j + q * M);
+                x[q].x *= v;
+                x[q].y *= v;
+            }
+            mr_dft<R, false>(x);
+            if (j > 0) {
+#pragma unroll
+                for (int s = 1; s < R; ++s) x[s] = mr_twiddle<false>(x[s], w[s - 1]);
+            }
+#pragma unroll
+            for (int q = 0; q < R; ++q) buf[f * P + j + q * M] = x[q];
+        }
+    }
+    __syncthreads();
 }
 
 // NF transforms X_k = sum_n x_n e^{-+2 pi i n k / P} (unnormalised): x_n = ld(f, n)
@@ -427,19 +509,32 @@ __global__ void __launch_bounds__(MR_THREADS, 3) k_quad_mr(const float2 *__restr
         const float2 v = x[P - 1 - t];
         return make_float2(sgn[q] * v.x, sgn[q] * v.y);
     };
-    mr_fft_dif<P, false, CPB>(mr_buf, T.tw, ext, [&](int q, int pos, float2 v) {
-        mr_buf[q * P + pos] = mr_twiddle<false>(v, __ldg(T.shm + pos));
-    });
-    // (its 1/P is in ve) times the weights of the shifted points
-    mr_fft_dit<P, true, CPB>(mr_buf, T.tw, sm, [&](int q, int t, float2 v) {
-        const float w = __ldg(T.ve + t);
-        mr_buf[q * P + t] = make_float2(v.x * w, v.y * w);
-    });
-    // K^T: DFT, conjugate phases (with 1/P), inverse DFT
-    mr_fft_dif<P, false, CPB>(mr_buf, T.tw, sm, [&](int q, int pos, float2 v) {
-        mr_buf[q * P + pos] = mr_twiddle<false>(v, __ldg(T.shp + pos));
-    });
-    mr_fft_dit<P, true, CPB>(mr_buf, T.tw, sm, sm);
+    constexpr int NP = mr_factors(P).n;
+    if constexpr (NP >= 2) {
+        // the junctions between the four transforms as fused passes (three fewer
+        // round trips through shared memory)
+        mr_run_range<P, 0, NP - 2, false, false, CPB>(mr_buf, T.tw, ext, sm, 0);
+        mr_pass_dif_last_dit_first<P, CPB>(mr_buf, T.shm);          // K: phases
+        mr_run_range<P, NP - 2, 1, true, true, CPB>(mr_buf, T.tw, sm, sm, NP - 2);
+        mr_pass_dit_last_dif_first<P, CPB>(mr_buf, T.tw, T.ve);     // (1/P in ve) weights
+        mr_run_range<P, 1, NP - 2, false, false, CPB>(mr_buf, T.tw, sm, sm, 1);
+        mr_pass_dif_last_dit_first<P, CPB>(mr_buf, T.shp);          // K^T: phases (with 1/P)
+        mr_run_range<P, NP - 2, 0, true, true, CPB>(mr_buf, T.tw, sm, sm, NP - 2);
+    } else {
+        mr_fft_dif<P, false, CPB>(mr_buf, T.tw, ext, [&](int q, int pos, float2 v) {
+            mr_buf[q * P + pos] = mr_twiddle<false>(v, __ldg(T.shm + pos));
+        });
+        // (its 1/P is in ve) times the weights of the shifted points
+        mr_fft_dit<P, true, CPB>(mr_buf, T.tw, sm, [&](int q, int t, float2 v) {
+            const float w = __ldg(T.ve + t);
+            mr_buf[q * P + t] = make_float2(v.x * w, v.y * w);
+        });
+        // K^T: DFT, conjugate phases (with 1/P), inverse DFT
+        mr_fft_dif<P, false, CPB>(mr_buf, T.tw, sm, [&](int q, int pos, float2 v) {
+            mr_buf[q * P + pos] = mr_twiddle<false>(v, __ldg(T.shp + pos));
+        });
+        mr_fft_dit<P, true, CPB>(mr_buf, T.tw, sm, sm);
+    }
     // fold, plus the odd-point term
     for (int i = threadIdx.x; i < CPB * N; i += blockDim.x) {
         const int q = i / N, t = i - q * N, row = rowof[q];
