@@ -538,10 +538,12 @@ def run_batch256(a, rank, world, local_rank):
     f, fw, fs, fo = bp.buffers()
     lib = _lib.lib()
     # inputs: per group, seeded complex Gaussian f_lm -> maps with the group plan's inverse transform
+    kept = {}                          # the first map of each group: its coefficients, for the oracle check
     for g, (ph, f_off, _, _) in enumerate(bp.groups):
         members = [i for i in range(256) if bp.layout[i][2] == g]
         L = Ls[members[0]]
         flm = np.stack([inputs.random_flm(L, 4000 + rank * 256 + i, real=False) for i in members])
+        kept[members[0]] = flm[0]
         fl = torch.from_numpy(np.stack([flm.real, flm.imag], -1)).to("cuda", bp.dtype).contiguous()
         n = len(members) * L * (2 * L - 1) * 2
         check = lib.s2let_sht_inverse(ctypes.c_void_p(ph), ctypes.c_void_p(fl.data_ptr()),
@@ -567,6 +569,31 @@ def run_batch256(a, rank, world, local_rank):
     err = max(float(((bp.map_view(fo, i) - bp.map_view(f, i)).abs().max() / bp.map_view(f, i).abs().max()).item())
               for i in range(256))
     hist = {int(L): Ls.count(L) for L in sorted(set(Ls))}
+    # the wavelet maps of the first map of every group against the oracle's direct sum
+    # of Eq. wav2 on sampled rings (every scale), as in the main workload's check
+    wav_err = 0.0
+    if rank == 0 and not a.skip_check:
+        import oracle.sht as osht
+        import oracle.wavelet as ow
+        for i, flm in kept.items():
+            L, B = Ls[i], Bs[i]
+            _, _, g, k = bp.layout[i]
+            ph, _, wav_off, _ = bp.groups[g]
+            _, psi = ow.tables(L, B, 1)
+            l_of = np.repeat(np.arange(L), 2 * np.arange(L) + 1)
+            norm = np.sqrt(4 * np.pi / (2 * l_of + 1))
+            for j, kern in zip(range(1, 1 + len(psi)), psi):
+                n_, off_, cnt_ = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+                assert lib.s2let_wav_layout(ctypes.c_void_p(ph), j, ctypes.byref(n_), ctypes.byref(off_),
+                                            ctypes.byref(cnt_)) == 0
+                n = n_.value
+                per = n * (2 * n - 1) * 2
+                start = wav_off + off_.value + k * per
+                v = fw[start:start + per].view(n, 2 * n - 1, 2).double().cpu().numpy()
+                v = v[..., 0] + 1j * v[..., 1]
+                rings = sorted({0, 1, n // 3, n // 2, n - 2, n - 1} & set(range(n)))
+                ref = osht.inverse_at((norm * flm * kern[l_of])[:n * n], n, rings, np.arange(2 * n - 1))
+                wav_err = max(wav_err, float(np.max(np.abs(v[rings] - ref)) / np.max(np.abs(v))))
     res = {"metric": "uneven-batch wavelet round-trips/s (256 complex maps, one graph launch per round trip)",
            "value": world * 256 * a.steps / (ms / 1000.0), "unit": UNIT, "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -574,7 +601,11 @@ def run_batch256(a, rank, world, local_rank):
            "data": "synthetic",
            "config": {"workload": "256 complex maps, L histogram %s, B in {2,3}, J_min=1, multiresolution" % hist,
                       "groups": bp.n_groups, "graph_launches_per_step": 1},
-           "round_trip_rel_err": err, "clocks": clk}
+           "round_trip_rel_err": err, "clocks": clk,
+           "max_rel_err": wav_err,
+           "check": "round trip of all 256 maps; wavelet maps (every scale, rings {0,1,N/3,N/2,N-2,N-1}) of "
+                    "the first map of each (L, B) group against the oracle's direct sum, normalised by the "
+                    "scale map's max"}
     if rank == 0:
         print(json.dumps(res), flush=True)
     return 0

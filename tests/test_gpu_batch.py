@@ -81,3 +81,53 @@ def test_autotuned_batch_round_trip():
             stream.synchronize()
             for i in range(len(Ls)):
                 assert rel_err(from_dev_map(bp.map_view(fo, i), real), maps[i]) < TOL[prec], (rep, i)
+
+
+def _wavelet_view(bp, fw, i, j, real):
+    """The scale-j wavelet map of map i inside the batch's flat f_wav buffer."""
+    lib = _lib.lib()
+    _, _, g, k = bp.layout[i]
+    ph, _, wav_off, _ = bp.groups[g]
+    n = ctypes.c_int()
+    off = ctypes.c_int64()
+    cnt = ctypes.c_int64()
+    assert lib.s2let_wav_layout(ctypes.c_void_p(ph), j, ctypes.byref(n), ctypes.byref(off), ctypes.byref(cnt)) == 0
+    per = n.value * (2 * n.value - 1) * (1 if real else 2)
+    start = wav_off + off.value + k * per
+    shape = (n.value, 2 * n.value - 1) if real else (n.value, 2 * n.value - 1, 2)
+    return n.value, fw[start:start + per].view(shape)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_uneven_complex_batch_with_large_maps(prec):
+    """A reduced uneven batch of the batching workload (complex maps, B in {2, 3},
+    J_min = 1) that includes L = 1024 and 512: every map's wavelet maps of every
+    scale on sampled rings against the oracle's direct sum of Eq. wav2 from its
+    coefficients, and every map's reconstruction against its input."""
+    Ls = [1024, 128, 512, 128, 256]
+    Bs = [2, 3, 3, 2, 2]
+    J0, real = 1, False
+    bp = BatchPlan(Ls, Bs, J0, real=real, multires=True, precision=prec)
+    f, fw, fs, fo = bp.buffers()
+    flms, maps = [], []
+    for i, L in enumerate(Ls):
+        flm = inputs.random_flm(L, 4000 + i, real)
+        x = sht.inverse(flm, L)
+        flms.append(flm)
+        maps.append(x)
+        bp.map_view(f, i).copy_(torch.from_numpy(np.ascontiguousarray(np.stack([x.real, x.imag], -1))))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        bp.round_trip(f, fw, fs, fo)
+        stream.synchronize()
+    for i, (L, B) in enumerate(zip(Ls, Bs)):
+        assert rel_err(from_dev_map(bp.map_view(fo, i), real), maps[i]) < TOL[prec], ("round trip", i)
+        _, psi = wavelet.tables(L, B, J0)
+        l_of = np.repeat(np.arange(L), 2 * np.arange(L) + 1)
+        norm = np.sqrt(4 * np.pi / (2 * l_of + 1))
+        for j, kern in zip(range(J0, J0 + len(psi)), psi):
+            n, view = _wavelet_view(bp, fw, i, j, real)
+            rings = sorted({0, 1, n // 3, n // 2, n - 2, n - 1} & set(range(n)))
+            ref = sht.inverse_at((norm * flms[i] * kern[l_of])[:n * n], n, rings, np.arange(2 * n - 1))
+            got = from_dev_map(view, real)[rings]
+            assert np.max(np.abs(got - ref)) / np.max(np.abs(from_dev_map(view, real))) < TOL[prec], (i, j)
