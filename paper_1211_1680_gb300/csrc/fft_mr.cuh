@@ -80,12 +80,13 @@ __host__ __device__ constexpr bool mr_supported(int P)
 //   shm[p]   = e^{-i a pi / P} at position p = rev[k], a = k (k < N) or k - P:
 //              the half-sample shift theta -> theta - pi/P of the quadrature
 //   shp[p]   = conj(shm[p]) / P
-//   ve[t]    = v(theta_t - pi/P) / P, vfold[t] (t < N): quadrature weights (k_quad_mr)
+//   ve[t]    = v_even(theta_t - pi/P) / P, vfold[t] (t < N): quadrature weights,
+//   qd[t], qa[t] (t < N): pole-ring columns of the shifted-grid product (k_quad_mr)
 struct MrTab {
     const float2 *tw;
     const int *rev;
     const float2 *shm, *shp;
-    const float *ve, *vfold;
+    const float *ve, *vfold, *qd, *qa;
 };
 
 // ---------------------------------------------------------------- small DFTs
@@ -459,55 +460,80 @@ __global__ void __launch_bounds__(MR_THREADS, 3) k_ring_inv_real_mr(const float2
 // trigonometric polynomial of degree N - 1).  With x~_{P-1-t} = sigma x_t the
 // v_odd term folds to vfold_t x_t.  The products with the phases and weights
 // ride on the last pass of each transform; the extension on the first.
+//
+// Two columns per transform.  Write v = v_s + v_a with v_a = (pi/2) sin(phi), the
+// part odd under the reflection t -> P - 1 - t.  The shifted-grid product with v_s
+// alone, W = K^T diag(v_s) K, commutes with the reflection, so it keeps the
+// symmetric and antisymmetric parts of its input apart: a column e of parity +1
+// and a column o of parity -1 (adjacent orders) share one transform of
+//   z = ext_+(e) + ext_-(o)   (z_t = e_t + o_t, z_{P-1-t} = e_t - o_t, t < N),
+// and w = W z splits by the reflection.  ext_-(o) is antisymmetric except at the
+// fixed point t = N - 1, where it holds d = o_{N-1}; that part, d delta_{N-1}, is
+// symmetric, and so is the v_a part of the full product applied to ext_-(o) off the
+// pole.  With the pole-ring columns qd = W delta_{N-1} and qa = 2 K^T diag(v_a) K
+// delta_{N-1} (antisymmetric; tables of the plan), for t < N - 1:
+//   G_e,t = w_t + w_{P-1-t} - 2 d qd_t + vfold_t e_t
+//   G_o,t = w_t - w_{P-1-t} + d qa_t + vfold_t o_t
+// and at the pole ring
+//   G_e,N-1 = w_{N-1} - d qd_{N-1} + vfold_{N-1} e_{N-1}
+//   G_o,N-1 = d (qd_{N-1} + vfold_{N-1}) + sum_{t < N-1} qa_t o_t,
+// the same linear map per column as one transform each, at half the transforms.
+//
 // In FP32 the FFT form spreads each column's rounding error evenly over theta,
 // where the dense product keeps it local; for the smallest orders, whose
 // Legendre functions are largest at the poles, that raised the error of the
 // finest wavelet maps at L = 2048 near the poles tenfold, to 1.8e-5.  So the
 // orders |m| <= MR_QUAD_DENSE_M stay with the dense product (measured at L =
 // 2048: 8.6e-7 with that split, 1.1e-6 all dense) and this kernel takes the rest.
-// CPB columns per block; column c of map b is the row [b][mi] of the
-// order-major spectra with mi = mstart + r + (r >= seg0 ? gap : 0), r = c mod K
-// (K columns per map), m = mi - m_offset.
+// CPB transforms per block; map b has K columns r = 0..K-1, the rows [b][mi] of
+// the order-major spectra with mi = mstart + r + (r >= seg0 ? gap : 0) (m = mi -
+// m_offset), in two segments [0, seg0) and [seg0, K) of consecutive orders.
+// Transform (unit) uu of a map takes columns r0 = 2 uu and r0 + 1 of the first
+// segment (uu < useg = ceil(seg0 / 2)), else r0 = seg0 + 2 (uu - useg) and r0 + 1
+// of the second; the second column is absent past its segment's end.
 constexpr int MR_QUAD_DENSE_M = 32;
 template <int P> constexpr int mr_quad_cpb() { return P > 2048 ? 2 : 8; }
 template <int P> constexpr size_t mr_quad_smem() { return (size_t)mr_quad_cpb<P>() * P * sizeof(float2); }
 
 struct MrCols {
-    int nmi, m_offset, K, mstart, seg0, gap, ncols;
+    int nmi, m_offset, K, mstart, seg0, gap;
+    int useg, upm, nunits;           // units in the first segment, per map, in all
 };
 
 template <int P>
 __global__ void __launch_bounds__(MR_THREADS, 3) k_quad_mr(const float2 *__restrict__ Fin, float2 *__restrict__ Gout,
                                                            MrCols C, MrTab T)
 {
-    constexpr int N = (P + 1) / 2, CPB = mr_quad_cpb<P>();
+    constexpr int N = (P + 1) / 2, CPB = mr_quad_cpb<P>(), NW = MR_THREADS / 32;
     extern __shared__ __align__(16) float2 mr_buf[];
-    __shared__ float sgn[CPB];
-    __shared__ int rowof[CPB];       // [b][mi] row of each column of the block, -1 past the end
-    const int c0 = blockIdx.x * CPB;
+    __shared__ int rowe[CPB], rowo[CPB];      // rows of the parity +1 and -1 columns, -1 if absent
+    __shared__ float2 red[CPB][NW];
     if (threadIdx.x < CPB) {
-        const int c = c0 + threadIdx.x;
-        int row = -1;
-        float sg = 1.f;
-        if (c < C.ncols) {
-            const int b = c / C.K, r = c - b * C.K;
-            const int mi = C.mstart + r + (r >= C.seg0 ? C.gap : 0);
-            row = b * C.nmi + mi;
-            sg = ((mi - C.m_offset) & 1) ? -1.f : 1.f;
+        const int u = blockIdx.x * CPB + threadIdx.x;
+        int re = -1, ro = -1;
+        if (u < C.nunits) {
+            const int b = u / C.upm, uu = u - b * C.upm;
+            const bool first = uu < C.useg;
+            const int r0 = first ? 2 * uu : C.seg0 + 2 * (uu - C.useg);
+            const int rend = first ? C.seg0 : C.K;
+            const int mi0 = C.mstart + r0 + (first ? 0 : C.gap);
+            const int row0 = b * C.nmi + mi0, row1 = r0 + 1 < rend ? row0 + 1 : -1;
+            const bool odd0 = ((mi0 - C.m_offset) & 1) != 0;
+            re = odd0 ? row1 : row0;
+            ro = odd0 ? row0 : row1;
         }
-        rowof[threadIdx.x] = row;
-        sgn[threadIdx.x] = sg;
+        rowe[threadIdx.x] = re;
+        rowo[threadIdx.x] = ro;
     }
     __syncthreads();
     const MrSmem<P> sm{mr_buf};
-    // K x~: DFT of the extension (read from global memory), shift phases, inverse DFT
+    // z = ext_+(e) + ext_-(o), read from global memory by the first pass
     auto ext = [&](int q, int t) -> float2 {
-        const int row = rowof[q];
-        if (row < 0) return make_float2(0.f, 0.f);
-        const float2 *x = Fin + (size_t)row * N;
-        if (t < N) return x[t];
-        const float2 v = x[P - 1 - t];
-        return make_float2(sgn[q] * v.x, sgn[q] * v.y);
+        const int re = rowe[q], ro = rowo[q];
+        const int tt = t < N ? t : P - 1 - t;
+        const float2 e = re >= 0 ? Fin[(size_t)re * N + tt] : make_float2(0.f, 0.f);
+        const float2 o = ro >= 0 ? Fin[(size_t)ro * N + tt] : make_float2(0.f, 0.f);
+        return t < N ? make_float2(e.x + o.x, e.y + o.y) : make_float2(e.x - o.x, e.y - o.y);
     };
     constexpr int NP = mr_factors(P).n;
     if constexpr (NP >= 2) {
@@ -535,19 +561,57 @@ __global__ void __launch_bounds__(MR_THREADS, 3) k_quad_mr(const float2 *__restr
         });
         mr_fft_dit<P, true, CPB>(mr_buf, T.tw, sm, sm);
     }
-    // fold, plus the odd-point term
-    for (int i = threadIdx.x; i < CPB * N; i += blockDim.x) {
-        const int q = i / N, t = i - q * N, row = rowof[q];
-        if (row < 0) continue;
-        float2 g = mr_buf[q * P + t];
-        if (t < N - 1) {
-            const float2 h = mr_buf[q * P + P - 1 - t];
-            g.x = fmaf(sgn[q], h.x, g.x);
-            g.y = fmaf(sgn[q], h.y, g.y);
+    // split by the reflection, fold, pole-ring terms and the odd-point term
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = 0; q < CPB; ++q) {
+        const int re = rowe[q], ro = rowo[q];
+        float2 acc = make_float2(0.f, 0.f);
+        if (re >= 0 || ro >= 0) {
+            const float2 d = ro >= 0 ? Fin[(size_t)ro * N + N - 1] : make_float2(0.f, 0.f);
+            for (int t = threadIdx.x; t < N; t += blockDim.x) {
+                const float2 w = mr_buf[q * P + t];
+                const float vf = __ldg(T.vfold + t), qd = __ldg(T.qd + t);
+                if (t < N - 1) {
+                    const float2 h = mr_buf[q * P + P - 1 - t];
+                    if (re >= 0) {
+                        const float2 e = Fin[(size_t)re * N + t];
+                        Gout[(size_t)re * N + t] = make_float2(fmaf(vf, e.x, fmaf(-2.f * qd, d.x, w.x + h.x)),
+                                                               fmaf(vf, e.y, fmaf(-2.f * qd, d.y, w.y + h.y)));
+                    }
+                    if (ro >= 0) {
+                        const float2 o = Fin[(size_t)ro * N + t];
+                        const float qa = __ldg(T.qa + t);
+                        Gout[(size_t)ro * N + t] = make_float2(fmaf(vf, o.x, fmaf(qa, d.x, w.x - h.x)),
+                                                               fmaf(vf, o.y, fmaf(qa, d.y, w.y - h.y)));
+                        acc.x = fmaf(qa, o.x, acc.x);
+                        acc.y = fmaf(qa, o.y, acc.y);
+                    }
+                } else if (re >= 0) {
+                    const float2 e = Fin[(size_t)re * N + t];
+                    Gout[(size_t)re * N + t] = make_float2(fmaf(vf, e.x, fmaf(-qd, d.x, w.x)),
+                                                           fmaf(vf, e.y, fmaf(-qd, d.y, w.y)));
+                }
+            }
         }
-        const float2 x = Fin[(size_t)row * N + t];
-        const float vf = __ldg(T.vfold + t);
-        Gout[(size_t)row * N + t] = make_float2(fmaf(vf, x.x, g.x), fmaf(vf, x.y, g.y));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (lane == 0) red[q][warp] = acc;
+    }
+    __syncthreads();
+    // the pole ring of each parity -1 column: warp partial sums in a fixed order
+    if (threadIdx.x < CPB && rowo[threadIdx.x] >= 0) {
+        const int q = threadIdx.x, ro = rowo[q];
+        float2 s = red[q][0];
+        for (int i = 1; i < NW; ++i) {
+            s.x += red[q][i].x;
+            s.y += red[q][i].y;
+        }
+        const float2 d = Fin[(size_t)ro * N + N - 1];
+        const float c = __ldg(T.qd + N - 1) + __ldg(T.vfold + N - 1);
+        Gout[(size_t)ro * N + N - 1] = make_float2(fmaf(c, d.x, s.x), fmaf(c, d.y, s.y));
     }
 }
 

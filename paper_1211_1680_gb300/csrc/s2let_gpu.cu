@@ -307,9 +307,40 @@ int build_mr_tables(s2let_plan *p, int N, BandDev &bd)
         }
         v[u] = acc + 0.5 * M_PI * s1;
     }
-    std::vector<float> ve(P), vfold(N);
-    for (int t = 0; t < P; ++t) ve[t] = (float)(v[2 * t] / P);
+    // The shifted-grid products keep only the even part of v (without the sin term),
+    // which commutes with the reflection t -> P - 1 - t; the sin term reaches the
+    // folded result only through the pole ring t = N - 1, by the two columns of
+    // K^T diag(.) K at t = N - 1 below.  With K[u][t] = D(2u - 2t - 1),
+    // D(s) = (1/P) sum_{|a| <= N-1} e^{i pi a s / P} = (-1)^((s-1)/2) / (P sin(pi s / 2P)), s odd:
+    //   qd_t = sum_u K[u][t] v_even(u) K[u][N-1],  qa_t = 2 sum_u K[u][t] (pi/2) sin(phi_2u) K[u][N-1]
+    std::vector<double> dk(2 * P + 2 * N);                    // D(s) at dk[s + 2N - 1], s odd
+    for (int s = -(2 * N - 1); s < 2 * P; s += 2) {
+        double sn, cs;
+        s2h::sincospi_rat(s, 2 * P, &sn, &cs);
+        dk[s + 2 * N - 1] = ((((s - 1) / 2) & 1) ? -1.0 : 1.0) / (P * sn);
+    }
+    auto Dk = [&](int s) { return dk[s + 2 * N - 1]; };
+    std::vector<double> vs(P), va(P), kd(P);
+    for (int u = 0; u < P; ++u) {
+        double s1, c1;
+        s2h::sincospi_rat(2 * u, P, &s1, &c1);
+        va[u] = 0.5 * M_PI * s1;
+        vs[u] = v[2 * u] - va[u];
+        kd[u] = Dk(2 * u - P);
+    }
+    std::vector<float> ve(P), vfold(N), qd(N), qa(N);
+    for (int t = 0; t < P; ++t) ve[t] = (float)(vs[t] / P);
     for (int t = 0; t < N; ++t) vfold[t] = (float)(t < N - 1 ? v[2 * t + 1] + v[2 * (P - 1 - t) + 1] : v[2 * t + 1]);
+    for (int t = 0; t < N; ++t) {
+        double sd = 0.0, sa = 0.0;
+        for (int u = 0; u < P; ++u) {
+            const double k = Dk(2 * u - 2 * t - 1) * kd[u];
+            sd += k * vs[u];
+            sa += k * va[u];
+        }
+        qd[t] = (float)sd;
+        qa[t] = (float)(2.0 * sa);
+    }
     int err = S2LET_OK;
     auto &o = p->owned;
     bd.mr.tw = dev_upload(p->mem, tw, o, err);
@@ -318,6 +349,8 @@ int build_mr_tables(s2let_plan *p, int N, BandDev &bd)
     bd.mr.shp = dev_upload(p->mem, shp, o, err);
     bd.mr.ve = dev_upload(p->mem, ve, o, err);
     bd.mr.vfold = dev_upload(p->mem, vfold, o, err);
+    bd.mr.qd = dev_upload(p->mem, qd, o, err);
+    bd.mr.qa = dev_upload(p->mem, qa, o, err);
     if (!err) bd.has_mr = true;
     return err;
 }
@@ -438,13 +471,15 @@ void *run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream
                 C.K = 2 * C.seg0;
             } else {
                 C.mstart = mcut + 1;
-                C.seg0 = n;
-                C.gap = 0;
                 C.K = n - mcut - 1;
+                C.seg0 = C.K;
+                C.gap = 0;
             }
-            C.ncols = C.K * p->batch;
-#define S2G_MR_LAUNCH(P_)                                                                                          \
-    k_quad_mr<P_><<<(C.ncols + mr_quad_cpb<P_>() - 1) / mr_quad_cpb<P_>(), MR_THREADS, mr_quad_smem<P_>(), st>>>( \
+            C.useg = (C.seg0 + 1) / 2;
+            C.upm = C.useg + (C.K - C.seg0 + 1) / 2;
+            C.nunits = C.upm * p->batch;
+#define S2G_MR_LAUNCH(P_)                                                                                           \
+    k_quad_mr<P_><<<(C.nunits + mr_quad_cpb<P_>() - 1) / mr_quad_cpb<P_>(), MR_THREADS, mr_quad_smem<P_>(), st>>>( \
         (const float2 *)F, (float2 *)p->G, C, bd.mr)
             S2G_MR_SWITCH(bd.P)
 #undef S2G_MR_LAUNCH
