@@ -47,14 +47,18 @@ WORK = {
 }
 # DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
 # stage's kernel at band-limit N with `batch` maps, from one capture of the kernel
-# as it is now, scaled by N^2 x maps (the stage's data grow so); a stage missing
-# here has no capture of its current kernels, and its traffic is reported as null
+# as it is now, scaled by N^2 x maps (the stage's data grow so); keyed by stage and
+# by the Legendre kernel variant in use ("recurrence": the float-float recurrence
+# kernels, "table": the kernels that stream the plan's Legendre tables).  A stage
+# or variant missing here has no capture of its current kernel, and its traffic
+# is reported as null
 TRAFFIC = {
     # k_leg_anal_tc, full-band-limit launch at L = 1024, 64 maps: 772.0 + 255.5 MB
     # (G and the recurrence tables read, f_lm written), profiles/quad_anal_tc_L1024_b64_tf32x3.md
-    "leg_anal": {"bytes_at": (1024, 64, 1027.5e6),
-                 "source": "ncu dram read+write of k_leg_anal_tc at L=1024 x 64 maps (1027.5 MB per launch), "
-                           "scaled by N^2 x maps to every launch of the step"},
+    ("leg_anal", "recurrence"): {
+        "bytes_at": (1024, 64, 1027.5e6),
+        "source": "ncu dram read+write of k_leg_anal_tc at L=1024 x 64 maps (1027.5 MB per launch), "
+                  "scaled by N^2 x maps to every launch of the step"},
 }
 
 # noise level of the --denoise steps: white noise of this harmonic standard
@@ -265,6 +269,21 @@ def peak_table(peaks):
     }
 
 
+def legendre_tables(plan):
+    """Per Legendre stage: which values it contracts ("table": the plan's stored
+    Legendre tables, "recurrence": computed in the kernel) at the full band-limit,
+    and the table bytes its launches of one round trip read."""
+    if plan.precision != "tf32x3":
+        return {}
+    tun = plan.tuning()
+    out = {}
+    for stage, key in (("leg_anal", "table_anal"), ("leg_synth", "table_synth")):
+        variant = "table" if tun[plan.L][key] else "recurrence"
+        tbytes = sum(plan.table_bytes(n) for n in plan_bandlimits(plan) if tun[n][key])
+        out[stage] = (variant, tbytes)
+    return out
+
+
 def plan_bandlimits(plan):
     """Band-limits of the transforms in one round trip: each direction runs one
     SHT at L and one per wavelet or scaling map."""
@@ -301,15 +320,26 @@ def stage_roofline(name, st, steps, precision, pk, batch):
     return rec
 
 
-def rooflines(stats, a, peaks, batch, bandlimits):
-    """(roofline of the dominant stage, Legendre sub-record, every stage's record)."""
+def rooflines(stats, a, peaks, batch, bandlimits, tables=None):
+    """(roofline of the dominant stage, Legendre sub-record, every stage's record).
+    tables: {stage: (variant, table bytes read per step)} of the Legendre stages."""
     pk = peak_table(peaks)
+    tables = tables or {}
     recs = {k: stage_roofline(k, v, a.steps, a.precision, pk, batch) for k, v in stats.items() if v["launches"]}
     recs = {k: v for k, v in recs.items() if v is not None}
+    for k, (variant, tbytes) in tables.items():
+        if k in recs:
+            recs[k]["legendre_values"] = variant
+            if tbytes:
+                # the tables are streamed from HBM once per launch
+                recs[k]["table_bytes_per_step"] = tbytes
+                recs[k]["table_gbs"] = tbytes / (recs[k]["ms_per_step"] / 1000) / 1e9
+                recs[k]["table_frac_of_hbm"] = recs[k]["table_gbs"] / pk["hbm"][0]
     dom = max(recs, key=lambda k: recs[k]["ms_per_step"])
     roof = dict(recs[dom])
     roof["kernel"] = dom
-    tr = TRAFFIC.get(dom) if a.precision == "tf32x3" else None
+    variant = tables.get(dom, ("recurrence", 0))[0]
+    tr = TRAFFIC.get((dom, variant)) if a.precision == "tf32x3" else None
     if tr:
         n0, b0, by = tr["bytes_at"]
         # one launch of the stage per transform direction and band-limit of the round trip
@@ -418,7 +448,8 @@ def run_gpu(a, rank, world, local_rank):
         ms = float(t.item())
     value = world * a.batch * a.steps / (ms / 1000.0)
 
-    roof, legendre, all_stages = rooflines(stats, a, measured_peaks(), a.batch, plan_bandlimits(plan))
+    roof, legendre, all_stages = rooflines(stats, a, measured_peaks(), a.batch, plan_bandlimits(plan),
+                                           legendre_tables(plan))
     total_ms = sum(s["ms"] for s in stats.values())
     stage_share = {k: {"share": (s["ms"] / total_ms if total_ms else 0.0), "ms_per_step": s["ms"] / a.steps,
                        "launches_per_step": s["launches"] / a.steps} for k, s in stats.items()}

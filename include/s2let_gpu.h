@@ -72,6 +72,9 @@ extern "C" {
 #define S2LET_QUAD_DENSE 0x800   /* FP32 / TF32X3 plans: the dense quadrature
                                     product at every band-limit, also where the
                                     FFT form (mixed-radix ring length) exists  */
+#define S2LET_LEG_RECURRENCE 0x1000 /* TF32X3 plans only: no Legendre tables;
+                                    every Legendre contraction runs the float-
+                                    float recurrence (see s2let_plan_create) */
 #define S2LET_KERNEL_BSPLINE 0x400 /* B-spline generating functions (footnote of
                                     Sect. 2.2) instead of the smooth scale-
                                     discretised ones: k(t) = 3/2 B_3(2 t B^(J-1)
@@ -98,8 +101,16 @@ int s2let_jmax(int L, int B);
  * workspace.  Limits: 3 <= L <= 4096, 1 <= batch (else S2LET_ERR_ARG); FP64
  * plans and S2LET_QUAD_FFT64 only up to L = 2048 (their shared-memory FFTs of
  * length M >= 4L - 3 would exceed the SM's shared memory; S2LET_ERR_UNSUPPORTED).
- * The MW sampling theorem is stable to such band-limits (Sect. 2.1).  On error
- * *plan is NULL. */
+ * The MW sampling theorem is stable to such band-limits (Sect. 2.1).
+ * TF32X3 plans without S2LET_LEG_RECURRENCE also store the associated Legendre
+ * values lambda_lm(theta_t) of each band-limit N (the FP64 recurrence from the
+ * FP64 seeds, rounded to FP32; about N^3 / 2 values less those below 2^-100, 4
+ * bytes each), so that the Legendre stages stream them instead of recomputing
+ * them for every batch.  Band-limits are stored from the smallest up while the
+ * total stays within S2LET_LEG_TABLE_MAX_BYTES and half the device memory free
+ * at creation; the others use the recurrence.  s2let_plan_leg_table_bytes
+ * reports the sizes.  On error *plan is NULL. */
+#define S2LET_LEG_TABLE_MAX_BYTES (64ull << 30)
 int s2let_plan_create(s2let_plan **plan, int L, int B, int J_min, int flags, int batch);
 
 /* Free a plan and everything it owns (NULL is accepted). */
@@ -237,16 +248,25 @@ int s2let_sht_forward_adjoint(s2let_plan *plan, const void *glm, void *gf, void 
  * each stage on the plan's own workspace (contents ignored) with the plan's
  * batch, and keeps the fastest: the ring-DFT block size (M/8, M/16, M/32 or
  * M/64 threads, 32..512) for all plans, and for TF32X3 plans, per contraction stage
- * (quadrature, Legendre analysis, Legendre synthesis), the tensor-core kernel
- * or the CUDA-core FP32 kernel (same float-float recurrence; both meet the
- * TF32X3 accuracy).  Runs on `stream` and synchronises it; overwrites the
- * workspace; the choices persist for the plan.  Without this call the plan
- * uses the tensor-core kernels and M/16 threads. */
+ * (quadrature: dense tensor-core, dense CUDA-core or FFT form; Legendre
+ * analysis and synthesis: the tensor-core kernel on the plan's Legendre tables
+ * where it holds them, the tensor-core kernel with the float-float recurrence,
+ * or the CUDA-core FP32 kernel; all meet the TF32X3 accuracy).  Runs on
+ * `stream` and synchronises it; overwrites the workspace; the choices persist
+ * for the plan.  Without this call the plan uses the tensor-core kernels (on
+ * the tables where held) and M/16 threads. */
 int s2let_plan_autotune(s2let_plan *plan, void *stream);
+
+/* Bytes of device memory that hold the Legendre tables of band-limit N of the
+ * plan (0: no tables there), or of all its band-limits for N = 0.  A band-limit
+ * the plan does not have: S2LET_ERR_ARG. */
+int s2let_plan_leg_table_bytes(const s2let_plan *plan, int N, size_t *bytes);
 
 /* The choices in force for band-limit N of the plan: 1 = tensor-core kernel,
  * 0 = CUDA-core kernel; *tc_quad = 2: the theta quadrature runs in its FFT form
- * (mixed-radix, FP32) instead of a dense product. */
+ * (mixed-radix, FP32) instead of a dense product; *tc_anal, *tc_synth = 2: the
+ * tensor-core Legendre kernel reads the plan's Legendre tables (1: it runs the
+ * recurrence). */
 int s2let_plan_tuning(const s2let_plan *plan, int N, int *tc_quad, int *tc_anal, int *tc_synth,
                       int *fft_threads);
 

@@ -25,6 +25,7 @@ S2LET_QUAD_FFT64 = 0x100
 S2LET_TC_SPLIT3 = 0x200
 S2LET_KERNEL_BSPLINE = 0x400
 S2LET_QUAD_DENSE = 0x800
+S2LET_LEG_RECURRENCE = 0x1000
 
 # every symbol the header declares, with (restype, argtypes)
 _vp = ctypes.c_void_p
@@ -50,6 +51,7 @@ SIGNATURES = {
     "s2let_sht_forward_adjoint": (_i, [_vp, _vp, _vp, _vp]),
     "s2let_plan_status": (_i, [_vp]),
     "s2let_plan_test_timeout": (_i, [_vp, _vp]),
+    "s2let_plan_leg_table_bytes": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_size_t)]),
     "s2let_set_allocator": (_i, [ALLOC_FN, FREE_FN, _vp]),
     "s2let_plan_autotune": (_i, [_vp, _vp]),
     "s2let_batch_autotune": (_i, [_vp, _vp]),

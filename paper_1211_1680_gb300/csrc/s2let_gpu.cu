@@ -28,6 +28,7 @@
 #include "gemm_fp32.cuh"
 #include "tc_kernels.cuh"
 #include "legendre_tc.cuh"
+#include "legendre_img.cuh"
 #include "quad_tc.cuh"
 #include "host_tables.h"
 #include "legendre.cuh"
@@ -120,6 +121,13 @@ struct BandDev {
     // (mr_quad; else the dense product)
     bool has_mr = false, mr_quad = true;
     MrTab mr{};
+    // TF32X3 plans: precomputed Legendre tables (legendre_img.cuh) when they fit
+    // the plan's budget, used by the tensor-core contractions (img_*; else the
+    // recurrence kernels)
+    bool has_img = false, img_anal = true, img_synth = true;
+    LegImg img{};
+    int n_adt = 0;                          // analysis blocks (m, degree tile)
+    size_t img_bytes = 0;
 };
 
 }  // namespace
@@ -140,6 +148,7 @@ struct s2let_plan {
     void *F = nullptr, *flm = nullptr, *G = nullptr;   // workspace
     void *Ft = nullptr;                                // ring-major spectra of the ring DFTs
     float4 *anal_st = nullptr;                         // TF32X3, L > 2048: recurrence states of k_leg_anal_tc
+    size_t img_budget = 0, img_used = 0;               // TF32X3: bytes allowed / held by Legendre tables
     bool quad_gemm = false;                 // FP32 plans: theta quadrature as a dense FP32 product
     bool tc = false;                        // TF32X3 plans: dense products on the tensor cores
     int tc_split = 2;                       // TF32 parts per operand in the tensor-core products
@@ -524,7 +533,13 @@ int run_synth(const s2let_plan *p, const BandDev &bd, const void *src, const voi
         const int bt = p->cplx ? LegCols<true>::BT : LegCols<false>::BT;
         dim3 grid((bd.N + LS_RT - 1) / LS_RT, bd.N, (p->batch + bt - 1) / bt);
         const LegTab<float> tab = leg_tab<float>(p, bd);
-        if (p->tc && bd.tc_synth && p->cplx)
+        if (p->tc && bd.tc_synth && bd.has_img && bd.img_synth) {
+            const LegImgArgs a{(const float2 *)src, p->L, (const float *)kfac, (float)scale, 0, (float2 *)dst, 0,
+                               bd.N, p->batch, bd.img, p->d_err};
+            const dim3 g((bd.N + 127) / 128, bd.N, (p->batch + bt - 1) / bt);
+            if (p->cplx) k_leg_img<false, true><<<g, LT_THREADS, leg_img_smem(), st>>>(a);
+            else k_leg_img<false, false><<<g, LT_THREADS, leg_img_smem(), st>>>(a);
+        } else if (p->tc && bd.tc_synth && p->cplx)
             k_leg_synth_tc<true><<<grid, LT_THREADS, ls_synth_smem(), st>>>(
                 (const float2 *)src, p->L, (const float *)kfac, (float)scale, (float2 *)dst, bd.N, p->batch, tab,
                 p->d_err);
@@ -586,7 +601,13 @@ int run_anal(const s2let_plan *p, const BandDev &bd, const void *G, const void *
         dim3 grid(bd.N, (p->batch + bt - 1) / bt);
         const size_t sm = anal_gemm_smem(bd.N);
         const LegTab<float> tab = leg_tab<float>(p, bd);
-        if (p->tc && bd.tc_anal && p->cplx)
+        if (p->tc && bd.tc_anal && bd.has_img && bd.img_anal) {
+            const LegImgArgs a{(const float2 *)G, 0, (const float *)kfac, (float)scale, acc, (float2 *)dst, p->L,
+                               bd.N, p->batch, bd.img, p->d_err};
+            const dim3 g(bd.n_adt, (p->batch + bt - 1) / bt);
+            if (p->cplx) k_leg_img<true, true><<<g, LT_THREADS, leg_img_smem(), st>>>(a);
+            else k_leg_img<true, false><<<g, LT_THREADS, leg_img_smem(), st>>>(a);
+        } else if (p->tc && bd.tc_anal && p->cplx)
             k_leg_anal_tc<true><<<grid, LT_ANAL_THREADS, la_anal_smem(bd.N), st>>>(
                 (const float2 *)G, bd.N, (const float *)kfac, (float)scale, acc, (float2 *)dst, p->L, p->batch, tab,
                 p->d_err, p->anal_st);
@@ -881,6 +902,10 @@ void set_smem_limits(int Mmax)
     allow_smem(k_leg_synth_tc<true>, ls_synth_smem());
     allow_smem(k_leg_anal_tc<false>, la_anal_smem(LA_ST_SMEM_MAX));
     allow_smem(k_leg_anal_tc<true>, la_anal_smem(LA_ST_SMEM_MAX));
+    allow_smem(k_leg_img<true, false>, leg_img_smem());
+    allow_smem(k_leg_img<true, true>, leg_img_smem());
+    allow_smem(k_leg_img<false, false>, leg_img_smem());
+    allow_smem(k_leg_img<false, true>, leg_img_smem());
     allow_smem(k_leg_anal_gemm<false>, anal_gemm_smem(kMaxL));
     allow_smem(k_leg_anal_gemm<true>, anal_gemm_smem(kMaxL));
     allow_smem(k_theta_quad<double, double, 16>, d);
@@ -985,6 +1010,61 @@ std::vector<s2h::cd> group_major(const std::vector<s2h::cd> &v, int R)
     return out;
 }
 
+// Legendre tables of band-limit N (TF32X3 plans), after the seeds: kept when
+// they fit the plan's remaining budget, else the band uses the recurrence kernels.
+int build_leg_img(s2let_plan *p, BandDev &bd)
+{
+    const int N = bd.N, nkr = (N + 31) / 32;
+    const size_t nmk = (size_t)N * nkr;
+    int *i0 = nullptr, *off_d = nullptr;
+    int2 *adt_d = nullptr;
+    unsigned char *img = nullptr;
+    if (dm_alloc(p->mem, &i0, nmk * sizeof(int)) != cudaSuccess) return S2LET_ERR_ALLOC;
+    k_img_i0<<<(unsigned)((nmk + 255) / 256), 256>>>(N, bd.ls, i0);
+    std::vector<int> h(nmk), off(nmk);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpy(h.data(), i0, nmk * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        dm_free(p->mem, i0);
+        return S2LET_ERR_CUDA;
+    }
+    int64_t nblk = 1;                                   // block 0: zeros
+    for (int m = 0; m < N; ++m)
+        for (int k = 0; k < nkr; ++k) {
+            off[(size_t)m * nkr + k] = (int)std::min<int64_t>(nblk, INT32_MAX);
+            nblk += li_nib(N, m) - h[(size_t)m * nkr + k];
+        }
+    const size_t bytes = (size_t)nblk * LI_BLK;
+    if (nblk > INT32_MAX || p->img_used + bytes > p->img_budget) {
+        dm_free(p->mem, i0);
+        return S2LET_OK;                                // no tables for this band-limit
+    }
+    std::vector<int2> adt;
+    for (int m = 0; m < N; ++m)
+        for (int dt = 0; dt < (N - m + 127) / 128; ++dt) adt.push_back(make_int2(m, dt));
+    if (dm_alloc(p->mem, &img, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        dm_free(p->mem, i0);
+        return S2LET_OK;                                // no room after all: the recurrence kernels
+    }
+    p->owned.push_back(i0);
+    p->owned.push_back(img);
+    int err = S2LET_OK;
+    off_d = dev_upload(p->mem, off, p->owned, err);
+    adt_d = dev_upload(p->mem, adt, p->owned, err);
+    if (err) return err;
+    if (cudaMemset(img, 0, LI_BLK) != cudaSuccess) return S2LET_ERR_CUDA;
+    const size_t nthr = nmk * 32;
+    k_img_fill<<<(unsigned)((nthr + 127) / 128), 128>>>(N, bd.ls, bd.seed, bd.ringd, p->coefd, p->L, i0, off_d,
+                                                        img);
+    if (cudaGetLastError() != cudaSuccess) return S2LET_ERR_CUDA;
+    bd.img = LegImg{img, i0, off_d, adt_d, nkr};
+    bd.n_adt = (int)adt.size();
+    bd.img_bytes = bytes;
+    bd.has_img = true;
+    p->img_used += bytes;
+    return S2LET_OK;
+}
+
 int build_band_dev(s2let_plan *p, int N, BandDev &bd)
 {
     s2h::Band h;
@@ -1068,7 +1148,12 @@ int build_band_dev(s2let_plan *p, int N, BandDev &bd)
     if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
     dm_free(p->mem, mant);
     dm_free(p->mem, expo);
-    return ce == cudaSuccess ? S2LET_OK : S2LET_ERR_CUDA;
+    if (ce != cudaSuccess) return S2LET_ERR_CUDA;
+    if (p->tc && p->img_budget > 0) {
+        if ((err = build_leg_img(p, bd))) return err;
+        if (cudaDeviceSynchronize() != cudaSuccess) return S2LET_ERR_CUDA;
+    }
+    return S2LET_OK;
 }
 
 int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
@@ -1080,9 +1165,10 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
     const int prec = flags & S2LET_PREC_MASK;
     if (prec != S2LET_PREC_FP64 && prec != S2LET_PREC_FP32 && prec != S2LET_PREC_TF32X3) return S2LET_ERR_ARG;
     if (flags & ~(S2LET_COMPLEX | S2LET_MULTIRES | S2LET_PREC_MASK | S2LET_QUAD_FFT64 | S2LET_TC_SPLIT3 |
-                  S2LET_KERNEL_BSPLINE | S2LET_QUAD_DENSE))
+                  S2LET_KERNEL_BSPLINE | S2LET_QUAD_DENSE | S2LET_LEG_RECURRENCE))
         return S2LET_ERR_ARG;
     if ((flags & S2LET_TC_SPLIT3) && prec != S2LET_PREC_TF32X3) return S2LET_ERR_ARG;
+    if ((flags & S2LET_LEG_RECURRENCE) && prec != S2LET_PREC_TF32X3) return S2LET_ERR_ARG;
     if ((flags & S2LET_QUAD_FFT64) && prec == S2LET_PREC_FP64) return S2LET_ERR_ARG;
     if (L > kMaxL64 && (prec == S2LET_PREC_FP64 || (flags & S2LET_QUAD_FFT64))) return S2LET_ERR_UNSUPPORTED;
     if ((flags & S2LET_QUAD_DENSE) && (prec == S2LET_PREC_FP64 || (flags & S2LET_QUAD_FFT64))) return S2LET_ERR_ARG;
@@ -1123,6 +1209,12 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return S2LET_ERR_CUDA;
+    }
+    if (p->tc && !(flags & S2LET_LEG_RECURRENCE)) {
+        // Legendre tables: at most half the free device memory, and S2LET_LEG_TABLE_MAX_BYTES
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return S2LET_ERR_CUDA;
+        p->img_budget = std::min<size_t>(fr / 2, (size_t)S2LET_LEG_TABLE_MAX_BYTES);
     }
     if (dm_alloc(p->mem, &p->d_err, sizeof(int)) != cudaSuccess) return S2LET_ERR_ALLOC;
     p->owned.push_back(p->d_err);
@@ -1273,16 +1365,34 @@ template <typename R> int autotune_t(s2let_plan *p, cudaStream_t st)
                 const float q2 = time_best(st, [&] { run_theta_quad<R>(p, bd, p->F, st, &e); });
                 bd.mr_quad = q2 <= std::min(q0, q1);
             }
+            // Legendre stages: tensor-core kernel on the tables (where the plan holds
+            // them), tensor-core kernel with the recurrence, CUDA-core kernel
+            auto synth = [&] { run_synth<R>(p, bd, p->flm, nullptr, 1.0, p->F, st); };
+            auto anal = [&] { run_anal<R>(p, bd, p->F, nullptr, 1.0, 0, p->flm, st); };
             bd.tc_synth = true;
-            const float s1 = time_best(st, [&] { run_synth<R>(p, bd, p->flm, nullptr, 1.0, p->F, st); });
+            bd.img_synth = false;
+            const float s1 = time_best(st, synth);
+            float s2 = 1e30f;
+            if (bd.has_img) {
+                bd.img_synth = true;
+                s2 = time_best(st, synth);
+            }
             bd.tc_synth = false;
-            const float s0 = time_best(st, [&] { run_synth<R>(p, bd, p->flm, nullptr, 1.0, p->F, st); });
-            bd.tc_synth = s1 <= s0;
+            const float s0 = time_best(st, synth);
+            bd.tc_synth = std::min(s1, s2) <= s0;
+            bd.img_synth = s2 <= s1;
             bd.tc_anal = true;
-            const float a1 = time_best(st, [&] { run_anal<R>(p, bd, p->F, nullptr, 1.0, 0, p->flm, st); });
+            bd.img_anal = false;
+            const float a1 = time_best(st, anal);
+            float a2 = 1e30f;
+            if (bd.has_img) {
+                bd.img_anal = true;
+                a2 = time_best(st, anal);
+            }
             bd.tc_anal = false;
-            const float a0 = time_best(st, [&] { run_anal<R>(p, bd, p->F, nullptr, 1.0, 0, p->flm, st); });
-            bd.tc_anal = a1 <= a0;
+            const float a0 = time_best(st, anal);
+            bd.tc_anal = std::min(a1, a2) <= a0;
+            bd.img_anal = a2 <= a1;
         }
         if (cudaGetLastError() != cudaSuccess) e = S2LET_ERR_CUDA;
         if (e) break;
@@ -1518,6 +1628,19 @@ int s2let_plan_autotune(s2let_plan *p, void *stream)
     return S2_DISPATCH(autotune_t, p, (cudaStream_t)stream);
 }
 
+int s2let_plan_leg_table_bytes(const s2let_plan *p, int N, size_t *bytes)
+{
+    if (!p || !bytes) return S2LET_ERR_ARG;
+    if (N == 0) {
+        *bytes = p->img_used;
+        return S2LET_OK;
+    }
+    auto it = p->bands.find(N);
+    if (it == p->bands.end()) return S2LET_ERR_ARG;
+    *bytes = it->second.has_img ? it->second.img_bytes : 0;
+    return S2LET_OK;
+}
+
 int s2let_plan_tuning(const s2let_plan *p, int N, int *tc_quad, int *tc_anal, int *tc_synth, int *fft_threads_out)
 {
     if (!p) return S2LET_ERR_ARG;
@@ -1528,8 +1651,8 @@ int s2let_plan_tuning(const s2let_plan *p, int N, int *tc_quad, int *tc_anal, in
         *tc_quad = (!p->fp64 && p->quad_gemm && bd.has_mr && bd.mr_quad && bd.N - 1 > MR_QUAD_DENSE_M)
                        ? 2
                        : (p->tc && bd.tc_quad);
-    if (tc_anal) *tc_anal = p->tc && bd.tc_anal;
-    if (tc_synth) *tc_synth = p->tc && bd.tc_synth;
+    if (tc_anal) *tc_anal = (p->tc && bd.tc_anal) ? (bd.has_img && bd.img_anal ? 2 : 1) : 0;
+    if (tc_synth) *tc_synth = (p->tc && bd.tc_synth) ? (bd.has_img && bd.img_synth ? 2 : 1) : 0;
     if (fft_threads_out) *fft_threads_out = bd.fft_th ? bd.fft_th : fft_threads(bd.M);
     return S2LET_OK;
 }

@@ -8,8 +8,8 @@ import torch
 
 from . import _lib
 from ._lib import (S2LET_COMPLEX, S2LET_MULTIRES, S2LET_PREC_FP32, S2LET_PREC_FP64,  # noqa: F401
-                   S2LET_KERNEL_BSPLINE, S2LET_PREC_TF32X3, S2LET_QUAD_DENSE, S2LET_QUAD_FFT64, S2LET_TC_SPLIT3,
-                   check)
+                   S2LET_KERNEL_BSPLINE, S2LET_LEG_RECURRENCE, S2LET_PREC_TF32X3, S2LET_QUAD_DENSE,
+                   S2LET_QUAD_FFT64, S2LET_TC_SPLIT3, check)
 
 PRECISIONS = {"fp64": S2LET_PREC_FP64, "fp32": S2LET_PREC_FP32, "tf32x3": S2LET_PREC_TF32X3}
 
@@ -70,10 +70,13 @@ class Plan:
     """A batched transform plan: `batch` maps of band-limit L, dilation B,
     lowest scale J_min (Sect. 2.2), real or complex, multiresolution or not,
     precision "fp64", "fp32" or "tf32x3", generating functions `kernel` "sd"
-    (smooth scale-discretised) or "bspline" (footnote of Sect. 2.2)."""
+    (smooth scale-discretised) or "bspline" (footnote of Sect. 2.2).  TF32X3
+    plans store the Legendre values of each band-limit that fits the table budget
+    unless leg_recurrence is set (see table_bytes())."""
 
     def __init__(self, L, B, J_min, batch=1, real=True, multires=True, precision="fp64",
-                 quad_fft64=False, tc_split3=False, device=None, kernel="sd", quad_dense=False):
+                 quad_fft64=False, tc_split3=False, device=None, kernel="sd", quad_dense=False,
+                 leg_recurrence=False):
         flags = (0 if real else S2LET_COMPLEX) | (S2LET_MULTIRES if multires else 0) | PRECISIONS[precision]
         flags |= _kernel_flag(kernel)
         if quad_fft64:
@@ -82,6 +85,8 @@ class Plan:
             flags |= S2LET_TC_SPLIT3
         if quad_dense:
             flags |= S2LET_QUAD_DENSE
+        if leg_recurrence:
+            flags |= S2LET_LEG_RECURRENCE
         self.L, self.B, self.J_min, self.batch = L, B, J_min, batch
         self.real, self.multires, self.precision, self.kernel = real, multires, precision, kernel
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -115,14 +120,23 @@ class Plan:
         return self.tuning()
 
     def tuning(self):
-        """{band-limit: {"tc_quad", "fft_quad", "tc_anal", "tc_synth": bool, "fft_threads": int}}."""
+        """{band-limit: {"tc_quad", "fft_quad", "tc_anal", "tc_synth", "table_anal", "table_synth": bool,
+        "fft_threads": int}} (table_*: the tensor-core Legendre kernel reads the plan's tables)."""
         out = {}
         for n in sorted({self.L, self.N_scal} | {s[1] for s in self.scales}):
             v = [ctypes.c_int() for _ in range(4)]
             check("s2let_plan_tuning", _lib.lib().s2let_plan_tuning(self._h, n, *[ctypes.byref(x) for x in v]))
             out[n] = {"tc_quad": v[0].value == 1, "fft_quad": v[0].value == 2, "tc_anal": bool(v[1].value),
-                      "tc_synth": bool(v[2].value), "fft_threads": v[3].value}
+                      "tc_synth": bool(v[2].value), "table_anal": v[1].value == 2, "table_synth": v[2].value == 2,
+                      "fft_threads": v[3].value}
         return out
+
+    def table_bytes(self, N=0):
+        """Device bytes of the plan's Legendre tables at band-limit N, or of all of
+        them for N = 0 (s2let_plan_leg_table_bytes)."""
+        b = ctypes.c_size_t()
+        check("s2let_plan_leg_table_bytes", _lib.lib().s2let_plan_leg_table_bytes(self._h, N, ctypes.byref(b)))
+        return b.value
 
     def status(self):
         """S2LET_OK, or S2LET_ERR_TIMEOUT if a bounded device wait gave up (synchronises)."""

@@ -35,11 +35,13 @@ def rel_err(x, ref):
     return float(np.max(np.abs(x - ref)) / (den if den > 0 else 1.0))
 
 
-TOL = {"fp64": 1e-10, "fp32": 1e-5, "tf32x3": 1e-5, "tf32x3s3": 1e-5}
+TOL = {"fp64": 1e-10, "fp32": 1e-5, "tf32x3": 1e-5, "tf32x3s3": 1e-5, "tf32x3rec": 1e-5}
 
 
 def plan_kwargs(prec):
     """Plan keyword arguments for a precision label of the tests."""
     if prec == "tf32x3s3":
         return {"precision": "tf32x3", "tc_split3": True}
+    if prec == "tf32x3rec":                      # Legendre values by the recurrence, no tables
+        return {"precision": "tf32x3", "leg_recurrence": True}
     return {"precision": prec}

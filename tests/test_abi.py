@@ -48,7 +48,11 @@ def test_plan_argument_errors_need_no_gpu():
     assert L.s2let_plan_create(ctypes.byref(h), 32, 2, 5, 0, 1) == _lib.S2LET_ERR_ARG
     assert L.s2let_plan_create(ctypes.byref(h), 2, 2, 0, 0, 1) == _lib.S2LET_ERR_ARG
     assert L.s2let_plan_create(ctypes.byref(h), 32, 1, 0, 0, 1) == _lib.S2LET_ERR_ARG
-    assert L.s2let_plan_create(ctypes.byref(h), 32, 2, 0, 0x1000, 1) == _lib.S2LET_ERR_ARG
+    assert L.s2let_plan_create(ctypes.byref(h), 32, 2, 0, 0x2000, 1) == _lib.S2LET_ERR_ARG
+    # the Legendre-table switch belongs to TF32X3 plans only
+    for prec in (_lib.S2LET_PREC_FP64, _lib.S2LET_PREC_FP32):
+        assert L.s2let_plan_create(ctypes.byref(h), 32, 2, 0, prec | _lib.S2LET_LEG_RECURRENCE,
+                                   1) == _lib.S2LET_ERR_ARG
     assert L.s2let_plan_create(ctypes.byref(h), 4097, 2, 0, _lib.S2LET_PREC_TF32X3, 1) == _lib.S2LET_ERR_ARG
     # FP64 plans stop at L = 2048 (their shared-memory FFTs), FP32 / TF32X3 plans at 4096
     assert L.s2let_plan_create(ctypes.byref(h), 4096, 2, 0, 0, 1) == _lib.S2LET_ERR_UNSUPPORTED
@@ -67,7 +71,7 @@ def test_flag_constants_match_header():
         if hasattr(_lib, k):
             assert getattr(_lib, k) == v, k
     for k in ("S2LET_COMPLEX", "S2LET_MULTIRES", "S2LET_PREC_FP32", "S2LET_PREC_TF32X3", "S2LET_QUAD_FFT64",
-              "S2LET_TC_SPLIT3", "S2LET_KERNEL_BSPLINE", "S2LET_ERR_ARG"):
+              "S2LET_TC_SPLIT3", "S2LET_KERNEL_BSPLINE", "S2LET_LEG_RECURRENCE", "S2LET_ERR_ARG"):
         assert getattr(_lib, k) == defs[k], k
 
 

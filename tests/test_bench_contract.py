@@ -93,3 +93,12 @@ def test_stage_rooflines_follow_the_work_of_each_stage():
     roof2, _, _ = bench.rooflines(stats2, a, peaks, 64, [2048])
     assert roof2["kernel"] == "ring_fwd" and roof2["bound"] == "hbm" and roof2["traffic"] is None
     assert roof2["frac"] == pytest.approx(60e9 / 0.090 / 1e9 / 6000.0)
+    # Legendre stages on the plan's tables: the table bytes they stream per step
+    # against HBM; DRAM traffic only from a capture of that kernel variant
+    tabs = {"leg_anal": ("table", 30e9), "leg_synth": ("table", 30e9)}
+    roof3, leg3, _ = bench.rooflines(stats, a, peaks, 64, [2048, 8, 4], tabs)
+    assert roof3["legendre_values"] == "table"
+    assert roof3["table_gbs"] == pytest.approx(30e9 / 0.025 / 1e9)
+    assert roof3["table_frac_of_hbm"] == pytest.approx(1200.0 / 6000.0)
+    want = bench.TRAFFIC.get(("leg_anal", "table"))
+    assert (roof3["traffic"] is None) == (want is None)

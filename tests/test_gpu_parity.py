@@ -17,7 +17,7 @@ def _maps(L, seeds, real, kind="white"):
     return np.stack([sht.inverse(inputs.random_flm(L, s, real, kind), L, real=real) for s in seeds])
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "tf32x3s3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "tf32x3s3", "tf32x3rec"])
 @pytest.mark.parametrize("real", [True, False])
 @pytest.mark.parametrize("L", [3, 4, 8, 17, 33, 64, 130])
 def test_sht_forward_inverse(L, real, prec):
@@ -78,6 +78,8 @@ CASES = [  # L, B, J0, multires, real, prec
     (96, 2, 2, True, True, "tf32x3"),
     (40, 3, 1, True, False, "tf32x3"),
     (96, 2, 2, True, True, "tf32x3s3"),
+    (96, 2, 2, True, True, "tf32x3rec"),
+    (40, 3, 1, True, False, "tf32x3rec"),
 ]
 
 
