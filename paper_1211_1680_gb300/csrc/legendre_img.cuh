@@ -109,6 +109,8 @@ static __global__ void k_img_fill(int N, const int *__restrict__ ls, const doubl
 
 // ---------------------------------------------------------------- contraction
 constexpr int LI_NA = 2, LI_NACC = 3, LI_NB = 4, LI_NR = 12, LI_NRAW = 4, LI_D = 4;
+constexpr int LI_ACOL = 128 * LI_NACC;               // TMEM: accumulators, then the operand-A stages
+static_assert(LI_ACOL + 64 * LI_NA <= LT_TMEM_COLS, "tensor memory");
 constexpr int LI_RAW = 4 * LI_BLK;                  // one chunk: the four producer warps' blocks
 constexpr int LI_BSTAGE = 2 * LT_PLANE;             // operand B hi, lo
 constexpr int LI_MAXK = 128;                        // ring chunks of the analysis list (N <= 4096)
@@ -264,7 +266,7 @@ static __global__ void __launch_bounds__(LT_THREADS, 1) k_leg_img(LegImgArgs a)
             }
             if (c >= LI_NA) lt_wait(&sy.done[(c - LI_NA) % LI_NR], par(c - LI_NA), abort);
             tc::fence_after();
-            const uint32_t ahi = tmem + lane_addr + (uint32_t)(384 + 64 * (c % LI_NA)), alo = ahi + 32;
+            const uint32_t ahi = tmem + lane_addr + (uint32_t)(LI_ACOL + 64 * (c % LI_NA)), alo = ahi + 32;
 #pragma unroll
             for (int g = 0; g < 4; ++g) {
                 tc::tmem_st8(ahi + 8 * g, *reinterpret_cast<const float(*)[8]>(hi + 8 * g));
@@ -391,7 +393,7 @@ static __global__ void __launch_bounds__(LT_THREADS, 1) k_leg_img(LegImgArgs a)
             if (ok) {
                 const uint32_t bbase = tc::smem_addr(smem + (c % LI_NB) * LI_BSTAGE);
                 const uint32_t acc = tmem + (uint32_t)(128 * (g % LI_NACC));
-                const uint32_t ahi = tmem + (uint32_t)(384 + 64 * (c % LI_NA)), alo = ahi + 32;
+                const uint32_t ahi = tmem + (uint32_t)(LI_ACOL + 64 * (c % LI_NA)), alo = ahi + 32;
 #pragma unroll
                 for (int ks = 0; ks < 4; ++ks) {
                     const uint64_t b0d = tc::smem_desc_sw128(bbase + ks * 32);
