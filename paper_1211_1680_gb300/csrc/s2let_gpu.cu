@@ -29,6 +29,7 @@
 #include "tc_kernels.cuh"
 #include "legendre_tc.cuh"
 #include "legendre_img.cuh"
+#include "legendre_h16.cuh"
 #include "quad_tc.cuh"
 #include "host_tables.h"
 #include "legendre.cuh"
@@ -125,7 +126,8 @@ struct BandDev {
     // the plan's budget, used by the tensor-core contractions (img_*; else the
     // recurrence kernels)
     bool has_img = false, img_anal = true, img_synth = true;
-    LegImg img{};
+    LegImg img{};                           // block index; img.img = the analysis copy (rows = degrees)
+    unsigned char *img_t = nullptr;         // the synthesis copy (rows = rings)
     int n_adt = 0;                          // analysis blocks (m, degree tile)
     size_t img_bytes = 0;
 };
@@ -149,6 +151,7 @@ struct s2let_plan {
     void *Ft = nullptr;                                // ring-major spectra of the ring DFTs
     float4 *anal_st = nullptr;                         // TF32X3, L > 2048: recurrence states of k_leg_anal_tc
     size_t img_budget = 0, img_used = 0;               // TF32X3: bytes allowed / held by Legendre tables
+    float *csc = nullptr;                              // TF32X3: column scales of the table contractions [b][mi]
     bool quad_gemm = false;                 // FP32 plans: theta quadrature as a dense FP32 product
     bool tc = false;                        // TF32X3 plans: dense products on the tensor cores
     int tc_split = 2;                       // TF32 parts per operand in the tensor-core products
@@ -534,11 +537,15 @@ int run_synth(const s2let_plan *p, const BandDev &bd, const void *src, const voi
         dim3 grid((bd.N + LS_RT - 1) / LS_RT, bd.N, (p->batch + bt - 1) / bt);
         const LegTab<float> tab = leg_tab<float>(p, bd);
         if (p->tc && bd.tc_synth && bd.has_img && bd.img_synth) {
-            const LegImgArgs a{(const float2 *)src, p->L, (const float *)kfac, (float)scale, 0, (float2 *)dst, 0,
-                               bd.N, p->batch, bd.img, p->d_err};
+            const size_t rows = (size_t)p->batch * nmi(p, p->L);
+            p->launches[S2LET_STAGE_LEG_SYNTH] += 1;           // the column scales
+            k_h16_colscale<false><<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(
+                (const float2 *)src, p->L, (const float *)kfac, bd.N, p->batch, p->cplx, p->csc);
+            const LegH16Args a{(const float2 *)src, p->L, (const float *)kfac, (float)scale, 0, (float2 *)dst, 0,
+                               bd.N, p->batch, bd.img, bd.img_t, p->csc, p->d_err};
             const dim3 g((bd.N + 127) / 128, bd.N, (p->batch + bt - 1) / bt);
-            if (p->cplx) k_leg_img<false, true><<<g, LT_THREADS, leg_img_smem(), st>>>(a);
-            else k_leg_img<false, false><<<g, LT_THREADS, leg_img_smem(), st>>>(a);
+            if (p->cplx) k_leg_h16<false, true><<<g, LH_THREADS, leg_h16_smem(), st>>>(a);
+            else k_leg_h16<false, false><<<g, LH_THREADS, leg_h16_smem(), st>>>(a);
         } else if (p->tc && bd.tc_synth && p->cplx)
             k_leg_synth_tc<true><<<grid, LT_THREADS, ls_synth_smem(), st>>>(
                 (const float2 *)src, p->L, (const float *)kfac, (float)scale, (float2 *)dst, bd.N, p->batch, tab,
@@ -602,11 +609,15 @@ int run_anal(const s2let_plan *p, const BandDev &bd, const void *G, const void *
         const size_t sm = anal_gemm_smem(bd.N);
         const LegTab<float> tab = leg_tab<float>(p, bd);
         if (p->tc && bd.tc_anal && bd.has_img && bd.img_anal) {
-            const LegImgArgs a{(const float2 *)G, 0, (const float *)kfac, (float)scale, acc, (float2 *)dst, p->L,
-                               bd.N, p->batch, bd.img, p->d_err};
+            const size_t rows = (size_t)p->batch * nmi(p, bd.N);
+            p->launches[S2LET_STAGE_LEG_ANAL] += 1;            // the column scales
+            k_h16_colscale<true><<<(unsigned)((rows + 7) / 8), 256, 0, st>>>((const float2 *)G, 0, nullptr, bd.N,
+                                                                             p->batch, p->cplx, p->csc);
+            const LegH16Args a{(const float2 *)G, 0, (const float *)kfac, (float)scale, acc, (float2 *)dst, p->L,
+                               bd.N, p->batch, bd.img, bd.img.img, p->csc, p->d_err};
             const dim3 g(bd.n_adt, (p->batch + bt - 1) / bt);
-            if (p->cplx) k_leg_img<true, true><<<g, LT_THREADS, leg_img_smem(), st>>>(a);
-            else k_leg_img<true, false><<<g, LT_THREADS, leg_img_smem(), st>>>(a);
+            if (p->cplx) k_leg_h16<true, true><<<g, LH_THREADS, leg_h16_smem(), st>>>(a);
+            else k_leg_h16<true, false><<<g, LH_THREADS, leg_h16_smem(), st>>>(a);
         } else if (p->tc && bd.tc_anal && p->cplx)
             k_leg_anal_tc<true><<<grid, LT_ANAL_THREADS, la_anal_smem(bd.N), st>>>(
                 (const float2 *)G, bd.N, (const float *)kfac, (float)scale, acc, (float2 *)dst, p->L, p->batch, tab,
@@ -902,10 +913,10 @@ void set_smem_limits(int Mmax)
     allow_smem(k_leg_synth_tc<true>, ls_synth_smem());
     allow_smem(k_leg_anal_tc<false>, la_anal_smem(LA_ST_SMEM_MAX));
     allow_smem(k_leg_anal_tc<true>, la_anal_smem(LA_ST_SMEM_MAX));
-    allow_smem(k_leg_img<true, false>, leg_img_smem());
-    allow_smem(k_leg_img<true, true>, leg_img_smem());
-    allow_smem(k_leg_img<false, false>, leg_img_smem());
-    allow_smem(k_leg_img<false, true>, leg_img_smem());
+    allow_smem(k_leg_h16<true, false>, leg_h16_smem());
+    allow_smem(k_leg_h16<true, true>, leg_h16_smem());
+    allow_smem(k_leg_h16<false, false>, leg_h16_smem());
+    allow_smem(k_leg_h16<false, true>, leg_h16_smem());
     allow_smem(k_leg_anal_gemm<false>, anal_gemm_smem(kMaxL));
     allow_smem(k_leg_anal_gemm<true>, anal_gemm_smem(kMaxL));
     allow_smem(k_theta_quad<double, double, 16>, d);
@@ -1033,7 +1044,8 @@ int build_leg_img(s2let_plan *p, BandDev &bd)
             off[(size_t)m * nkr + k] = (int)std::min<int64_t>(nblk, INT32_MAX);
             nblk += li_nib(N, m) - h[(size_t)m * nkr + k];
         }
-    const size_t bytes = (size_t)nblk * LI_BLK;
+    // two copies of the blocks: rows = degrees (analysis), rows = rings (synthesis)
+    const size_t bytes = 2 * (size_t)nblk * LI_BLK;
     if (nblk > INT32_MAX || p->img_used + bytes > p->img_budget) {
         dm_free(p->mem, i0);
         return S2LET_OK;                                // no tables for this band-limit
@@ -1052,12 +1064,15 @@ int build_leg_img(s2let_plan *p, BandDev &bd)
     off_d = dev_upload(p->mem, off, p->owned, err);
     adt_d = dev_upload(p->mem, adt, p->owned, err);
     if (err) return err;
-    if (cudaMemset(img, 0, LI_BLK) != cudaSuccess) return S2LET_ERR_CUDA;
+    unsigned char *img_t = img + bytes / 2;
+    if (cudaMemset(img, 0, LI_BLK) != cudaSuccess || cudaMemset(img_t, 0, LI_BLK) != cudaSuccess)
+        return S2LET_ERR_CUDA;
     const size_t nthr = nmk * 32;
-    k_img_fill<<<(unsigned)((nthr + 127) / 128), 128>>>(N, bd.ls, bd.seed, bd.ringd, p->coefd, p->L, i0, off_d,
-                                                        img);
+    k_h16_fill<<<(unsigned)((nthr + 127) / 128), 128>>>(N, bd.ls, bd.seed, bd.ringd, p->coefd, p->L, i0, off_d,
+                                                        img, img_t);
     if (cudaGetLastError() != cudaSuccess) return S2LET_ERR_CUDA;
     bd.img = LegImg{img, i0, off_d, adt_d, nkr};
+    bd.img_t = img_t;
     bd.n_adt = (int)adt.size();
     bd.img_bytes = bytes;
     bd.has_img = true;
@@ -1277,6 +1292,12 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
     if (p->quad_gemm) {
         if (dm_alloc(p->mem, &p->G, ws) != cudaSuccess) return S2LET_ERR_ALLOC;
         p->owned.push_back(p->G);
+    }
+    if (p->tc) {
+        // column scales of the table contractions: one per (map, order row) of an L-rectangle
+        if (dm_alloc(p->mem, &p->csc, (size_t)batch * nmi(p.get(), L) * sizeof(float)) != cudaSuccess)
+            return S2LET_ERR_ALLOC;
+        p->owned.push_back(p->csc);
     }
     if (p->tc && L > LA_ST_SMEM_MAX) {
         // one block per (order, batch tile) of the analysis at band-limit L, N float4 each

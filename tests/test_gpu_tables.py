@@ -17,9 +17,10 @@ from tests.gpu_util import TOL, flm_from_dev, flm_to_dev, from_dev_map, rel_err,
 
 
 def _table_bytes_bound(N):
-    """Every degree block of every (order, ring block) plus the zero block, 4 KB each."""
+    """Every degree block of every (order, ring block) plus the zero block, 4 KB each,
+    in two copies (rows = degrees for the analysis, rows = rings for the synthesis)."""
     nkr = (N + 31) // 32
-    return 4096 * (1 + nkr * sum((N - m + 31) // 32 for m in range(N)))
+    return 2 * 4096 * (1 + nkr * sum((N - m + 31) // 32 for m in range(N)))
 
 
 @pytest.mark.parametrize("real,nb", [(True, 3), (False, 3), (True, 70), (False, 35)])
@@ -49,6 +50,31 @@ def test_tables_against_oracle_and_recurrence(L, real, nb):
     assert rel_err(g_tab[sub], ref) < TOL["tf32x3"]
     assert rel_err(g_tab, g_rec) < 2e-6
     assert tab.status() == 0 and rec.status() == 0
+
+
+@pytest.mark.parametrize("real", [True, False])
+def test_tables_column_scales(real):
+    """The FP16 operands of the table kernels are scaled per column (map, order):
+    maps of magnitude 1e-30, 1 and 1e30 and an all-zero map in one batch
+    transform like the unit map scaled (each within the tolerance of its own
+    magnitude; the zero map to exact zeros)."""
+    L = 72
+    base = inputs.random_flm(L, 700, real, "white")
+    mags = [1e-30, 1.0, 1e30]
+    flm = np.stack([base * s for s in mags] + [np.zeros_like(base)])
+    plan = Plan(L, 2, 0, batch=4, real=real, precision="tf32x3")
+    assert plan.tuning()[L]["table_anal"] and plan.tuning()[L]["table_synth"]
+    f = from_dev_map(plan.sht_inverse(flm_to_dev(flm, plan.dtype)), real)
+    f_ref = sht.inverse(base, L, real=real)
+    for b, s in enumerate(mags):
+        assert rel_err(f[b] / s, f_ref) < TOL["tf32x3"], "map %d" % b
+    assert np.all(f[3] == 0)
+    g = flm_from_dev(plan.sht_forward(to_dev_map(f, plan.dtype, real)))
+    g_ref = sht.forward(f[1], L)
+    for b, s in enumerate(mags):
+        assert rel_err(g[b] / s, g_ref) < TOL["tf32x3"], "map %d" % b
+    assert np.all(g[3] == 0)
+    assert plan.status() == 0
 
 
 @pytest.mark.parametrize("real", [True, False])
