@@ -45,7 +45,9 @@ constexpr int LH_RAW_OFF = LH_B_OFF + LH_NB * LH_STAGE;    // operand B as read:
 constexpr int LH_LIST_OFF = LH_RAW_OFF + LH_NRAW * LH_STAGE;
 constexpr int LH_BLKS_OFF = LH_LIST_OFF + LI_MAXK * 4;      // table blocks of every chunk [c][4]
 constexpr int LH_EPI_OFF = LH_BLKS_OFF + LI_MAXK * 16;      // per column pair: epilogue factor, output row
-constexpr int LH_SYNC_OFF = LH_EPI_OFF + 64 * 12;
+constexpr int LH_KF_OFF = LH_EPI_OFF + 64 * 12;             // synthesis: c_l of degrees m .. N - 1
+constexpr int LH_MAXN = 2048;                                 // largest band-limit of the tables
+constexpr int LH_SYNC_OFF = LH_KF_OFF + LH_MAXN * 4;
 struct LhSync {
     uint64_t afull[LH_NA], bfull[LH_NB], done[LH_NR], tempty[LH_NACC], fin;
     uint32_t tslot;
@@ -217,6 +219,7 @@ static __global__ void __launch_bounds__(LH_THREADS, 1) k_leg_h16(LegH16Args a)
     int4 *blks = reinterpret_cast<int4 *>(smem + LH_BLKS_OFF);
     long long *epi_row = reinterpret_cast<long long *>(smem + LH_EPI_OFF);
     float *epi_f = reinterpret_cast<float *>(smem + LH_EPI_OFF + 64 * 8);
+    float *kf_s = reinterpret_cast<float *>(smem + LH_KF_OFF);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int N = a.N;
     int m, tile, b0;
@@ -288,6 +291,8 @@ static __global__ void __launch_bounds__(LH_THREADS, 1) k_leg_h16(LegH16Args a)
             blks[c] = make_int4(bl[0], bl[1], bl[2], bl[3]);
         }
     }
+    if (!ANAL && a.kfac && warp < LH_BWARPS)
+        for (int l = m + tid; l < N; l += 32 * LH_BWARPS) kf_s[l - m] = a.kfac[l];
     if (warp < LH_BWARPS && (lane & 0x14) == 0) {
         // per column pair p (one thread each): the factor that undoes the scales and
         // the offset of its output row (-1: absent pair)
@@ -329,7 +334,7 @@ static __global__ void __launch_bounds__(LH_THREADS, 1) k_leg_h16(LegH16Args a)
         const long long rp = src_row(p);
         const float2 *row = rp >= 0 ? a.src + rp * lds : nullptr;
         const float cs = rp >= 0 ? a.csc[rp] : 0.f;
-        const float *fac = ANAL ? nullptr : a.kfac;
+        const float *fac = (ANAL || !a.kfac) ? nullptr : kf_s - m;   // c_l by degree, from shared memory
         // the parity of the first K of every chunk is that of kstart(0), so
         // whether the thread's 64 source bytes are 16-byte aligned is fixed
         const bool al16 = row && ((reinterpret_cast<uintptr_t>(row + (ANAL ? 0 : m) + 8 * kq) & 15) == 0);

@@ -1046,7 +1046,7 @@ int build_leg_img(s2let_plan *p, BandDev &bd)
         }
     // two copies of the blocks: rows = degrees (analysis), rows = rings (synthesis)
     const size_t bytes = 2 * (size_t)nblk * LI_BLK;
-    if (nblk > INT32_MAX || p->img_used + bytes > p->img_budget) {
+    if (N > LH_MAXN || nblk > INT32_MAX || p->img_used + bytes > p->img_budget) {
         dm_free(p->mem, i0);
         return S2LET_OK;                                // no tables for this band-limit
     }
