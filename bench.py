@@ -262,6 +262,8 @@ def peak_table(peaks):
         "hbm": (hbm, "GB/s", "HBM copy bandwidth hbm_gbs %.0f GB/s (%s)" % (hbm, hsrc)),
         "tf32": (bf * TF32_PER_BF16, "TFLOP/s",
                  "TF32 dense = bf16_tflops_sustained %.1f (%s) x 1.1/2.25 (nominal TF32/BF16 ratio)" % (bf, bsrc)),
+        "f16": (bf, "TFLOP/s",
+                "FP16 dense = bf16_tflops_sustained %.1f (%s) (FP16 and BF16 share one nominal rate)" % (bf, bsrc)),
         "fp32": (SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12, "TFLOP/s",
                  "derived: %d SMs x %d FP32 lanes x 2 flop/FMA x %.0f MHz (%s)" % (SM_COUNT, FP32_LANES, mhz, msrc)),
         "fp64": (SM_COUNT * FP64_FMA_PER_SM * 2 * mhz * 1e6 / 1e12, "TFLOP/s",
@@ -284,29 +286,47 @@ def legendre_tables(plan):
     return out
 
 
+def dtype_of(precision, plan=None):
+    """Arithmetic types of the path: split tensor-core plans contract in FP16 hi/lo
+    where they stream Legendre tables, in split TF32 elsewhere (the recurrence
+    kernels, the dense quadrature), with FP32 FFTs."""
+    if precision == "tf32x3":
+        if plan is not None and any(t["table_anal"] or t["table_synth"] for t in plan.tuning().values()):
+            return "f16x3+tf32x3+f32"
+        return "tf32x3+f32"
+    return {"fp32": "f32", "fp64": "f64"}[precision]
+
+
 def plan_bandlimits(plan):
     """Band-limits of the transforms in one round trip: each direction runs one
     SHT at L and one per wavelet or scaling map."""
     return [plan.L] + [n for (_, n, _, _) in plan.scales] + [plan.N_scal]
 
 
-def stage_roofline(name, st, steps, precision, pk, batch):
+def stage_roofline(name, st, steps, precision, pk, batch, variant="recurrence"):
     """Roofline record of one stage from its per-stage statistics: achieved =
     algorithmic work / device time (all launches of the stage, so the average
-    over its launches weighted by their duration)."""
+    over its launches weighted by their duration).  variant: the Legendre values
+    of a split tensor-core plan's stage ("table": the FP16 hi/lo kernels on the
+    plan's tables, measured against the FP16 peak; "recurrence": the split-TF32
+    kernels, against the TF32 peak)."""
     sec = st["ms"] / 1000.0
     if sec <= 0:
         return None
     rec = {"ms_per_step": st["ms"] / steps, "launches_per_step": st["launches"] / steps, "work": WORK.get(name, "")}
     if st["flops"] > 0:
         key = {"tf32x3": "tf32", "fp32": "fp32", "fp64": "fp64"}[precision]
+        if key == "tf32" and variant == "table":
+            key = "f16"
         peak, unit, src = pk[key]
         achieved = st["flops"] / sec / 1e12
-        rec.update(bound="tensor" if key == "tf32" else "alu", achieved=achieved, peak=peak, unit=unit,
+        tensor = key in ("tf32", "f16")
+        rec.update(bound="tensor" if tensor else "alu", achieved=achieved, peak=peak, unit=unit,
                    frac=achieved / peak, peak_source=src)
-        if key == "tf32":
+        if tensor:
             rec["executed_mma_frac"] = 3.0 * achieved / peak
-            rec["executed_note"] = "split TF32 runs 3 MMAs per algorithmic product (hi*lo + lo*hi + hi*hi)"
+            rec["executed_note"] = ("split %s runs 3 MMAs per algorithmic product (hi*hi + hi*lo + lo*hi)"
+                                    % ("FP16" if key == "f16" else "TF32"))
         # the three-term recurrence behind the products: 4 flops per lambda value; real
         # maps share one value among the batch's maps (and re/im), so per step it is
         # the contraction's count divided by the maps
@@ -325,7 +345,8 @@ def rooflines(stats, a, peaks, batch, bandlimits, tables=None):
     tables: {stage: (variant, table bytes read per step)} of the Legendre stages."""
     pk = peak_table(peaks)
     tables = tables or {}
-    recs = {k: stage_roofline(k, v, a.steps, a.precision, pk, batch) for k, v in stats.items() if v["launches"]}
+    recs = {k: stage_roofline(k, v, a.steps, a.precision, pk, batch, tables.get(k, ("recurrence", 0))[0])
+            for k, v in stats.items() if v["launches"]}
     recs = {k: v for k, v in recs.items() if v is not None}
     for k, (variant, tbytes) in tables.items():
         if k in recs:
@@ -457,7 +478,7 @@ def run_gpu(a, rank, world, local_rank):
 
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
            "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": {"fp32": "f32", "tf32x3": "tf32x3+f32", "fp64": "f64"}[a.precision], "data": "synthetic",
+           "dtype": dtype_of(a.precision, plan), "data": "synthetic",
            "config": config(a),
            "gpu_launches": launches, "roofline": roof, "legendre": legendre, "stage_rooflines": all_stages,
            "stages": stage_share, "clocks": clk}

@@ -130,9 +130,12 @@ static __global__ void k_h16_colscale(const float2 *__restrict__ src, int Lsrc, 
     if (lane == 0) csc[gw] = lh_colscale(mx);
 }
 
-// The stored blocks of both tables: one warp per (m, ring block k), lane = ring,
-// the FP64 recurrence of k_img_fill; each value scaled by 2^9 and split into
-// FP16 hi and lo (lo from the FP64 remainder).
+// The stored blocks of both tables: one warp per (m, ring block k), lane = ring.
+// Each lane runs the FP64 three-term recurrence of its ring from its seed
+// (zero below the start degree l_s), the recurrence of the FP64 kernels
+// (legendre.cuh); each value is scaled by 2^9 and split into FP16 hi and lo (lo
+// from the FP64 remainder), and written to row r of the `ta` block and to
+// column r of the `ts` block.
 static __global__ void k_h16_fill(int N, const int *__restrict__ ls, const double2 *__restrict__ seed,
                                   const RingD *__restrict__ ring, const double2 *__restrict__ coef, int ldc,
                                   const int *__restrict__ i0, const int *__restrict__ off,

@@ -122,7 +122,7 @@ struct BandDev {
     // (mr_quad; else the dense product)
     bool has_mr = false, mr_quad = true;
     MrTab mr{};
-    // TF32X3 plans: precomputed Legendre tables (legendre_img.cuh) when they fit
+    // TF32X3 plans: precomputed Legendre tables (legendre_img.cuh, legendre_h16.cuh) when they fit
     // the plan's budget, used by the tensor-core contractions (img_*; else the
     // recurrence kernels)
     bool has_img = false, img_anal = true, img_synth = true;

@@ -98,6 +98,9 @@ def test_stage_rooflines_follow_the_work_of_each_stage():
     tabs = {"leg_anal": ("table", 30e9), "leg_synth": ("table", 30e9)}
     roof3, leg3, _ = bench.rooflines(stats, a, peaks, 64, [2048, 8, 4], tabs)
     assert roof3["legendre_values"] == "table"
+    # the table kernels contract FP16 hi/lo parts: measured against the FP16 (= BF16) peak
+    assert roof3["peak"] == pytest.approx(1800.0) and roof3["frac"] == pytest.approx(200.0 / 1800.0)
+    assert roof3["executed_mma_frac"] == pytest.approx(3 * 200.0 / 1800.0) and "FP16" in roof3["peak_source"]
     assert roof3["table_gbs"] == pytest.approx(30e9 / 0.025 / 1e9)
     assert roof3["table_frac_of_hbm"] == pytest.approx(1200.0 / 6000.0)
     want = bench.TRAFFIC.get(("leg_anal", "table"))
