@@ -53,6 +53,17 @@ WORK = {
 # or variant missing here has no capture of its current kernel, and its traffic
 # is reported as null
 TRAFFIC = {
+    # k_leg_h16<false> (synthesis on the FP16 tables), full-band-limit launch at
+    # L = 1024, 64 maps: 2461.2 + 478.0 MB, profiles/leg_h16_L1024_b64.md; scaled
+    # as its table part (one table copy) plus the rest by N^2 x maps
+    ("leg_synth", "table"): {
+        "bytes_at": (1024, 64, 2939.1e6),
+        "source": "ncu dram read+write of k_leg_h16 (synthesis) at L=1024 x 64 maps (2939.1 MB per launch): "
+                  "the table copy it streams scaled as the table, the rest by N^2 x maps"},
+    ("leg_anal", "table"): {
+        "bytes_at": (1024, 64, 2789.4e6),
+        "source": "ncu dram read+write of k_leg_h16 (analysis) at L=1024 x 64 maps (2789.4 MB per launch): "
+                  "the table copy it streams scaled as the table, the rest by N^2 x maps"},
     # k_leg_anal_tc, full-band-limit launch at L = 1024, 64 maps: 772.0 + 255.5 MB
     # (G and the recurrence tables read, f_lm written), profiles/quad_anal_tc_L1024_b64_tf32x3.md
     ("leg_anal", "recurrence"): {
@@ -274,15 +285,18 @@ def peak_table(peaks):
 def legendre_tables(plan):
     """Per Legendre stage: which values it contracts ("table": the plan's stored
     Legendre tables, "recurrence": computed in the kernel) at the full band-limit,
-    and the table bytes its launches of one round trip read."""
+    the table bytes its launches of one round trip read, and the bytes one launch
+    reads at each band-limit (one of the two copies the plan stores: rows =
+    degrees for the analysis, rows = rings for the synthesis; 0 where the stage
+    runs the recurrence)."""
     if plan.precision != "tf32x3":
         return {}
     tun = plan.tuning()
     out = {}
     for stage, key in (("leg_anal", "table_anal"), ("leg_synth", "table_synth")):
         variant = "table" if tun[plan.L][key] else "recurrence"
-        tbytes = sum(plan.table_bytes(n) for n in plan_bandlimits(plan) if tun[n][key])
-        out[stage] = (variant, tbytes)
+        per = {n: (plan.table_bytes(n) // 2 if tun[n][key] else 0) for n in set(plan_bandlimits(plan))}
+        out[stage] = (variant, sum(per[n] for n in plan_bandlimits(plan)), per)
     return out
 
 
@@ -347,8 +361,9 @@ def rooflines(stats, a, peaks, batch, bandlimits, tables=None):
     tables = tables or {}
     recs = {k: stage_roofline(k, v, a.steps, a.precision, pk, batch, tables.get(k, ("recurrence", 0))[0])
             for k, v in stats.items() if v["launches"]}
+    tables = {k: (t + ({},))[:3] for k, t in tables.items()}
     recs = {k: v for k, v in recs.items() if v is not None}
-    for k, (variant, tbytes) in tables.items():
+    for k, (variant, tbytes, _) in tables.items():
         if k in recs:
             recs[k]["legendre_values"] = variant
             if tbytes:
@@ -359,9 +374,16 @@ def rooflines(stats, a, peaks, batch, bandlimits, tables=None):
     dom = max(recs, key=lambda k: recs[k]["ms_per_step"])
     roof = dict(recs[dom])
     roof["kernel"] = dom
-    variant = tables.get(dom, ("recurrence", 0))[0]
+    variant, _, per = tables.get(dom, ("recurrence", 0, {}))
     tr = TRAFFIC.get((dom, variant)) if a.precision == "tf32x3" else None
-    if tr:
+    if tr and variant == "table" and tr["bytes_at"][0] in per:
+        # table kernels: the table part of a launch is the copy it streams (grows as
+        # the table, ~N^3); the rest (data read, results written) as N^2 x maps
+        n0, b0, by = tr["bytes_at"]
+        rest = by - per[n0]
+        roof["traffic"] = sum(per.get(n, 0) + rest * (n / n0) ** 2 * batch / b0 for n in bandlimits)
+        roof["traffic_note"] = tr["source"]
+    elif tr and variant != "table":
         n0, b0, by = tr["bytes_at"]
         # one launch of the stage per transform direction and band-limit of the round trip
         roof["traffic"] = sum(by * (n / n0) ** 2 * batch / b0 for n in bandlimits)

@@ -95,7 +95,8 @@ def test_stage_rooflines_follow_the_work_of_each_stage():
     assert roof2["frac"] == pytest.approx(60e9 / 0.090 / 1e9 / 6000.0)
     # Legendre stages on the plan's tables: the table bytes they stream per step
     # against HBM; DRAM traffic only from a capture of that kernel variant
-    tabs = {"leg_anal": ("table", 30e9), "leg_synth": ("table", 30e9)}
+    per = {2048: 9e9, 8: 1e6, 4: 0}
+    tabs = {"leg_anal": ("table", 30e9, per), "leg_synth": ("table", 30e9, per)}
     roof3, leg3, _ = bench.rooflines(stats, a, peaks, 64, [2048, 8, 4], tabs)
     assert roof3["legendre_values"] == "table"
     # the table kernels contract FP16 hi/lo parts: measured against the FP16 (= BF16) peak
@@ -103,5 +104,14 @@ def test_stage_rooflines_follow_the_work_of_each_stage():
     assert roof3["executed_mma_frac"] == pytest.approx(3 * 200.0 / 1800.0) and "FP16" in roof3["peak_source"]
     assert roof3["table_gbs"] == pytest.approx(30e9 / 0.025 / 1e9)
     assert roof3["table_frac_of_hbm"] == pytest.approx(1200.0 / 6000.0)
-    want = bench.TRAFFIC.get(("leg_anal", "table"))
-    assert (roof3["traffic"] is None) == (want is None)
+    # traffic of the table kernels: the table copy per launch plus the rest of the
+    # captured launch scaled by N^2 x maps; no capture at the capture's band-limit -> None
+    n0, b0, by = bench.TRAFFIC[("leg_anal", "table")]["bytes_at"]
+    per1 = dict(per)
+    per1[n0] = 2e9
+    roof4, _, _ = bench.rooflines(stats, a, peaks, 64, [2048, 8, 4],
+                                  {"leg_anal": ("table", 30e9, per1), "leg_synth": ("table", 30e9, per1)})
+    rest = by - 2e9
+    want = sum(per1[n] + rest * (n / n0) ** 2 * 64 / b0 for n in (2048, 8, 4))
+    assert roof4["traffic"] == pytest.approx(want)
+    assert roof3["traffic"] is None
