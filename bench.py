@@ -303,9 +303,11 @@ def legendre_tables(plan):
 def dtype_of(precision, plan=None):
     """Arithmetic types of the path: split tensor-core plans contract in FP16 hi/lo
     where they stream Legendre tables, in split TF32 elsewhere (the recurrence
-    kernels, the dense quadrature), with FP32 FFTs."""
+    kernels, the dense quadrature), with FP32 FFTs.  Without a plan to ask (the
+    batch and gradient workloads), the types of a default plan, which stores the
+    tables of band-limits up to 2048."""
     if precision == "tf32x3":
-        if plan is not None and any(t["table_anal"] or t["table_synth"] for t in plan.tuning().values()):
+        if plan is None or any(t["table_anal"] or t["table_synth"] for t in plan.tuning().values()):
             return "f16x3+tf32x3+f32"
         return "tf32x3+f32"
     return {"fp32": "f32", "fp64": "f64"}[precision]
@@ -671,7 +673,7 @@ def run_batch256(a, rank, world, local_rank):
     res = {"metric": "uneven-batch wavelet round-trips/s (256 complex maps, one graph launch per round trip)",
            "value": world * 256 * a.steps / (ms / 1000.0), "unit": UNIT, "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": {"fp32": "f32", "tf32x3": "tf32x3+f32", "fp64": "f64"}[prec],
+           "vs_baseline": None, "dtype": dtype_of(prec),
            "data": "synthetic",
            "config": {"workload": "256 complex maps, L histogram %s, B in {2,3}, J_min=1, multiresolution" % hist,
                       "groups": bp.n_groups, "graph_launches_per_step": 1},
@@ -742,7 +744,7 @@ def run_grad(a, rank, world, local_rank):
     res = {"metric": "loss + gradient evaluations of sum_j 2^-j ||W^j||^2 (maps/s), L=1024 x 16 real maps",
            "value": world * first["maps_per_s"], "unit": "maps/s", "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": first["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": {"fp32": "f32", "tf32x3": "tf32x3+f32", "fp64": "f64"}[a.precision],
+           "vs_baseline": None, "dtype": dtype_of(a.precision),
            "data": "synthetic",
            "config": {"workload": "loss + gradient: L=1024 x 16 real maps (adjoint kernel and per-scale "
                                   "recomputation), L=4096 x 1 map (per-scale recomputation); B=2, J_min=2, "
