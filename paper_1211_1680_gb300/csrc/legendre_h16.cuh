@@ -49,7 +49,7 @@ constexpr int LH_KF_OFF = LH_EPI_OFF + 64 * 12;             // synthesis: c_l of
 constexpr int LH_MAXN = 2048;                                 // largest band-limit of the tables
 constexpr int LH_SYNC_OFF = LH_KF_OFF + LH_MAXN * 4;
 struct LhSync {
-    uint64_t afull[LH_NA], bfull[LH_NB], done[LH_NR], tempty[LH_NACC], fin;
+    uint64_t afull[LH_NA], bfull[LH_NB], done[LH_NR], tempty[LH_NACC], fin, mfull;
     uint32_t tslot;
     int abort, nk, ibase;
 };
@@ -241,7 +241,11 @@ static __global__ void __launch_bounds__(LH_THREADS, 1) k_leg_h16(LegH16Args a)
     volatile int *abort = &sy.abort;
     auto par = [](int c, int n) -> uint32_t { return (uint32_t)((c / n) & 1); };
 
-    if (tid == 0) {
+    if (warp == LH_MMA_WARP) {
+        tc::tmem_alloc(&sy.tslot, LT_TMEM_COLS);
+    } else if (warp == LH_COPY_WARP && lane == 0) {
+        // barriers, then the item's chunk list (built at plan creation) by bulk copies,
+        // so that the first table copies can go out as soon as it lands
 #pragma unroll
         for (int i = 0; i < LH_NA; ++i) tc::mbar_init(&sy.afull[i], 1);
 #pragma unroll
@@ -251,47 +255,17 @@ static __global__ void __launch_bounds__(LH_THREADS, 1) k_leg_h16(LegH16Args a)
 #pragma unroll
         for (int i = 0; i < LH_NACC; ++i) tc::mbar_init(&sy.tempty[i], LH_BWARPS);
         tc::mbar_init(&sy.fin, 1);
+        tc::mbar_init(&sy.mfull, 1);
         sy.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == LH_MMA_WARP) {
-        tc::tmem_alloc(&sy.tslot, LT_TMEM_COLS);
-    } else if (warp == LH_COPY_WARP) {
-        // the chunk sequence, the same for every role
-        if constexpr (ANAL) {
-            // ring chunks with a stored block among degree blocks 4 tile .. 4 tile + 3
-            int n = 0;
-            for (int k0 = 0; k0 < a.T.nkr; k0 += 32) {
-                const int k = k0 + lane;
-                const bool act = k < a.T.nkr && a.T.i0[m * a.T.nkr + k] <= 4 * tile + 3;
-                const unsigned bal = __ballot_sync(0xffffffffu, act);
-                if (act) klist[n + __popc(bal & ((1u << lane) - 1u))] = k;
-                n += __popc(bal);
-            }
-            if (lane == 0) {
-                sy.nk = n;
-                sy.ibase = 0;
-            }
-        } else {
-            // degree blocks from the smallest i0 of the tile's ring blocks
-            int v = nib;
-            if (lane < 4 && 4 * tile + lane < a.T.nkr) v = a.T.i0[m * a.T.nkr + 4 * tile + lane];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-            if (lane == 0) {
-                sy.ibase = v;
-                sy.nk = nib - v;
-            }
-        }
-        // the four table blocks of every chunk, looked up once
-        __syncwarp();
-        const int n = sy.nk, ib = sy.ibase;
-        for (int c = lane; c < n; c += 32) {
-            int bl[4];
-#pragma unroll
-            for (int w = 0; w < 4; ++w)
-                bl[w] = ANAL ? li_block(a.T, nib, m, 4 * tile + w, klist[c]) : li_block(a.T, nib, m, ib + c, 4 * tile + w);
-            blks[c] = make_int4(bl[0], bl[1], bl[2], bl[3]);
+        const int4 md = ANAL ? a.T.ameta[blockIdx.x] : a.T.smeta[(size_t)m * ((N + 127) / 128) + tile];
+        sy.nk = md.y;
+        sy.ibase = ANAL ? 0 : md.z;
+        const uint32_t nb = (uint32_t)md.y * 16u, nl = ANAL ? (uint32_t)((md.y + 3) & ~3) * 4u : 0u;
+        tc::mbar_arrive_expect_tx(&sy.mfull, nb + nl);
+        if (md.y > 0) {
+            tc::bulk_g2s(blks, (ANAL ? a.T.ablk : a.T.sblk) + md.x, nb, &sy.mfull);
+            if (ANAL) tc::bulk_g2s(klist, a.T.ack + md.z, nl, &sy.mfull);
         }
     }
     if (!ANAL && a.kfac && warp < LH_BWARPS)
@@ -415,6 +389,7 @@ static __global__ void __launch_bounds__(LH_THREADS, 1) k_leg_h16(LegH16Args a)
             *reinterpret_cast<uint4 *>(Bst + lh_sw(n1, 64 + 16 * kq)) = li;
         };
         int drained = 0;
+        if (ANAL) lt_spin(&sy.mfull, 0, abort);       // the chunks' ring blocks (klist) have landed
         for (int c = 0; c < LH_NRAW - 1; ++c) issue(c);
         // output index of this thread in the epilogue (TMEM lane = degree or ring)
         const int oidx = ANAL ? m + 128 * tile + 32 * (warp & 3) + lane : 128 * tile + 32 * (warp & 3) + lane;
@@ -471,6 +446,7 @@ static __global__ void __launch_bounds__(LH_THREADS, 1) k_leg_h16(LegH16Args a)
         // ------------------------------------------------ operand A: four table blocks per chunk
         if (lane == 0) {
             int issued = 0;
+            lt_spin(&sy.mfull, 0, abort);              // the chunks' table blocks (blks) have landed
             for (int c = 0; c < nk; ++c) {
                 if (c >= LH_NA && !lt_spin(&sy.done[(c - LH_NA) % LH_NR], par(c - LH_NA, LH_NR), abort)) break;
                 if (*abort) break;
@@ -485,6 +461,7 @@ static __global__ void __launch_bounds__(LH_THREADS, 1) k_leg_h16(LegH16Args a)
                 issued = c + 1;
             }
             // no copy in flight when the block ends (only possible after an abort)
+            tc::mbar_wait(&sy.mfull, 0, 1u << 22);
             for (int c = issued - LH_NA > 0 ? issued - LH_NA : 0; c < issued; ++c)
                 tc::mbar_wait(&sy.afull[c % LH_NA], par(c, LH_NA), 1u << 22);
         }

@@ -27,6 +27,14 @@ struct LegImg {
     const int *off;                                 // [m][k] block index of degree block i0
     const int2 *adt;                                // analysis blocks: (m, degree tile)
     int nkr;                                        // ring blocks: ceil(N / 32)
+    // chunk lists of every item, built once per plan:
+    //   ameta[adt item] = (first chunk, chunks, first entry of ack, 0), ablk[chunk] = the
+    //   four blocks (degree blocks 4 tile .. 4 tile + 3 of ring block ack[chunk]);
+    //   smeta[m * ceil(N / 128) + ring tile] = (first chunk, chunks, first degree block
+    //   ibase, 0), sblk[chunk] = the four blocks (ring blocks 4 tile .. 4 tile + 3 of
+    //   degree block ibase + chunk)
+    const int4 *ameta, *ablk, *smeta, *sblk;
+    const int *ack;                                 // each item's list starts at a multiple of 4
 };
 __host__ __device__ constexpr int li_nib(int N, int m) { return (N - m + 31) / 32; }
 

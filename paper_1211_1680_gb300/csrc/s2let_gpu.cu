@@ -1053,6 +1053,41 @@ int build_leg_img(s2let_plan *p, BandDev &bd)
     std::vector<int2> adt;
     for (int m = 0; m < N; ++m)
         for (int dt = 0; dt < (N - m + 127) / 128; ++dt) adt.push_back(make_int2(m, dt));
+    // the chunk list of every item: the four table blocks of each chunk and, for the
+    // analysis, its ring block (each item's ring blocks start at a multiple of 4 entries)
+    auto blk_of = [&](int m, int i, int k) -> int {
+        if (k >= nkr || i >= li_nib(N, m)) return 0;
+        const int b = h[(size_t)m * nkr + k];
+        return i >= b ? off[(size_t)m * nkr + k] + (i - b) : 0;
+    };
+    std::vector<int4> ameta, ablk, smeta, sblk;
+    std::vector<int> ack;
+    for (const int2 &md : adt) {
+        const int m = md.x, t4 = 4 * md.y;
+        while (ack.size() % 4) ack.push_back(0);
+        const int o = (int)ablk.size(), oc = (int)ack.size();
+        for (int k = 0; k < nkr; ++k)
+            if (h[(size_t)m * nkr + k] <= t4 + 3) {
+                ack.push_back(k);
+                ablk.push_back(make_int4(blk_of(m, t4, k), blk_of(m, t4 + 1, k), blk_of(m, t4 + 2, k),
+                                         blk_of(m, t4 + 3, k)));
+            }
+        ameta.push_back(make_int4(o, (int)ablk.size() - o, oc, 0));
+    }
+    for (int q = 0; q < 4; ++q) ack.push_back(0);      // a list's copy rounds up to 4 entries
+    const int nrt = (N + 127) / 128;
+    for (int m = 0; m < N; ++m)
+        for (int rt = 0; rt < nrt; ++rt) {
+            const int nib = li_nib(N, m);
+            int v = nib;
+            for (int w = 0; w < 4; ++w)
+                if (4 * rt + w < nkr) v = std::min(v, h[(size_t)m * nkr + 4 * rt + w]);
+            const int o = (int)sblk.size();
+            for (int i = v; i < nib; ++i)
+                sblk.push_back(make_int4(blk_of(m, i, 4 * rt), blk_of(m, i, 4 * rt + 1), blk_of(m, i, 4 * rt + 2),
+                                         blk_of(m, i, 4 * rt + 3)));
+            smeta.push_back(make_int4(o, nib - v, v, 0));
+        }
     if (dm_alloc(p->mem, &img, bytes) != cudaSuccess) {
         cudaGetLastError();
         dm_free(p->mem, i0);
@@ -1063,6 +1098,9 @@ int build_leg_img(s2let_plan *p, BandDev &bd)
     int err = S2LET_OK;
     off_d = dev_upload(p->mem, off, p->owned, err);
     adt_d = dev_upload(p->mem, adt, p->owned, err);
+    const int4 *ameta_d = dev_upload(p->mem, ameta, p->owned, err), *ablk_d = dev_upload(p->mem, ablk, p->owned, err);
+    const int4 *smeta_d = dev_upload(p->mem, smeta, p->owned, err), *sblk_d = dev_upload(p->mem, sblk, p->owned, err);
+    const int *ack_d = dev_upload(p->mem, ack, p->owned, err);
     if (err) return err;
     unsigned char *img_t = img + bytes / 2;
     if (cudaMemset(img, 0, LI_BLK) != cudaSuccess || cudaMemset(img_t, 0, LI_BLK) != cudaSuccess)
@@ -1071,7 +1109,7 @@ int build_leg_img(s2let_plan *p, BandDev &bd)
     k_h16_fill<<<(unsigned)((nthr + 127) / 128), 128>>>(N, bd.ls, bd.seed, bd.ringd, p->coefd, p->L, i0, off_d,
                                                         img, img_t);
     if (cudaGetLastError() != cudaSuccess) return S2LET_ERR_CUDA;
-    bd.img = LegImg{img, i0, off_d, adt_d, nkr};
+    bd.img = LegImg{img, i0, off_d, adt_d, nkr, ameta_d, ablk_d, smeta_d, sblk_d, ack_d};
     bd.img_t = img_t;
     bd.n_adt = (int)adt.size();
     bd.img_bytes = bytes;
