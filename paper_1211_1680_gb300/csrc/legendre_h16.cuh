@@ -135,10 +135,15 @@ static __global__ void k_h16_colscale(const float2 *__restrict__ src, int Lsrc, 
 // (zero below the start degree l_s), the recurrence of the FP64 kernels
 // (legendre.cuh); each value is scaled by 2^9 and split into FP16 hi and lo (lo
 // from the FP64 remainder), and written to row r of the `ta` block and to
-// column r of the `ts` block.
+// column r of the `ts` block.  `ta` holds the blocks of (m, k) in degree order
+// (off[m][k] + i - i0[m][k]); `ts` holds those of (m, i) in ring-block order,
+// soff[m][i] + k - klo[m][i], so that the ring blocks of one degree block are
+// adjacent (klo: the first ring block with a stored block i; rows [m][i] of
+// stride ceil(N / 32)).
 static __global__ void k_h16_fill(int N, const int *__restrict__ ls, const double2 *__restrict__ seed,
                                   const RingD *__restrict__ ring, const double2 *__restrict__ coef, int ldc,
                                   const int *__restrict__ i0, const int *__restrict__ off,
+                                  const int *__restrict__ soff, const int *__restrict__ klo,
                                   unsigned char *__restrict__ ta, unsigned char *__restrict__ ts)
 {
     const int nkr = (N + 31) / 32;
@@ -160,6 +165,7 @@ static __global__ void k_h16_fill(int N, const int *__restrict__ ls, const doubl
     const double2 *cm = coef + (size_t)m * ldc;
     size_t blk = (size_t)off[gw] * LI_BLK;
     for (int i = ib; i < nib; ++i, blk += LI_BLK) {
+        const size_t tblk = (size_t)(soff[m * nkr + i] + k - klo[m * nkr + i]) * LI_BLK;
         for (int r = 0; r < 32; ++r) {
             const int l = m + 32 * i + r;
             double v = 0.0;
@@ -173,8 +179,8 @@ static __global__ void k_h16_fill(int N, const int *__restrict__ ls, const doubl
             const __half lo = __float2half_rn((float)(x - (double)__half2float(h)));
             *reinterpret_cast<__half *>(ta + blk + lh_sw(r, 2 * lane)) = h;
             *reinterpret_cast<__half *>(ta + blk + lh_sw(r, 64 + 2 * lane)) = lo;
-            *reinterpret_cast<__half *>(ts + blk + lh_sw(lane, 2 * r)) = h;
-            *reinterpret_cast<__half *>(ts + blk + lh_sw(lane, 64 + 2 * r)) = lo;
+            *reinterpret_cast<__half *>(ts + tblk + lh_sw(lane, 2 * r)) = h;
+            *reinterpret_cast<__half *>(ts + tblk + lh_sw(lane, 64 + 2 * r)) = lo;
         }
     }
 }
@@ -454,10 +460,15 @@ static __global__ void __launch_bounds__(LH_THREADS, 1) k_leg_h16(LegH16Args a)
                 unsigned char *dstA = smem + s * LH_STAGE;
                 const int4 bl = blks[c];
                 tc::mbar_arrive_expect_tx(&sy.afull[s], LH_STAGE);
-                tc::bulk_g2s(dstA, a.tab + (size_t)bl.x * LI_BLK, LI_BLK, &sy.afull[s]);
-                tc::bulk_g2s(dstA + LI_BLK, a.tab + (size_t)bl.y * LI_BLK, LI_BLK, &sy.afull[s]);
-                tc::bulk_g2s(dstA + 2 * LI_BLK, a.tab + (size_t)bl.z * LI_BLK, LI_BLK, &sy.afull[s]);
-                tc::bulk_g2s(dstA + 3 * LI_BLK, a.tab + (size_t)bl.w * LI_BLK, LI_BLK, &sy.afull[s]);
+                if (bl.y == bl.x + 1 && bl.z == bl.x + 2 && bl.w == bl.x + 3) {
+                    // four adjacent blocks: one copy
+                    tc::bulk_g2s(dstA, a.tab + (size_t)bl.x * LI_BLK, LH_STAGE, &sy.afull[s]);
+                } else {
+                    tc::bulk_g2s(dstA, a.tab + (size_t)bl.x * LI_BLK, LI_BLK, &sy.afull[s]);
+                    tc::bulk_g2s(dstA + LI_BLK, a.tab + (size_t)bl.y * LI_BLK, LI_BLK, &sy.afull[s]);
+                    tc::bulk_g2s(dstA + 2 * LI_BLK, a.tab + (size_t)bl.z * LI_BLK, LI_BLK, &sy.afull[s]);
+                    tc::bulk_g2s(dstA + 3 * LI_BLK, a.tab + (size_t)bl.w * LI_BLK, LI_BLK, &sy.afull[s]);
+                }
                 issued = c + 1;
             }
             // no copy in flight when the block ends (only possible after an abort)

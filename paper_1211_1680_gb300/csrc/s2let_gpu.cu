@@ -1044,9 +1044,26 @@ int build_leg_img(s2let_plan *p, BandDev &bd)
             off[(size_t)m * nkr + k] = (int)std::min<int64_t>(nblk, INT32_MAX);
             nblk += li_nib(N, m) - h[(size_t)m * nkr + k];
         }
+    // the synthesis copy: for each (m, degree block i), the ring blocks klo .. khi of
+    // the blocks stored at i, adjacent (a gap, if the stored ring blocks of i were
+    // not contiguous, holds zeros)
+    std::vector<int> soff((size_t)N * nkr, 0), klo((size_t)N * nkr, 0);
+    int64_t nblk_s = 1;                                 // block 0: zeros
+    for (int m = 0; m < N; ++m)
+        for (int i = 0; i < li_nib(N, m); ++i) {
+            int lo = nkr, hi = -1;
+            for (int k = 0; k < nkr; ++k)
+                if (h[(size_t)m * nkr + k] <= i) {
+                    lo = std::min(lo, k);
+                    hi = k;
+                }
+            soff[(size_t)m * nkr + i] = (int)std::min<int64_t>(nblk_s, INT32_MAX);
+            klo[(size_t)m * nkr + i] = lo;
+            if (hi >= lo) nblk_s += hi - lo + 1;
+        }
     // two copies of the blocks: rows = degrees (analysis), rows = rings (synthesis)
-    const size_t bytes = 2 * (size_t)nblk * LI_BLK;
-    if (N > LH_MAXN || nblk > INT32_MAX || p->img_used + bytes > p->img_budget) {
+    const size_t bytes = ((size_t)nblk + (size_t)nblk_s) * LI_BLK;
+    if (N > LH_MAXN || nblk > INT32_MAX || nblk_s > INT32_MAX || p->img_used + bytes > p->img_budget) {
         dm_free(p->mem, i0);
         return S2LET_OK;                                // no tables for this band-limit
     }
@@ -1083,9 +1100,15 @@ int build_leg_img(s2let_plan *p, BandDev &bd)
             for (int w = 0; w < 4; ++w)
                 if (4 * rt + w < nkr) v = std::min(v, h[(size_t)m * nkr + 4 * rt + w]);
             const int o = (int)sblk.size();
-            for (int i = v; i < nib; ++i)
-                sblk.push_back(make_int4(blk_of(m, i, 4 * rt), blk_of(m, i, 4 * rt + 1), blk_of(m, i, 4 * rt + 2),
-                                         blk_of(m, i, 4 * rt + 3)));
+            for (int i = v; i < nib; ++i) {
+                int b[4];
+                for (int w = 0; w < 4; ++w) {
+                    const int k = 4 * rt + w;
+                    const bool st = k < nkr && h[(size_t)m * nkr + k] <= i;
+                    b[w] = st ? soff[(size_t)m * nkr + i] + k - klo[(size_t)m * nkr + i] : 0;
+                }
+                sblk.push_back(make_int4(b[0], b[1], b[2], b[3]));
+            }
             smeta.push_back(make_int4(o, nib - v, v, 0));
         }
     if (dm_alloc(p->mem, &img, bytes) != cudaSuccess) {
@@ -1101,13 +1124,14 @@ int build_leg_img(s2let_plan *p, BandDev &bd)
     const int4 *ameta_d = dev_upload(p->mem, ameta, p->owned, err), *ablk_d = dev_upload(p->mem, ablk, p->owned, err);
     const int4 *smeta_d = dev_upload(p->mem, smeta, p->owned, err), *sblk_d = dev_upload(p->mem, sblk, p->owned, err);
     const int *ack_d = dev_upload(p->mem, ack, p->owned, err);
+    const int *soff_d = dev_upload(p->mem, soff, p->owned, err), *klo_d = dev_upload(p->mem, klo, p->owned, err);
     if (err) return err;
-    unsigned char *img_t = img + bytes / 2;
-    if (cudaMemset(img, 0, LI_BLK) != cudaSuccess || cudaMemset(img_t, 0, LI_BLK) != cudaSuccess)
+    unsigned char *img_t = img + (size_t)nblk * LI_BLK;
+    if (cudaMemset(img, 0, LI_BLK) != cudaSuccess || cudaMemset(img_t, 0, (size_t)nblk_s * LI_BLK) != cudaSuccess)
         return S2LET_ERR_CUDA;
     const size_t nthr = nmk * 32;
     k_h16_fill<<<(unsigned)((nthr + 127) / 128), 128>>>(N, bd.ls, bd.seed, bd.ringd, p->coefd, p->L, i0, off_d,
-                                                        img, img_t);
+                                                        soff_d, klo_d, img, img_t);
     if (cudaGetLastError() != cudaSuccess) return S2LET_ERR_CUDA;
     bd.img = LegImg{img, i0, off_d, adt_d, nkr, ameta_d, ablk_d, smeta_d, sblk_d, ack_d};
     bd.img_t = img_t;
