@@ -513,3 +513,340 @@ static __global__ void __launch_bounds__(LH_THREADS, 1) k_leg_h16(LegH16Args a)
 }
 
 }  // namespace s2g
+
+namespace s2g {
+
+// ---------------------------------------------------------------- two kernel sets
+// k_leg_h16s2: the synthesis of two maps that share the band-limit N and the
+// coefficients f_lm and differ in the kernel factors (two wavelet scales whose
+// band-limits are both capped at L):
+//   F^s_m(theta_t) = scale sum_l lambda_lm(theta_t) c^s_l f_lm,  s = 0, 1.
+// One stream of the table feeds both: per chunk the four table blocks are
+// copied once and the MMAs run for each set against its own operand B (the
+// same raw f_lm rows, scaled by c^s_l and the set's column scale).  Tensor
+// memory holds, per set, one accumulator (four K chunks) and the running sum
+// (columns 256 s and 256 s + 128): the drain warps add the accumulator into the
+// running sum with FP32 adds (the same sums the single-set kernel keeps in
+// registers, for which two sets leave too few registers).
+constexpr int LH2_NA = 5, LH2_NB = 2, LH2_NRAW = 3;
+constexpr int LH2_B_OFF = LH2_NA * LH_STAGE;                   // stage s: set 0, set 1 (16 KB each)
+constexpr int LH2_RAW_OFF = LH2_B_OFF + LH2_NB * 2 * LH_STAGE;
+constexpr int LH2_BLKS_OFF = LH2_RAW_OFF + LH2_NRAW * LH_STAGE;
+constexpr int LH2_EPI_OFF = LH2_BLKS_OFF + LI_MAXK * 16;       // output row [64], factors [2][64]
+constexpr int LH2_KF_OFF = LH2_EPI_OFF + 64 * 8 + 2 * 64 * 4;  // c^s_l of degrees m .. N - 1 [2][LH_MAXN]
+constexpr int LH2_SYNC_OFF = LH2_KF_OFF + 2 * LH_MAXN * 4;
+struct Lh2Sync {
+    uint64_t afull[LH2_NA], bfull[LH2_NB], done[LH_NR], tempty, fin, mfull;
+    uint32_t tslot;
+    int abort, nk, ibase;
+};
+static_assert(sizeof(Lh2Sync) <= LH_SYNC_BYTES, "sync block");
+static_assert(LH2_NA < LH_NR && LH2_NB < LH_D, "barrier ring: a drain follows its group's last chunk");
+__host__ __device__ constexpr size_t leg_h16s2_smem() { return (size_t)LH2_SYNC_OFF + LH_SYNC_BYTES + 1024; }
+static_assert(leg_h16s2_smem() <= 227 * 1024, "shared memory");
+
+struct LegH16Args2 {
+    const float2 *src;       // f [b][mi][l] (rectangle Lsrc)
+    int Lsrc;
+    const float *kfac[2];    // per-degree factors of the two sets
+    float scale;
+    float2 *dst[2];          // F^s [b][mi][t] (band-limit N)
+    int N, B;
+    LegImg T;
+    const unsigned char *tab;   // ts
+    const float *csc[2];     // column scales of c^s_l f_lm [b][mi]
+    int *err;
+};
+
+// 16 consecutive 32-bit columns of this thread's TMEM lane (two x8 stores)
+__device__ __forceinline__ void lh_tmem_st16(uint32_t taddr, const float (&v)[16])
+{
+    tc::tmem_st8(taddr, *reinterpret_cast<const float(*)[8]>(v));
+    tc::tmem_st8(taddr + 8, *reinterpret_cast<const float(*)[8]>(v + 8));
+}
+
+template <bool CPLX>
+static __global__ void __launch_bounds__(LH_THREADS, 1) k_leg_h16s2(LegH16Args2 a)
+{
+    using Cols = LegCols<CPLX>;
+    constexpr int BT = Cols::BT;
+    extern __shared__ __align__(1024) unsigned char smem_dyn[];
+    unsigned char *smem = lt_align(smem_dyn);
+    Lh2Sync &sy = *reinterpret_cast<Lh2Sync *>(smem + LH2_SYNC_OFF);
+    int4 *blks = reinterpret_cast<int4 *>(smem + LH2_BLKS_OFF);
+    long long *epi_row = reinterpret_cast<long long *>(smem + LH2_EPI_OFF);
+    float *epi_f = reinterpret_cast<float *>(smem + LH2_EPI_OFF + 64 * 8);       // [2][64]
+    float *kf_s = reinterpret_cast<float *>(smem + LH2_KF_OFF);                  // [2][LH_MAXN]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N = a.N;
+    const int tile = blockIdx.x, m = blockIdx.y, b0 = blockIdx.z * BT;
+    const bool two = CPLX && m > 0;
+    volatile int *abort = &sy.abort;
+    auto par = [](int c, int n) -> uint32_t { return (uint32_t)((c / n) & 1); };
+
+    if (warp == LH_MMA_WARP) {
+        tc::tmem_alloc(&sy.tslot, LT_TMEM_COLS);
+    } else if (warp == LH_COPY_WARP && lane == 0) {
+#pragma unroll
+        for (int i = 0; i < LH2_NA; ++i) tc::mbar_init(&sy.afull[i], 1);
+#pragma unroll
+        for (int i = 0; i < LH2_NB; ++i) tc::mbar_init(&sy.bfull[i], LH_BWARPS);
+#pragma unroll
+        for (int i = 0; i < LH_NR; ++i) tc::mbar_init(&sy.done[i], 1);
+        tc::mbar_init(&sy.tempty, LH_BWARPS);
+        tc::mbar_init(&sy.fin, 1);
+        tc::mbar_init(&sy.mfull, 1);
+        sy.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const int4 md = a.T.smeta[(size_t)m * ((N + 127) / 128) + tile];
+        sy.nk = md.y;
+        sy.ibase = md.z;
+        const uint32_t nb = (uint32_t)md.y * 16u;
+        tc::mbar_arrive_expect_tx(&sy.mfull, nb);
+        if (md.y > 0) tc::bulk_g2s(blks, a.T.sblk + md.x, nb, &sy.mfull);
+    }
+    if (warp < LH_BWARPS)
+        for (int l = m + tid; l < N; l += 32 * LH_BWARPS) {
+            kf_s[l - m] = a.kfac[0] ? a.kfac[0][l] : 1.f;
+            kf_s[LH_MAXN + l - m] = a.kfac[1] ? a.kfac[1][l] : 1.f;
+        }
+    const int nmi_src = CPLX ? 2 * a.Lsrc - 1 : a.Lsrc;
+    const int moff = a.Lsrc - 1;
+    if (warp < LH_BWARPS && (lane & 0x14) == 0) {
+        const int p = 8 * warp + (lane & 3) + 4 * ((lane >> 3) & 1);
+        const int sg = p / BT, b = p % BT;
+        const bool live = b0 + b < a.B && (sg == 0 || two);
+        const int mi = sg == 0 ? (CPLX ? m + moff : m) : (-m + moff);
+        const int nmi_dst = CPLX ? 2 * N - 1 : N;
+        const int mid = sg == 0 ? (CPLX ? m + N - 1 : m) : (-m + N - 1);
+        const float sgn = (sg == 1 && (m & 1)) ? -1.f : 1.f;
+        const size_t rs = (size_t)(b0 + b) * nmi_src + mi;
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+            epi_f[64 * s + p] = live ? sgn * a.scale * (1.f / LH_TSCALE) / a.csc[s][rs] : 0.f;
+        epi_row[p] = live ? ((long long)(b0 + b) * nmi_dst + mid) * N : -1;
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = sy.tslot;
+    const int nk = sy.nk, ibase = sy.ibase;
+    const int ng = (nk + LH_D - 1) / LH_D;
+    auto kstart = [&](int c) -> int { return m + 32 * (ibase + c); };
+
+    if (warp < LH_BWARPS) {
+        // ------------------------------------------------ operand B of both sets, drains, epilogue
+        const int p = 8 * warp + (lane & 3) + 4 * ((lane >> 3) & 1);
+        const int kq = ((lane >> 2) & 1) + 2 * (lane >> 4);
+        const int sg = p / BT, b = p % BT;
+        const bool live = b0 + b < a.B && (sg == 0 || two);
+        const long long rp = live ? (long long)(b0 + b) * nmi_src + (sg == 0 ? (CPLX ? m + moff : m) : (-m + moff)) : -1;
+        const float2 *row = live ? a.src + rp * a.Lsrc : nullptr;
+        const float cs0 = live ? a.csc[0][rp] : 0.f, cs1 = live ? a.csc[1][rp] : 0.f;
+        const bool al16 = row && ((reinterpret_cast<uintptr_t>(row + m + 8 * kq) & 15) == 0);
+        const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+        const int h = warp >> 2;
+        // the accumulators of group g into the running sums (both sets)
+        auto drain = [&](int g) {
+            const int cl = min(LH_D * g + LH_D - 1, nk - 1);
+            lt_spin(&sy.done[cl % LH_NR], par(cl, LH_NR), abort);
+            tc::fence_after();
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const uint32_t acc = tmem + lane_addr + (uint32_t)(256 * s + 64 * h);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float v[16];
+                    tc::tmem_ld16(acc + 16 * q, v);
+                    if (g > 0) {
+                        float w[16];
+                        tc::tmem_ld16(acc + 128 + 16 * q, w);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v[i] += w[i];
+                    }
+                    lh_tmem_st16(acc + 128 + 16 * q, v);
+                }
+            }
+            tc::tmem_wait_st();
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&sy.tempty);
+        };
+        auto raw = [&](int c, int q) -> unsigned char * {
+            return smem + LH2_RAW_OFF + (c % LH2_NRAW) * LH_STAGE + (256 * q + tid) * 16;
+        };
+        auto issue = [&](int c) {
+            if (c < nk) {
+                const int k = kstart(c) + 8 * kq, kv = row ? N - k : 0;
+                if (al16) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int nb = min(16, max(0, 8 * (kv - 2 * q)));
+                        tc::cp_async16(tc::smem_addr(raw(c, q)), nb ? (const void *)(row + k + 2 * q) : a.src, nb);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const bool in = q < kv;
+                        tc::cp_async8(tc::smem_addr(raw(c, q >> 1) + 8 * (q & 1)), in ? (const void *)(row + k + q) : a.src,
+                                      in ? 8 : 0);
+                    }
+                }
+            }
+            tc::cp_async_commit();
+        };
+        auto store = [&](int c) {
+            unsigned char *Bst = smem + LH2_B_OFF + (c % LH2_NB) * 2 * LH_STAGE;
+            const int k = kstart(c) + 8 * kq;
+            float2 x[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 v = *reinterpret_cast<const float4 *>(raw(c, q));
+                x[2 * q] = make_float2(v.x, v.y);
+                x[2 * q + 1] = make_float2(v.z, v.w);
+            }
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                float xr[8], xi[8];
+                const float *kf = kf_s + LH_MAXN * s - m;
+                const float cs = s ? cs1 : cs0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float f = (k + q < N) ? cs * kf[k + q] : 0.f;
+                    xr[q] = x[q].x * f;
+                    xi[q] = x[q].y * f;
+                }
+                uint4 hr, lr, hi, li;
+                lh_split8(xr, hr, lr);
+                lh_split8(xi, hi, li);
+                unsigned char *Bs = Bst + s * LH_STAGE;
+                const int n0 = 2 * p, n1 = 2 * p + 1;
+                *reinterpret_cast<uint4 *>(Bs + lh_sw(n0, 16 * kq)) = hr;
+                *reinterpret_cast<uint4 *>(Bs + lh_sw(n0, 64 + 16 * kq)) = lr;
+                *reinterpret_cast<uint4 *>(Bs + lh_sw(n1, 16 * kq)) = hi;
+                *reinterpret_cast<uint4 *>(Bs + lh_sw(n1, 64 + 16 * kq)) = li;
+            }
+        };
+        const int oidx = 128 * tile + 32 * (warp & 3) + lane;   // output ring (TMEM lane)
+        int drained = 0;
+        for (int c = 0; c < LH2_NRAW - 1; ++c) issue(c);
+        for (int c = 0; c < nk; ++c) {
+            if (c == (nk > 8 ? nk - 8 : 0) && oidx < N) {
+#pragma unroll 4
+                for (int j = 0; j < 32; ++j) {
+                    const long long ro = epi_row[32 * h + j];
+                    if (ro >= 0) {
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(a.dst[0] + ro + oidx));
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(a.dst[1] + ro + oidx));
+                    }
+                }
+            }
+            issue(c + LH2_NRAW - 1);
+            if (c >= LH2_NB) {
+                // stage c % LH2_NB is free once chunk c - LH2_NB is done; if that chunk
+                // closed a group, its accumulators go into the running sums now (the
+                // MMAs of the next group wait for it)
+                lt_spin(&sy.done[(c - LH2_NB) % LH_NR], par(c - LH2_NB, LH_NR), abort);
+                if ((c - LH2_NB) % LH_D == LH_D - 1) drain(drained++);
+            }
+            tc::cp_async_wait<LH2_NRAW - 1>();
+            store(c);
+            lt_warp_arrive(&sy.bfull[c % LH2_NB], lane);
+        }
+        tc::cp_async_wait<0>();
+        while (drained < ng) drain(drained++);
+        // the TMEM loads are warp-collective: the whole warp takes them (the abort
+        // flag read once per warp), and only the lanes of rings below N store
+        if (!__shfl_sync(0xffffffffu, sy.abort, 0)) {
+            // epilogue: TMEM lane = ring; columns 64 h .. of each set's running sum
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const uint32_t tot = tmem + lane_addr + (uint32_t)(256 * s + 128 + 64 * h);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float v[16];
+                    if (nk > 0) {
+                        tc::tmem_ld16(tot + 16 * q, v);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int pp = 32 * h + 8 * q + i;
+                        const long long ro = epi_row[pp];
+                        if (ro >= 0 && oidx < N) {
+                            const float f = epi_f[64 * s + pp];
+                            a.dst[s][ro + oidx] = make_float2(v[2 * i] * f, v[2 * i + 1] * f);
+                        }
+                    }
+                }
+            }
+        }
+    } else if (warp == LH_COPY_WARP) {
+        // ------------------------------------------------ the table blocks of each chunk, once for both sets
+        if (lane == 0) {
+            int issued = 0;
+            lt_spin(&sy.mfull, 0, abort);
+            for (int c = 0; c < nk; ++c) {
+                if (c >= LH2_NA && !lt_spin(&sy.done[(c - LH2_NA) % LH_NR], par(c - LH2_NA, LH_NR), abort)) break;
+                if (*abort) break;
+                const int s = c % LH2_NA;
+                unsigned char *dstA = smem + s * LH_STAGE;
+                const int4 bl = blks[c];
+                tc::mbar_arrive_expect_tx(&sy.afull[s], LH_STAGE);
+                if (bl.y == bl.x + 1 && bl.z == bl.x + 2 && bl.w == bl.x + 3) {
+                    tc::bulk_g2s(dstA, a.tab + (size_t)bl.x * LI_BLK, LH_STAGE, &sy.afull[s]);
+                } else {
+                    tc::bulk_g2s(dstA, a.tab + (size_t)bl.x * LI_BLK, LI_BLK, &sy.afull[s]);
+                    tc::bulk_g2s(dstA + LI_BLK, a.tab + (size_t)bl.y * LI_BLK, LI_BLK, &sy.afull[s]);
+                    tc::bulk_g2s(dstA + 2 * LI_BLK, a.tab + (size_t)bl.z * LI_BLK, LI_BLK, &sy.afull[s]);
+                    tc::bulk_g2s(dstA + 3 * LI_BLK, a.tab + (size_t)bl.w * LI_BLK, LI_BLK, &sy.afull[s]);
+                }
+                issued = c + 1;
+            }
+            tc::mbar_wait(&sy.mfull, 0, 1u << 22);
+            for (int c = issued - LH2_NA > 0 ? issued - LH2_NA : 0; c < issued; ++c)
+                tc::mbar_wait(&sy.afull[c % LH2_NA], par(c, LH2_NA), 1u << 22);
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------ MMAs: both sets per chunk
+        constexpr uint32_t IDESC = idesc_f16(128, 128);
+        for (int c = 0; c < nk; ++c) {
+            const int g = c / LH_D;
+            const bool first = c % LH_D == 0;
+            bool ok = lt_spin(&sy.afull[c % LH2_NA], par(c, LH2_NA), abort);
+            ok = lt_spin(&sy.bfull[c % LH2_NB], par(c, LH2_NB), abort) && ok;
+            if (first && g >= 1) ok = lt_spin(&sy.tempty, (uint32_t)((g - 1) & 1), abort) && ok;
+            tc::fence_after();
+            if (ok) {
+                const uint32_t abase = tc::smem_addr(smem + (c % LH2_NA) * LH_STAGE);
+                const uint32_t bst = tc::smem_addr(smem + LH2_B_OFF + (c % LH2_NB) * 2 * LH_STAGE);
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    const uint32_t acc = tmem + (uint32_t)(256 * s);
+                    const uint32_t bbase = bst + s * LH_STAGE;
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint64_t ah = tc::smem_desc_sw128(abase + 32 * ks);
+                        const uint64_t al = tc::smem_desc_sw128(abase + 64 + 32 * ks);
+                        const uint64_t bh = tc::smem_desc_sw128(bbase + 32 * ks);
+                        const uint64_t bl = tc::smem_desc_sw128(bbase + 64 + 32 * ks);
+                        mma_f16_ss(acc, ah, bh, IDESC, (ks > 0 || !first) ? 1u : 0u);
+                        mma_f16_ss(acc, ah, bl, IDESC, 1u);
+                        mma_f16_ss(acc, al, bh, IDESC, 1u);
+                    }
+                }
+            }
+            tc::mma_commit(&sy.done[c % LH_NR]);
+        }
+        tc::mma_commit(&sy.fin);
+        tc::mbar_wait(&sy.fin, 0, 1u << 22);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == LH_MMA_WARP) tc::tmem_free(tmem, LT_TMEM_COLS);
+    if (tid == 0 && sy.abort) atomicExch(a.err, 1);
+}
+
+}  // namespace s2g

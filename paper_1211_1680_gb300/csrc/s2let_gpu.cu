@@ -152,6 +152,8 @@ struct s2let_plan {
     float4 *anal_st = nullptr;                         // TF32X3, L > 2048: recurrence states of k_leg_anal_tc
     size_t img_budget = 0, img_used = 0;               // TF32X3: bytes allowed / held by Legendre tables
     float *csc = nullptr;                              // TF32X3: column scales of the table contractions [b][mi]
+    float *csc2 = nullptr;                             // TF32X3: the second set's column scales (k_leg_h16s2)
+    void *G2 = nullptr;                                // TF32X3 with tables: the second set's spectra
     bool quad_gemm = false;                 // FP32 plans: theta quadrature as a dense FP32 product
     bool tc = false;                        // TF32X3 plans: dense products on the tensor cores
     int tc_split = 2;                       // TF32 parts per operand in the tensor-core products
@@ -569,6 +571,46 @@ int run_synth(const s2let_plan *p, const BandDev &bd, const void *src, const voi
     return S2LET_OK;
 }
 
+// S5 of two kernel sets that share the band-limit and f_lm: dst0, dst1 from the
+// plan's L-rectangle src with factors kfac0, kfac1, one table stream (table
+// kernels only: the caller checks synth2_ok).
+bool synth2_ok(const s2let_plan *p, const BandDev &bd)
+{
+    return p->tc && p->G2 && p->csc2 && bd.tc_synth && bd.has_img && bd.img_synth;
+}
+
+int run_synth2(const s2let_plan *p, const BandDev &bd, const void *src, const void *kfac0, const void *kfac1,
+               double scale, void *dst0, void *dst1, cudaStream_t st)
+{
+    StageScope sc(p, S2LET_STAGE_LEG_SYNTH, st, 2.0 * legendre_flops(p, bd.N), 0.0, 3);
+    const size_t rows = (size_t)p->batch * nmi(p, p->L);
+    k_h16_colscale<false><<<(unsigned)((rows + 7) / 8), 256, 0, st>>>((const float2 *)src, p->L, (const float *)kfac0,
+                                                                      bd.N, p->batch, p->cplx, p->csc);
+    k_h16_colscale<false><<<(unsigned)((rows + 7) / 8), 256, 0, st>>>((const float2 *)src, p->L, (const float *)kfac1,
+                                                                      bd.N, p->batch, p->cplx, p->csc2);
+    LegH16Args2 a{};
+    a.src = (const float2 *)src;
+    a.Lsrc = p->L;
+    a.kfac[0] = (const float *)kfac0;
+    a.kfac[1] = (const float *)kfac1;
+    a.scale = (float)scale;
+    a.dst[0] = (float2 *)dst0;
+    a.dst[1] = (float2 *)dst1;
+    a.N = bd.N;
+    a.B = p->batch;
+    a.T = bd.img;
+    a.tab = bd.img_t;
+    a.csc[0] = p->csc;
+    a.csc[1] = p->csc2;
+    a.err = p->d_err;
+    const int bt = p->cplx ? LegCols<true>::BT : LegCols<false>::BT;
+    const dim3 g((bd.N + 127) / 128, bd.N, (p->batch + bt - 1) / bt);
+    if (p->cplx) k_leg_h16s2<true><<<g, LH_THREADS, leg_h16s2_smem(), st>>>(a);
+    else k_leg_h16s2<false><<<g, LH_THREADS, leg_h16s2_smem(), st>>>(a);
+    S2_LAUNCH_CHECK();
+    return S2LET_OK;
+}
+
 size_t anal_gemm_smem(int N)
 {
     return (size_t)(LA_LT * LA_RG + LA_RG * 128) * sizeof(float) + (size_t)N * (sizeof(float4) + sizeof(int));
@@ -784,9 +826,21 @@ template <typename R> int analysis_t(s2let_plan *p, const void *f, void *fw, voi
     int e = sht_fwd_to_rect<R>(p, f, st);
     if (e) return e;
     const int es = elem_size(p);
-    for (const MapRef &mr : map_order(p)) {
+    const std::vector<MapRef> maps = map_order(p);
+    for (size_t i = 0; i < maps.size(); ++i) {
+        const MapRef &mr = maps[i];
         const BandDev &bd = p->bands.at(mr.N);
         char *out = mr.scal ? (char *)fs : (char *)fw + mr.off * es;
+        if (std::is_same<R, float>::value && i + 1 < maps.size() && maps[i + 1].N == mr.N && synth2_ok(p, bd)) {
+            // two maps at one band-limit: one table stream for both syntheses
+            const MapRef &m2 = maps[i + 1];
+            char *out2 = m2.scal ? (char *)fs : (char *)fw + m2.off * es;
+            if ((e = run_synth2(p, bd, p->flm, p->kfac[mr.k], p->kfac[m2.k], 1.0, p->F, p->G2, st))) return e;
+            if ((e = run_ring_inv<R>(p, bd, p->F, out, 1.0, st))) return e;
+            if ((e = run_ring_inv<R>(p, bd, p->G2, out2, 1.0, st))) return e;
+            ++i;
+            continue;
+        }
         if ((e = run_synth<R>(p, bd, p->flm, p->kfac[mr.k], 1.0, p->F, st))) return e;
         if ((e = run_ring_inv<R>(p, bd, p->F, out, 1.0, st))) return e;
     }
@@ -917,6 +971,8 @@ void set_smem_limits(int Mmax)
     allow_smem(k_leg_h16<true, true>, leg_h16_smem());
     allow_smem(k_leg_h16<false, false>, leg_h16_smem());
     allow_smem(k_leg_h16<false, true>, leg_h16_smem());
+    allow_smem(k_leg_h16s2<false>, leg_h16s2_smem());
+    allow_smem(k_leg_h16s2<true>, leg_h16s2_smem());
     allow_smem(k_leg_anal_gemm<false>, anal_gemm_smem(kMaxL));
     allow_smem(k_leg_anal_gemm<true>, anal_gemm_smem(kMaxL));
     allow_smem(k_theta_quad<double, double, 16>, d);
@@ -1360,6 +1416,14 @@ int plan_create(s2let_plan **out, int L, int B, int J0, int flags, int batch)
         if (dm_alloc(p->mem, &p->csc, (size_t)batch * nmi(p.get(), L) * sizeof(float)) != cudaSuccess)
             return S2LET_ERR_ALLOC;
         p->owned.push_back(p->csc);
+        if (p->img_used > 0) {
+            // two wavelet scales at one band-limit share one table stream (k_leg_h16s2)
+            if (dm_alloc(p->mem, &p->csc2, (size_t)batch * nmi(p.get(), L) * sizeof(float)) != cudaSuccess)
+                return S2LET_ERR_ALLOC;
+            p->owned.push_back(p->csc2);
+            if (dm_alloc(p->mem, &p->G2, ws) != cudaSuccess) return S2LET_ERR_ALLOC;
+            p->owned.push_back(p->G2);
+        }
     }
     if (p->tc && L > LA_ST_SMEM_MAX) {
         // one block per (order, batch tile) of the analysis at band-limit L, N float4 each
