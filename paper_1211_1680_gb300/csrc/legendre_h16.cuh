@@ -850,3 +850,335 @@ static __global__ void __launch_bounds__(LH_THREADS, 1) k_leg_h16s2(LegH16Args2 
 }
 
 }  // namespace s2g
+
+namespace s2g {
+
+// k_leg_h16a2: the analysis of two maps at one band-limit N (two wavelet scales
+// whose band-limits are both capped at L) into one set of coefficients:
+//   f_lm (+)= scale (c^0_l sum_t lambda_lm(theta_t) G^0_m(theta_t) + c^1_l sum_t lambda_lm(theta_t) G^1_m(theta_t)).
+// One stream of the table feeds both contractions, as in k_leg_h16s2; each set
+// has its own source rows (copied by cp.async into its own ring, two chunks
+// deep, with L2 prefetches four chunks ahead) and column scales.
+constexpr int LH3_NA = 5, LH3_NB = 2, LH3_NRAW = 2;
+constexpr int LH3_B_OFF = LH3_NA * LH_STAGE;                   // stage s: set 0, set 1
+constexpr int LH3_RAW_OFF = LH3_B_OFF + LH3_NB * 2 * LH_STAGE; // slot r: set 0, set 1
+constexpr int LH3_LIST_OFF = LH3_RAW_OFF + LH3_NRAW * 2 * LH_STAGE;
+constexpr int LH3_BLKS_OFF = LH3_LIST_OFF + LI_MAXK * 4;
+constexpr int LH3_EPI_OFF = LH3_BLKS_OFF + LI_MAXK * 16;       // output row [64], factors [2][64]
+constexpr int LH3_SYNC_OFF = LH3_EPI_OFF + 64 * 8 + 2 * 64 * 4;
+struct Lh3Sync {
+    uint64_t afull[LH3_NA], bfull[LH3_NB], done[LH_NR], tempty, fin, mfull;
+    uint32_t tslot;
+    int abort, nk, ibase;
+};
+static_assert(sizeof(Lh3Sync) <= LH_SYNC_BYTES, "sync block");
+static_assert(LH3_NA < LH_NR && LH3_NB < LH_D, "barrier ring: a drain follows its group's last chunk");
+__host__ __device__ constexpr size_t leg_h16a2_smem() { return (size_t)LH3_SYNC_OFF + LH_SYNC_BYTES + 1024; }
+static_assert(leg_h16a2_smem() <= 227 * 1024, "shared memory");
+
+struct LegH16ArgsA2 {
+    const float2 *src[2];    // G^s [b][mi][t] (band-limit N)
+    const float *kfac[2];    // per-degree factors of the two sets (nullptr: 1)
+    float scale;
+    int accumulate;          // add to dst
+    float2 *dst;             // f [b][mi][l] (rectangle Ldst)
+    int Ldst;
+    int N, B;
+    LegImg T;
+    const unsigned char *tab;   // ta
+    const float *csc[2];     // column scales of G^s [b][mi]
+    int *err;
+};
+
+template <bool CPLX>
+static __global__ void __launch_bounds__(LH_THREADS, 1) k_leg_h16a2(LegH16ArgsA2 a)
+{
+    using Cols = LegCols<CPLX>;
+    constexpr int BT = Cols::BT;
+    extern __shared__ __align__(1024) unsigned char smem_dyn[];
+    unsigned char *smem = lt_align(smem_dyn);
+    Lh3Sync &sy = *reinterpret_cast<Lh3Sync *>(smem + LH3_SYNC_OFF);
+    int *klist = reinterpret_cast<int *>(smem + LH3_LIST_OFF);
+    int4 *blks = reinterpret_cast<int4 *>(smem + LH3_BLKS_OFF);
+    long long *epi_row = reinterpret_cast<long long *>(smem + LH3_EPI_OFF);
+    float *epi_f = reinterpret_cast<float *>(smem + LH3_EPI_OFF + 64 * 8);       // [2][64]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N = a.N;
+    const int2 md0 = a.T.adt[blockIdx.x];
+    const int m = md0.x, tile = md0.y, b0 = blockIdx.y * BT;
+    const bool two = CPLX && m > 0;
+    volatile int *abort = &sy.abort;
+    auto par = [](int c, int n) -> uint32_t { return (uint32_t)((c / n) & 1); };
+
+    if (warp == LH_MMA_WARP) {
+        tc::tmem_alloc(&sy.tslot, LT_TMEM_COLS);
+    } else if (warp == LH_COPY_WARP && lane == 0) {
+#pragma unroll
+        for (int i = 0; i < LH3_NA; ++i) tc::mbar_init(&sy.afull[i], 1);
+#pragma unroll
+        for (int i = 0; i < LH3_NB; ++i) tc::mbar_init(&sy.bfull[i], LH_BWARPS);
+#pragma unroll
+        for (int i = 0; i < LH_NR; ++i) tc::mbar_init(&sy.done[i], 1);
+        tc::mbar_init(&sy.tempty, LH_BWARPS);
+        tc::mbar_init(&sy.fin, 1);
+        tc::mbar_init(&sy.mfull, 1);
+        sy.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const int4 md = a.T.ameta[blockIdx.x];
+        sy.nk = md.y;
+        sy.ibase = 0;
+        const uint32_t nb = (uint32_t)md.y * 16u, nl = (uint32_t)((md.y + 3) & ~3) * 4u;
+        tc::mbar_arrive_expect_tx(&sy.mfull, nb + nl);
+        if (md.y > 0) {
+            tc::bulk_g2s(blks, a.T.ablk + md.x, nb, &sy.mfull);
+            tc::bulk_g2s(klist, a.T.ack + md.z, nl, &sy.mfull);
+        }
+    }
+    const int nmi_src = CPLX ? 2 * N - 1 : N;
+    const int moff = N - 1;
+    if (warp < LH_BWARPS && (lane & 0x14) == 0) {
+        const int p = 8 * warp + (lane & 3) + 4 * ((lane >> 3) & 1);
+        const int sg = p / BT, b = p % BT;
+        const bool live = b0 + b < a.B && (sg == 0 || two);
+        const int mi = sg == 0 ? (CPLX ? m + moff : m) : (-m + moff);
+        const int nmi_dst = CPLX ? 2 * a.Ldst - 1 : a.Ldst;
+        const int mid = sg == 0 ? (CPLX ? m + a.Ldst - 1 : m) : (-m + a.Ldst - 1);
+        const float sgn = (sg == 1 && (m & 1)) ? -1.f : 1.f;
+        const size_t rs = (size_t)(b0 + b) * nmi_src + mi;
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+            epi_f[64 * s + p] = live ? sgn * a.scale * (1.f / LH_TSCALE) / a.csc[s][rs] : 0.f;
+        epi_row[p] = live ? ((long long)(b0 + b) * nmi_dst + mid) * a.Ldst : -1;
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = sy.tslot;
+    const int nk = sy.nk;
+    const int ng = (nk + LH_D - 1) / LH_D;
+    auto kstart = [&](int c) -> int { return 32 * klist[c]; };
+
+    if (warp < LH_BWARPS) {
+        // ------------------------------------------------ operand B of both sets, drains, epilogue
+        const int p = 8 * warp + (lane & 3) + 4 * ((lane >> 3) & 1);
+        const int kq = ((lane >> 2) & 1) + 2 * (lane >> 4);
+        const int sg = p / BT, b = p % BT;
+        const bool live = b0 + b < a.B && (sg == 0 || two);
+        const long long rp = live ? (long long)(b0 + b) * nmi_src + (sg == 0 ? (CPLX ? m + moff : m) : (-m + moff)) : -1;
+        const float2 *row0 = live ? a.src[0] + rp * N : nullptr;
+        const float2 *row1 = live ? a.src[1] + rp * N : nullptr;
+        const float cs0 = live ? a.csc[0][rp] : 0.f, cs1 = live ? a.csc[1][rp] : 0.f;
+        // the first K of every chunk is a multiple of 32, so alignment is the row's
+        const bool al0 = row0 && ((reinterpret_cast<uintptr_t>(row0 + 8 * kq) & 15) == 0);
+        const bool al1 = row1 && ((reinterpret_cast<uintptr_t>(row1 + 8 * kq) & 15) == 0);
+        const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+        const int h = warp >> 2;
+        auto drain = [&](int g) {
+            const int cl = min(LH_D * g + LH_D - 1, nk - 1);
+            lt_spin(&sy.done[cl % LH_NR], par(cl, LH_NR), abort);
+            tc::fence_after();
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const uint32_t acc = tmem + lane_addr + (uint32_t)(256 * s + 64 * h);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float v[16];
+                    tc::tmem_ld16(acc + 16 * q, v);
+                    if (g > 0) {
+                        float w[16];
+                        tc::tmem_ld16(acc + 128 + 16 * q, w);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v[i] += w[i];
+                    }
+                    lh_tmem_st16(acc + 128 + 16 * q, v);
+                }
+            }
+            tc::tmem_wait_st();
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&sy.tempty);
+        };
+        auto raw = [&](int c, int s, int q) -> unsigned char * {
+            return smem + LH3_RAW_OFF + ((c % LH3_NRAW) * 2 + s) * LH_STAGE + (256 * q + tid) * 16;
+        };
+        auto issue_set = [&](int c, int s, const float2 *row, bool al) {
+            const int k = kstart(c) + 8 * kq, kv = row ? N - k : 0;
+            if (al) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int nb = min(16, max(0, 8 * (kv - 2 * q)));
+                    tc::cp_async16(tc::smem_addr(raw(c, s, q)), nb ? (const void *)(row + k + 2 * q) : (const void *)a.src[0],
+                                   nb);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const bool in = q < kv;
+                    tc::cp_async8(tc::smem_addr(raw(c, s, q >> 1) + 8 * (q & 1)),
+                                  in ? (const void *)(row + k + q) : (const void *)a.src[0], in ? 8 : 0);
+                }
+            }
+        };
+        auto issue = [&](int c) {
+            if (c < nk) {
+                issue_set(c, 0, row0, al0);
+                issue_set(c, 1, row1, al1);
+            }
+            tc::cp_async_commit();
+            // the rows of chunk c + 4 into L2, so that its copies find them there
+            if (c + 4 < nk) {
+                const int k = kstart(c + 4) + 8 * kq;
+                if (k < N) {
+                    if (row0) asm volatile("prefetch.global.L2 [%0];" ::"l"(row0 + k));
+                    if (row1) asm volatile("prefetch.global.L2 [%0];" ::"l"(row1 + k));
+                }
+            }
+        };
+        auto store = [&](int c) {
+            unsigned char *Bst = smem + LH3_B_OFF + (c % LH3_NB) * 2 * LH_STAGE;
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                float xr[8], xi[8];
+                const float cs = s ? cs1 : cs0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 v = *reinterpret_cast<const float4 *>(raw(c, s, q));
+                    xr[2 * q] = v.x * cs;
+                    xi[2 * q] = v.y * cs;
+                    xr[2 * q + 1] = v.z * cs;
+                    xi[2 * q + 1] = v.w * cs;
+                }
+                uint4 hr, lr, hi, li;
+                lh_split8(xr, hr, lr);
+                lh_split8(xi, hi, li);
+                unsigned char *Bs = Bst + s * LH_STAGE;
+                const int n0 = 2 * p, n1 = 2 * p + 1;
+                *reinterpret_cast<uint4 *>(Bs + lh_sw(n0, 16 * kq)) = hr;
+                *reinterpret_cast<uint4 *>(Bs + lh_sw(n0, 64 + 16 * kq)) = lr;
+                *reinterpret_cast<uint4 *>(Bs + lh_sw(n1, 16 * kq)) = hi;
+                *reinterpret_cast<uint4 *>(Bs + lh_sw(n1, 64 + 16 * kq)) = li;
+            }
+        };
+        const int oidx = m + 128 * tile + 32 * (warp & 3) + lane;   // output degree (TMEM lane)
+        int drained = 0;
+        lt_spin(&sy.mfull, 0, abort);                  // the chunks' ring blocks (klist) have landed
+        for (int c = 0; c < LH3_NRAW - 1; ++c) issue(c);
+        for (int c = 0; c < nk; ++c) {
+            if (c == (nk > 8 ? nk - 8 : 0) && oidx < N) {
+#pragma unroll 4
+                for (int j = 0; j < 32; ++j) {
+                    const long long ro = epi_row[32 * h + j];
+                    if (ro >= 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.dst + ro + oidx));
+                }
+            }
+            issue(c + LH3_NRAW - 1);
+            if (c >= LH3_NB) {
+                lt_spin(&sy.done[(c - LH3_NB) % LH_NR], par(c - LH3_NB, LH_NR), abort);
+                if ((c - LH3_NB) % LH_D == LH_D - 1) drain(drained++);
+            }
+            tc::cp_async_wait<LH3_NRAW - 1>();
+            store(c);
+            lt_warp_arrive(&sy.bfull[c % LH3_NB], lane);
+        }
+        tc::cp_async_wait<0>();
+        while (drained < ng) drain(drained++);
+        // the TMEM loads are warp-collective: the whole warp takes them, only the
+        // lanes of degrees below N load and store the coefficients
+        if (!__shfl_sync(0xffffffffu, sy.abort, 0)) {
+            const bool in = oidx < N;
+            const float k0 = (in && a.kfac[0]) ? a.kfac[0][oidx] : 1.f;
+            const float k1 = (in && a.kfac[1]) ? a.kfac[1][oidx] : 1.f;
+            const uint32_t tot = tmem + lane_addr + (uint32_t)(128 + 64 * h);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float v0[16], v1[16];
+                if (nk > 0) {
+                    tc::tmem_ld16(tot + 16 * q, v0);
+                    tc::tmem_ld16(tot + 256 + 16 * q, v1);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v0[i] = v1[i] = 0.f;
+                }
+                float2 w[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const long long ro = epi_row[32 * h + 8 * q + i];
+                    w[i] = (a.accumulate && in && ro >= 0) ? a.dst[ro + oidx] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int pp = 32 * h + 8 * q + i;
+                    const long long ro = epi_row[pp];
+                    if (in && ro >= 0) {
+                        const float f0 = epi_f[pp] * k0, f1 = epi_f[64 + pp] * k1;
+                        a.dst[ro + oidx] = make_float2(w[i].x + v0[2 * i] * f0 + v1[2 * i] * f1,
+                                                       w[i].y + v0[2 * i + 1] * f0 + v1[2 * i + 1] * f1);
+                    }
+                }
+            }
+        }
+    } else if (warp == LH_COPY_WARP) {
+        if (lane == 0) {
+            int issued = 0;
+            lt_spin(&sy.mfull, 0, abort);
+            for (int c = 0; c < nk; ++c) {
+                if (c >= LH3_NA && !lt_spin(&sy.done[(c - LH3_NA) % LH_NR], par(c - LH3_NA, LH_NR), abort)) break;
+                if (*abort) break;
+                const int s = c % LH3_NA;
+                unsigned char *dstA = smem + s * LH_STAGE;
+                const int4 bl = blks[c];
+                tc::mbar_arrive_expect_tx(&sy.afull[s], LH_STAGE);
+                if (bl.y == bl.x + 1 && bl.z == bl.x + 2 && bl.w == bl.x + 3) {
+                    tc::bulk_g2s(dstA, a.tab + (size_t)bl.x * LI_BLK, LH_STAGE, &sy.afull[s]);
+                } else {
+                    tc::bulk_g2s(dstA, a.tab + (size_t)bl.x * LI_BLK, LI_BLK, &sy.afull[s]);
+                    tc::bulk_g2s(dstA + LI_BLK, a.tab + (size_t)bl.y * LI_BLK, LI_BLK, &sy.afull[s]);
+                    tc::bulk_g2s(dstA + 2 * LI_BLK, a.tab + (size_t)bl.z * LI_BLK, LI_BLK, &sy.afull[s]);
+                    tc::bulk_g2s(dstA + 3 * LI_BLK, a.tab + (size_t)bl.w * LI_BLK, LI_BLK, &sy.afull[s]);
+                }
+                issued = c + 1;
+            }
+            tc::mbar_wait(&sy.mfull, 0, 1u << 22);
+            for (int c = issued - LH3_NA > 0 ? issued - LH3_NA : 0; c < issued; ++c)
+                tc::mbar_wait(&sy.afull[c % LH3_NA], par(c, LH3_NA), 1u << 22);
+        }
+    } else if (lane == 0) {
+        constexpr uint32_t IDESC = idesc_f16(128, 128);
+        for (int c = 0; c < nk; ++c) {
+            const int g = c / LH_D;
+            const bool first = c % LH_D == 0;
+            bool ok = lt_spin(&sy.afull[c % LH3_NA], par(c, LH3_NA), abort);
+            ok = lt_spin(&sy.bfull[c % LH3_NB], par(c, LH3_NB), abort) && ok;
+            if (first && g >= 1) ok = lt_spin(&sy.tempty, (uint32_t)((g - 1) & 1), abort) && ok;
+            tc::fence_after();
+            if (ok) {
+                const uint32_t abase = tc::smem_addr(smem + (c % LH3_NA) * LH_STAGE);
+                const uint32_t bst = tc::smem_addr(smem + LH3_B_OFF + (c % LH3_NB) * 2 * LH_STAGE);
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    const uint32_t acc = tmem + (uint32_t)(256 * s);
+                    const uint32_t bbase = bst + s * LH_STAGE;
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint64_t ah = tc::smem_desc_sw128(abase + 32 * ks);
+                        const uint64_t al = tc::smem_desc_sw128(abase + 64 + 32 * ks);
+                        const uint64_t bh = tc::smem_desc_sw128(bbase + 32 * ks);
+                        const uint64_t bl = tc::smem_desc_sw128(bbase + 64 + 32 * ks);
+                        mma_f16_ss(acc, ah, bh, IDESC, (ks > 0 || !first) ? 1u : 0u);
+                        mma_f16_ss(acc, ah, bl, IDESC, 1u);
+                        mma_f16_ss(acc, al, bh, IDESC, 1u);
+                    }
+                }
+            }
+            tc::mma_commit(&sy.done[c % LH_NR]);
+        }
+        tc::mma_commit(&sy.fin);
+        tc::mbar_wait(&sy.fin, 0, 1u << 22);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == LH_MMA_WARP) tc::tmem_free(tmem, LT_TMEM_COLS);
+    if (tid == 0 && sy.abort) atomicExch(a.err, 1);
+}
+
+}  // namespace s2g

@@ -440,8 +440,10 @@ int run_ring_inv(const s2let_plan *p, const BandDev &bd, const void *F, void *f,
 // S2.  Returns the buffer that holds G: F itself (in-place FFT quadrature) or
 // the plan's G buffer (dense-matrix quadrature of FP32 plans).
 template <typename R>
-void *run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream_t st, int *err)
+void *run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream_t st, int *err, void *Gout = nullptr)
 {
+    // Gout: where the dense-matrix quadrature writes G (default the plan's G buffer)
+    void *const Gb = Gout ? Gout : p->G;
     const int n = nmi(p, bd.N);
     const int off = p->cplx ? bd.N - 1 : 0;
     *err = S2LET_OK;
@@ -465,13 +467,13 @@ void *run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream
                 // F rows by bulk copies where every row starts on a 16-byte boundary
                 const bool fraw = bd.N % 2 == 0 && (reinterpret_cast<uintptr_t>(F) & 15) == 0;
                 (fraw ? k_quad_tcp<true> : k_quad_tcp<false>)<<<grid, LT_THREADS, quad_tc_smem(), st>>>(
-                    par ? bd.Qoi : bd.Qei, (const float2 *)F, (float2 *)p->G, bd.N, n, mi0, nj, npairs, p->d_err);
+                    par ? bd.Qoi : bd.Qei, (const float2 *)F, (float2 *)Gb, bd.N, n, mi0, nj, npairs, p->d_err);
             }
             else if (p->tc && bd.tc_quad)
                 k_quad_tc<3, 2><<<grid, TQ_THREADS, TqShape<3, 2>::SMEM, st>>>(
-                    par ? bd.Qo3 : bd.Qe3, (const float2 *)F, (float2 *)p->G, bd.N, n, mi0, nj, npairs, p->d_err);
+                    par ? bd.Qo3 : bd.Qe3, (const float2 *)F, (float2 *)Gb, bd.N, n, mi0, nj, npairs, p->d_err);
             else
-                k_quad_gemm<<<grid, 256, 0, st>>>(par ? bd.Qo : bd.Qe, (const float2 *)F, (float2 *)p->G, bd.N, n,
+                k_quad_gemm<<<grid, 256, 0, st>>>(par ? bd.Qo : bd.Qe, (const float2 *)F, (float2 *)Gb, bd.N, n,
                                                   mi0, nj, npairs);
         }
         if (fft) {
@@ -494,12 +496,12 @@ void *run_theta_quad(const s2let_plan *p, const BandDev &bd, void *F, cudaStream
             C.nunits = C.upm * p->batch;
 #define S2G_MR_LAUNCH(P_)                                                                                           \
     k_quad_mr<P_><<<(C.nunits + mr_quad_cpb<P_>() - 1) / mr_quad_cpb<P_>(), MR_THREADS, mr_quad_smem<P_>(), st>>>( \
-        (const float2 *)F, (float2 *)p->G, C, bd.mr)
+        (const float2 *)F, (float2 *)Gb, C, bd.mr)
             S2G_MR_SWITCH(bd.P)
 #undef S2G_MR_LAUNCH
         }
         if (cudaGetLastError() != cudaSuccess) *err = S2LET_ERR_CUDA;
-        return p->G;
+        return Gb;
     }
     const int th = fft_threads(bd.M);
     StageScope sc(p, S2LET_STAGE_THETA_QUAD, st, 0.0, 2.0 * spectrum_bytes(p, bd.N));
@@ -607,6 +609,46 @@ int run_synth2(const s2let_plan *p, const BandDev &bd, const void *src, const vo
     const dim3 g((bd.N + 127) / 128, bd.N, (p->batch + bt - 1) / bt);
     if (p->cplx) k_leg_h16s2<true><<<g, LH_THREADS, leg_h16s2_smem(), st>>>(a);
     else k_leg_h16s2<false><<<g, LH_THREADS, leg_h16s2_smem(), st>>>(a);
+    S2_LAUNCH_CHECK();
+    return S2LET_OK;
+}
+
+// S3 of two maps at one band-limit into one set of coefficients: dst (+)=
+// c^0 A(G0) + c^1 A(G1), one table stream (table kernels only: anal2_ok).
+bool anal2_ok(const s2let_plan *p, const BandDev &bd)
+{
+    return p->tc && p->G2 && p->csc2 && p->quad_gemm && bd.tc_anal && bd.has_img && bd.img_anal;
+}
+
+int run_anal2(const s2let_plan *p, const BandDev &bd, const void *G0, const void *G1, const void *kfac0,
+              const void *kfac1, double scale, int acc, void *dst, cudaStream_t st)
+{
+    StageScope sc(p, S2LET_STAGE_LEG_ANAL, st, 2.0 * legendre_flops(p, bd.N), 0.0, 3);
+    const size_t rows = (size_t)p->batch * nmi(p, bd.N);
+    k_h16_colscale<true><<<(unsigned)((rows + 7) / 8), 256, 0, st>>>((const float2 *)G0, 0, nullptr, bd.N, p->batch,
+                                                                     p->cplx, p->csc);
+    k_h16_colscale<true><<<(unsigned)((rows + 7) / 8), 256, 0, st>>>((const float2 *)G1, 0, nullptr, bd.N, p->batch,
+                                                                     p->cplx, p->csc2);
+    LegH16ArgsA2 a{};
+    a.src[0] = (const float2 *)G0;
+    a.src[1] = (const float2 *)G1;
+    a.kfac[0] = (const float *)kfac0;
+    a.kfac[1] = (const float *)kfac1;
+    a.scale = (float)scale;
+    a.accumulate = acc;
+    a.dst = (float2 *)dst;
+    a.Ldst = p->L;
+    a.N = bd.N;
+    a.B = p->batch;
+    a.T = bd.img;
+    a.tab = bd.img.img;
+    a.csc[0] = p->csc;
+    a.csc[1] = p->csc2;
+    a.err = p->d_err;
+    const int bt = p->cplx ? LegCols<true>::BT : LegCols<false>::BT;
+    const dim3 g(bd.n_adt, (p->batch + bt - 1) / bt);
+    if (p->cplx) k_leg_h16a2<true><<<g, LH_THREADS, leg_h16a2_smem(), st>>>(a);
+    else k_leg_h16a2<false><<<g, LH_THREADS, leg_h16a2_smem(), st>>>(a);
     S2_LAUNCH_CHECK();
     return S2LET_OK;
 }
@@ -851,9 +893,28 @@ template <typename R> int synthesis_t(s2let_plan *p, const void *fw, const void 
 {
     const int es = elem_size(p);
     int e, first = 1;
-    for (const MapRef &mr : map_order(p)) {
+    const std::vector<MapRef> maps = map_order(p);
+    for (size_t i = 0; i < maps.size(); ++i) {
+        const MapRef &mr = maps[i];
         const BandDev &bd = p->bands.at(mr.N);
         const char *in = mr.scal ? (const char *)fs : (const char *)fw + mr.off * es;
+        if (std::is_same<R, float>::value && i + 1 < maps.size() && maps[i + 1].N == mr.N && anal2_ok(p, bd)) {
+            // two maps at one band-limit: their spectra in G and G2, one table stream for both
+            const MapRef &m2 = maps[i + 1];
+            const char *in2 = m2.scal ? (const char *)fs : (const char *)fw + m2.off * es;
+            if ((e = run_ring_fwd<R>(p, bd, in, p->F, 1.0 / bd.P, st))) return e;
+            void *G = run_theta_quad<R>(p, bd, p->F, st, &e);
+            if (e) return e;
+            if ((e = run_ring_fwd<R>(p, bd, in2, p->F, 1.0 / bd.P, st))) return e;
+            void *G2 = run_theta_quad<R>(p, bd, p->F, st, &e, p->G2);
+            if (e) return e;
+            if ((e = run_anal2(p, bd, G, G2, p->kfac[mr.k], p->kfac[m2.k], 2.0 * M_PI / bd.P, first ? 0 : 1, p->flm,
+                               st)))
+                return e;
+            first = 0;
+            ++i;
+            continue;
+        }
         if ((e = run_ring_fwd<R>(p, bd, in, p->F, 1.0 / bd.P, st))) return e;
         void *G = run_theta_quad<R>(p, bd, p->F, st, &e);
         if (e) return e;
@@ -973,6 +1034,8 @@ void set_smem_limits(int Mmax)
     allow_smem(k_leg_h16<false, true>, leg_h16_smem());
     allow_smem(k_leg_h16s2<false>, leg_h16s2_smem());
     allow_smem(k_leg_h16s2<true>, leg_h16s2_smem());
+    allow_smem(k_leg_h16a2<false>, leg_h16a2_smem());
+    allow_smem(k_leg_h16a2<true>, leg_h16a2_smem());
     allow_smem(k_leg_anal_gemm<false>, anal_gemm_smem(kMaxL));
     allow_smem(k_leg_anal_gemm<true>, anal_gemm_smem(kMaxL));
     allow_smem(k_theta_quad<double, double, 16>, d);
