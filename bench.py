@@ -282,13 +282,34 @@ def peak_table(peaks):
     }
 
 
+def legendre_launches(plan, key):
+    """The Legendre launches of one round trip in one direction, as (band-limit,
+    maps per launch): the SHT at L, and one per wavelet or scaling map, where
+    two maps next to each other in the library's processing order (scale J
+    first, the scaling map last) that share a band-limit on the table kernels
+    share one launch (one table stream for both)."""
+    tun = plan.tuning()
+    order = [n for (_, n, _, _) in sorted(plan.scales, reverse=True)] + [plan.N_scal]
+    out = [(plan.L, 1)]
+    i = 0
+    while i < len(order):
+        n = order[i]
+        if i + 1 < len(order) and order[i + 1] == n and tun[n][key]:
+            out.append((n, 2))
+            i += 2
+        else:
+            out.append((n, 1))
+            i += 1
+    return out
+
+
 def legendre_tables(plan):
     """Per Legendre stage: which values it contracts ("table": the plan's stored
     Legendre tables, "recurrence": computed in the kernel) at the full band-limit,
-    the table bytes its launches of one round trip read, and the bytes one launch
+    the table bytes its launches of one round trip read, the bytes one launch
     reads at each band-limit (one of the two copies the plan stores: rows =
     degrees for the analysis, rows = rings for the synthesis; 0 where the stage
-    runs the recurrence)."""
+    runs the recurrence), and its launches as (band-limit, maps per launch)."""
     if plan.precision != "tf32x3":
         return {}
     tun = plan.tuning()
@@ -296,7 +317,8 @@ def legendre_tables(plan):
     for stage, key in (("leg_anal", "table_anal"), ("leg_synth", "table_synth")):
         variant = "table" if tun[plan.L][key] else "recurrence"
         per = {n: (plan.table_bytes(n) // 2 if tun[n][key] else 0) for n in set(plan_bandlimits(plan))}
-        out[stage] = (variant, sum(per[n] for n in plan_bandlimits(plan)), per)
+        launches = legendre_launches(plan, key)
+        out[stage] = (variant, sum(per[n] for n, _ in launches), per, launches)
     return out
 
 
@@ -363,9 +385,9 @@ def rooflines(stats, a, peaks, batch, bandlimits, tables=None):
     tables = tables or {}
     recs = {k: stage_roofline(k, v, a.steps, a.precision, pk, batch, tables.get(k, ("recurrence", 0))[0])
             for k, v in stats.items() if v["launches"]}
-    tables = {k: (t + ({},))[:3] for k, t in tables.items()}
+    tables = {k: (t + ({}, None))[:4] for k, t in tables.items()}
     recs = {k: v for k, v in recs.items() if v is not None}
-    for k, (variant, tbytes, _) in tables.items():
+    for k, (variant, tbytes, _, _) in tables.items():
         if k in recs:
             recs[k]["legendre_values"] = variant
             if tbytes:
@@ -376,14 +398,16 @@ def rooflines(stats, a, peaks, batch, bandlimits, tables=None):
     dom = max(recs, key=lambda k: recs[k]["ms_per_step"])
     roof = dict(recs[dom])
     roof["kernel"] = dom
-    variant, _, per = tables.get(dom, ("recurrence", 0, {}))
+    variant, _, per, launches = tables.get(dom, ("recurrence", 0, {}, None))
     tr = TRAFFIC.get((dom, variant)) if a.precision == "tf32x3" else None
     if tr and variant == "table" and tr["bytes_at"][0] in per:
         # table kernels: the table part of a launch is the copy it streams (grows as
-        # the table, ~N^3); the rest (data read, results written) as N^2 x maps
+        # the table, ~N^3), once per launch even where two maps share it; the rest
+        # (data read, results written) as N^2 x maps, per map of the launch
         n0, b0, by = tr["bytes_at"]
         rest = by - per[n0]
-        roof["traffic"] = sum(per.get(n, 0) + rest * (n / n0) ** 2 * batch / b0 for n in bandlimits)
+        launches = launches or [(n, 1) for n in bandlimits]
+        roof["traffic"] = sum(per.get(n, 0) + sets * rest * (n / n0) ** 2 * batch / b0 for n, sets in launches)
         roof["traffic_note"] = tr["source"]
     elif tr and variant != "table":
         n0, b0, by = tr["bytes_at"]

@@ -115,3 +115,10 @@ def test_stage_rooflines_follow_the_work_of_each_stage():
     want = sum(per1[n] + rest * (n / n0) ** 2 * 64 / b0 for n in (2048, 8, 4))
     assert roof4["traffic"] == pytest.approx(want)
     assert roof3["traffic"] is None
+    # two maps sharing a launch read the table once and their data twice
+    launches = [(2048, 1), (2048, 2), (8, 1), (4, 1)]
+    roof5, _, _ = bench.rooflines(stats, a, peaks, 64, [2048, 2048, 2048, 8, 4],
+                                  {"leg_anal": ("table", 30e9, per1, launches),
+                                   "leg_synth": ("table", 30e9, per1, launches)})
+    want5 = sum(per1[n] + k * rest * (n / n0) ** 2 * 64 / b0 for n, k in launches)
+    assert roof5["traffic"] == pytest.approx(want5)
