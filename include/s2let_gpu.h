@@ -60,9 +60,12 @@ extern "C" {
                                     FP64                                       */
 #define S2LET_PREC_TF32X3 0x20   /* as FP32, with the dense quadrature product and
                                     the Legendre contractions on the tensor cores
-                                    (tcgen05): operands split in TF32 hi + lo, 3
+                                    (tcgen05): operands split in hi + lo parts, 3
                                     MMAs per product, TMEM partial sums over at
-                                    most 128 K values added in FP32 registers  */
+                                    most 128 K values added in FP32; the parts
+                                    are TF32 in the quadrature and the
+                                    recurrence kernels, FP16 (with exact power-
+                                    of-two scales) on the Legendre tables      */
 #define S2LET_PREC_MASK 0xf0
 #define S2LET_QUAD_FFT64 0x100   /* FP32 plans only: theta quadrature by FP64 FFTs
                                     instead of the dense FP32 product          */
@@ -103,12 +106,15 @@ int s2let_jmax(int L, int B);
  * length M >= 4L - 3 would exceed the SM's shared memory; S2LET_ERR_UNSUPPORTED).
  * The MW sampling theorem is stable to such band-limits (Sect. 2.1).
  * TF32X3 plans without S2LET_LEG_RECURRENCE also store the associated Legendre
- * values lambda_lm(theta_t) of each band-limit N (the FP64 recurrence from the
- * FP64 seeds, rounded to FP32; about N^3 / 2 values less those below 2^-100, 4
- * bytes each), so that the Legendre stages stream them instead of recomputing
- * them for every batch.  Band-limits are stored from the smallest up while the
- * total stays within S2LET_LEG_TABLE_MAX_BYTES and half the device memory free
- * at creation; the others use the recurrence.  s2let_plan_leg_table_bytes
+ * values lambda_lm(theta_t) of each band-limit N <= 2048 (the FP64 recurrence
+ * from the FP64 seeds, scaled by 2^9 and split into FP16 hi + lo; about N^3 / 2
+ * values less those below 2^-100, 4 bytes each, in two copies: one laid out for
+ * the analysis, one for the synthesis), so that the Legendre stages stream them
+ * instead of recomputing them for every batch.  Band-limits are stored from the
+ * smallest up while the total stays within S2LET_LEG_TABLE_MAX_BYTES and half
+ * the device memory free at creation; the others use the recurrence.  Such
+ * plans also hold a second spectrum rectangle, so that two maps of a wavelet
+ * transform at one band-limit share a table stream.  s2let_plan_leg_table_bytes
  * reports the sizes.  On error *plan is NULL. */
 #define S2LET_LEG_TABLE_MAX_BYTES (64ull << 30)
 int s2let_plan_create(s2let_plan **plan, int L, int B, int J_min, int flags, int batch);
