@@ -97,6 +97,32 @@ def test_tables_wavelets_accumulate(real):
     assert plan.status() == 0
 
 
+@pytest.mark.parametrize("real,nb", [(True, 70), (False, 35)])
+def test_two_map_streams_two_batch_tiles(real, nb):
+    """The wavelet scales 5 and 6 of L = 64 (B = 2) share the band-limit 64, so the
+    analysis runs their syntheses as one two-map launch on one table stream and the
+    synthesis their analyses likewise; with 70 real (35 complex) maps both run two
+    batch tiles.  Maps of both tiles against the oracle."""
+    L, B, J0 = 64, 2, 2
+    seeds = list(range(800, 800 + nb))
+    sub = [0, nb // 2 + 3, nb - 1]
+    f = np.stack([sht.inverse(inputs.random_flm(L, s, real, "white"), L, real=real) for s in seeds])
+    plan = Plan(L, B, J0, batch=nb, real=real, multires=True, precision="tf32x3")
+    assert plan.tuning()[L]["table_anal"] and plan.tuning()[L]["table_synth"]
+    assert [n for (_, n, _, _) in plan.scales][-2:] == [L, L]
+    fw, fs = plan.analysis(to_dev_map(f, plan.dtype, real))
+    views = plan.wavelet_views(fw)
+    for b in sub:
+        ref_w, ref_s = wavelet.analysis(f[b], L, B, J0, True, real)
+        for i, v in enumerate(views):
+            assert rel_err(from_dev_map(v, real)[b], ref_w[i]) < TOL["tf32x3"], (b, i)
+        assert rel_err(from_dev_map(fs, real)[b], ref_s) < TOL["tf32x3"], b
+    rec = from_dev_map(plan.synthesis(fw, fs), real)
+    assert rel_err(rec[sub], f[sub]) < TOL["tf32x3"]
+    assert rel_err(rec, f) < TOL["tf32x3"]
+    assert plan.status() == 0
+
+
 def test_table_bytes_per_band_limit():
     """Per band-limit sizes add up to the total, stay within every-block bound,
     and leave out polar blocks below 2^-100 at N = 256."""
