@@ -7,8 +7,10 @@
 // degrees m + 32 i .. m + 32 i + 31 of order m, ring block k = rings 32 k ..
 // 32 k + 31.  For order m and ring block k only the degree blocks i >= i0[m][k]
 // are stored, the first holding a value >= 2^-SEED_EXP (the recurrence starts
-// at l_s(m, t) on each ring; below it the values are left out as zero), at
-// block index off[m][k] + i - i0[m][k]; block 0 holds zeros and stands for
+// at l_s(m, t) on each ring; below it the values are left out as zero): in the
+// analysis copy at block index off[m][k] + i - i0[m][k] (the degree blocks of a
+// ring block adjacent), in the synthesis copy in ring-block order per degree
+// block (legendre_h16.cuh, k_h16_fill); block 0 holds zeros and stands for
 // every block not stored.  The analysis walks, per (order, degree tile of 128),
 // the ring blocks with a stored block among its four degree blocks (adt lists
 // these (m, tile) items); the synthesis walks, per (ring tile of 128, order),

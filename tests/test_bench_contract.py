@@ -122,3 +122,27 @@ def test_stage_rooflines_follow_the_work_of_each_stage():
                                    "leg_synth": ("table", 30e9, per1, launches)})
     want5 = sum(per1[n] + k * rest * (n / n0) ** 2 * 64 / b0 for n, k in launches)
     assert roof5["traffic"] == pytest.approx(want5)
+
+
+def test_legendre_launches_pair_maps_at_one_band_limit():
+    """The bench counts the Legendre launches of a round trip as the library runs
+    them: the SHT at L, then the maps from scale J down (the scaling map last),
+    two neighbours that share a band-limit on the table kernels in one launch."""
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+    L = 2048
+    ns = [min(L, 2 ** (j + 1)) for j in range(2, 12)]
+    tun = {n: {"table_anal": True, "table_synth": n != 1024} for n in set(ns) | {L, 4}}
+    plan = types.SimpleNamespace(L=L, N_scal=4, scales=[(j, n, 0, 0) for j, n in zip(range(2, 12), ns)],
+                                 tuning=lambda: tun)
+    want = [(L, 1), (L, 2)] + [(n, 1) for n in ns[::-1][2:]] + [(4, 1)]
+    assert bench.legendre_launches(plan, "table_synth") == want
+    # full resolution: every scale at L, paired two by two, the last one alone
+    full = types.SimpleNamespace(L=64, N_scal=64, scales=[(j, 64, 0, 0) for j in range(0, 7)],
+                                 tuning=lambda: {64: {"table_anal": True, "table_synth": True}})
+    assert bench.legendre_launches(full, "table_anal") == [(64, 1), (64, 2), (64, 2), (64, 2), (64, 2)]
+    # no tables at the band-limit: one launch per map
+    rec = types.SimpleNamespace(L=64, N_scal=64, scales=[(j, 64, 0, 0) for j in range(0, 3)],
+                                tuning=lambda: {64: {"table_anal": False, "table_synth": False}})
+    assert bench.legendre_launches(rec, "table_anal") == [(64, 1)] * 5
