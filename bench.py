@@ -419,6 +419,12 @@ def rooflines(stats, a, peaks, batch, bandlimits, tables=None):
                                                "reads and f_lm writes")
     else:
         roof["traffic"] = None
+    if roof["traffic"] and variant == "table":
+        # the table kernels are bound by HBM (64 flop per table byte, 128 where two maps
+        # share a stream, below the FP16 ridge): their DRAM traffic against the HBM peak
+        sec = roof["ms_per_step"] / 1000.0
+        roof["traffic_gbs"] = roof["traffic"] / sec / 1e9
+        roof["traffic_frac_of_hbm"] = roof["traffic_gbs"] / pk["hbm"][0]
     roof["note"] = "achieved and traffic are per step of the stage (all its launches)"
     # the dense theta-quadrature products of FP32 / TF32X3 plans, as a labelled extra
     if "theta_quad" in recs and a.precision != "fp64":

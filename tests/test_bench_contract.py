@@ -122,6 +122,8 @@ def test_stage_rooflines_follow_the_work_of_each_stage():
                                    "leg_synth": ("table", 30e9, per1, launches)})
     want5 = sum(per1[n] + k * rest * (n / n0) ** 2 * 64 / b0 for n, k in launches)
     assert roof5["traffic"] == pytest.approx(want5)
+    assert roof5["traffic_gbs"] == pytest.approx(want5 / 0.025 / 1e9)
+    assert roof5["traffic_frac_of_hbm"] == pytest.approx(want5 / 0.025 / 1e9 / 6000.0)
 
 
 def test_legendre_launches_pair_maps_at_one_band_limit():
