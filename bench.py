@@ -260,8 +260,8 @@ def run_reference(a, rank):
 
 # ---------------------------------------------------------------- rooflines
 def peak_table(peaks):
-    """Peaks used for the roofline fractions: measured where the driver wrote
-    them (MEASURED_PEAKS.json), else the fallback figures; each with its source."""
+    """Peaks used for the roofline fractions: the measured ones where
+    MEASURED_PEAKS.json holds them, else the fallback figures; each with its source."""
     def get(k):
         if k in peaks:
             return float(peaks[k]), "of measured"

@@ -47,7 +47,7 @@ extern "C" {
 #define S2LET_ERR_ALLOC (-2)       /* device or host allocation failed            */
 #define S2LET_ERR_CUDA (-3)        /* a CUDA runtime call or kernel launch failed */
 #define S2LET_ERR_TIMEOUT (-4)     /* a bounded device-side wait gave up          */
-#define S2LET_ERR_UNSUPPORTED (-5) /* valid request this build does not support   */
+#define S2LET_ERR_UNSUPPORTED (-5) /* valid request the library does not support   */
 
 /* plan flags (bitwise or) */
 #define S2LET_REAL 0x0           /* real maps (default)                        */

@@ -144,9 +144,9 @@ def psi_l0_bspline(L, B, j, J):
     """Psi^j_l0 = sqrt((2l+1)/(4 pi)) kappa(l / lambda^j) with kappa(t) =
     sqrt(k(t/lambda) - k(t)) (Sect. 2.2) for j < J.  The finest scale j = J
     takes the remainder, kappa_J(l)^2 = 1 - k(l / lambda^J), so that the
-    squared kernels of all scales sum to one for every l < L (the reading of
-    this build: the paper's telescoping sum would end at k(l / lambda^(J+1)),
-    which is 1 only at l = 0 for this k)."""
+    squared kernels of all scales sum to one for every l < L (the reading taken
+    here: the paper's telescoping sum would end at k(l / lambda^(J+1)), which
+    is 1 only at l = 0 for this k)."""
     out = np.zeros(L)
     for l in range(L):
         if j < J:

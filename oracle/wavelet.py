@@ -130,7 +130,7 @@ def noise_std(L, B, J0, kernel="sd"):
 def hard_threshold(f_wav, sigma, L, B, J0, nsigma=3.0, kernel="sd"):
     """Eq. (threshold) with T^j = nsigma sigma^j: a sample of scale j is set to zero
     where its modulus is below T^j and kept otherwise (the paper writes the test
-    on the signed coefficient; the modulus is the reading of this build)."""
+    on the signed coefficient; the modulus is the reading taken here)."""
     _, s_j = noise_std(L, B, J0, kernel)
     return [np.where(np.abs(w) < nsigma * sigma * s, 0.0 * w, w) for w, s in zip(f_wav, s_j)]
 
