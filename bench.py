@@ -52,18 +52,9 @@ WORK = {
 # kernels, "table": the kernels that stream the plan's Legendre tables).  A stage
 # or variant missing here has no capture of its current kernel, and its traffic
 # is reported as null
+# The table kernels have no entry: their one capture (profiles/leg_h16_L1024_b64.md)
+# predates later changes to them and the two-map kernels were not captured.
 TRAFFIC = {
-    # k_leg_h16<false> (synthesis on the FP16 tables), full-band-limit launch at
-    # L = 1024, 64 maps: 2461.2 + 478.0 MB, profiles/leg_h16_L1024_b64.md; scaled
-    # as its table part (one table copy) plus the rest by N^2 x maps
-    ("leg_synth", "table"): {
-        "bytes_at": (1024, 64, 2939.1e6),
-        "source": "ncu dram read+write of k_leg_h16 (synthesis) at L=1024 x 64 maps (2939.1 MB per launch): "
-                  "the table copy it streams scaled as the table, the rest by N^2 x maps"},
-    ("leg_anal", "table"): {
-        "bytes_at": (1024, 64, 2789.4e6),
-        "source": "ncu dram read+write of k_leg_h16 (analysis) at L=1024 x 64 maps (2789.4 MB per launch): "
-                  "the table copy it streams scaled as the table, the rest by N^2 x maps"},
     # k_leg_anal_tc, full-band-limit launch at L = 1024, 64 maps: 772.0 + 255.5 MB
     # (G and the recurrence tables read, f_lm written), profiles/quad_anal_tc_L1024_b64_tf32x3.md
     ("leg_anal", "recurrence"): {

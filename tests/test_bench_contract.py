@@ -45,7 +45,7 @@ def test_reference_arm_other_ranks_print_nothing():
                 env={"RANK": "1", "WORLD_SIZE": "2"}) == []
 
 
-def test_stage_rooflines_follow_the_work_of_each_stage():
+def test_stage_rooflines_follow_the_work_of_each_stage(monkeypatch):
     """The per-stage roofline records on synthetic stage statistics: byte-counted
     stages (ring DFTs, quadrature) against HBM, the Legendre contractions against
     the pipe of their precision, the dominant stage picked by time, and the
@@ -104,9 +104,12 @@ def test_stage_rooflines_follow_the_work_of_each_stage():
     assert roof3["executed_mma_frac"] == pytest.approx(3 * 200.0 / 1800.0) and "FP16" in roof3["peak_source"]
     assert roof3["table_gbs"] == pytest.approx(30e9 / 0.025 / 1e9)
     assert roof3["table_frac_of_hbm"] == pytest.approx(1200.0 / 6000.0)
-    # traffic of the table kernels: the table copy per launch plus the rest of the
-    # captured launch scaled by N^2 x maps; no capture at the capture's band-limit -> None
-    n0, b0, by = bench.TRAFFIC[("leg_anal", "table")]["bytes_at"]
+    # no capture of the table kernels as they are: no traffic
+    assert ("leg_anal", "table") not in bench.TRAFFIC and roof3["traffic"] is None
+    # with a capture, the traffic of the table kernels is the table copy per launch
+    # plus the rest of the captured launch scaled by N^2 x maps
+    n0, b0, by = 1024, 64, 2.8e9
+    monkeypatch.setitem(bench.TRAFFIC, ("leg_anal", "table"), {"bytes_at": (n0, b0, by), "source": "a capture"})
     per1 = dict(per)
     per1[n0] = 2e9
     roof4, _, _ = bench.rooflines(stats, a, peaks, 64, [2048, 8, 4],
