@@ -71,8 +71,9 @@ class Plan:
     lowest scale J_min (Sect. 2.2), real or complex, multiresolution or not,
     precision "fp64", "fp32" or "tf32x3", generating functions `kernel` "sd"
     (smooth scale-discretised) or "bspline" (footnote of Sect. 2.2).  TF32X3
-    plans store the Legendre values of each band-limit that fits the table budget
-    unless leg_recurrence is set (see table_bytes())."""
+    plans (split tensor-core contractions) store the Legendre values of each
+    band-limit up to 2048 that fits the table budget, as FP16 hi/lo parts in two
+    copies, unless leg_recurrence is set (see table_bytes())."""
 
     def __init__(self, L, B, J_min, batch=1, real=True, multires=True, precision="fp64",
                  quad_fft64=False, tc_split3=False, device=None, kernel="sd", quad_dense=False,
